@@ -1,0 +1,132 @@
+/*
+ * Oracle for the recombination hot path of Jedamzik, Abel & Ali-Haimoud,
+ * "Cosmic Recombination in the Presence of Primordial Magnetic Fields"
+ * (arXiv:2312.11448).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded FP64
+ * restatement of what the GPU path computes, written from the paper.  Only the
+ * test suite, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it.  It shares no code, header, constant table or helper with the CUDA
+ * library; the two agree only because both follow the same definitions.
+ *
+ * Parity status of each function is stated beside it: "pinned by ..." names
+ * the independent check in tests/ that would fail on a plausible mistake.
+ *
+ * Conventions
+ *   - Cells are indexed c = (iz*n + iy)*n + ix of an n^3 periodic box.
+ *   - Velocities are peculiar velocities in km/s; vel4 is [n^3][4] with the
+ *     fourth slot unused.
+ *   - Every function returns 0 on success and a negative code on bad input.
+ */
+#ifndef REC_ORACLE_H
+#define REC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Cosmological and model parameters (Sec. II.C defaults: h=0.67,
+ * Omega_b h^2=0.0224, Omega_c h^2=0.12, Y_p=0.24; box 24 kpc comoving). */
+typedef struct {
+  double h, omega_b_h2, omega_c_h2, Y_p;
+  double T_cmb0;      /* K; not printed in the paper, 2.7255 taken */
+  double N_eff;       /* not printed in the paper, 3.046 taken */
+  double L_box_kpc;   /* comoving box side */
+  double fudge;       /* 1.14 multiplying the case-B coefficient (Sec. III.A.1) */
+  double heating;     /* uniform heating Gamma expressed per mean hydrogen atom, eV/s (Sec. VI) */
+} orc_cosmo;
+
+/* Background quantities at redshift z: out[0]=H [1/s], out[1]=nbar_H [1/m^3],
+ * out[2]=T_gamma [K], out[3]=Omega_r, out[4]=Omega_Lambda.  Pinned by closed forms. */
+int orc_background(const orc_cosmo* cp, double z, double* out);
+
+/* Cosmic time elapsed from z_from down to z_to (z_from > z_to), seconds.
+ * Pinned by the matter+radiation closed form. */
+double orc_dt(const orc_cosmo* cp, double z_from, double z_to);
+
+/* Rate coefficients of the effective three-level atom (Sec. III.A.1,
+ * Eqs. rec0, n2s-sol, Cfactor): out[0]=alpha_e(T_b) [m^3/s],
+ * out[1]=beta_e(T_gamma) [1/s per 2s atom], out[2]=exp(-E_alpha/kT_gamma),
+ * out[3]=Lambda_2gamma, out[4]=8 pi H/lambda_alpha^3 [1/(m^3 s)]...per n_1s,
+ * out[5]=Saha factor (2 pi m_e k T/h^2)^{3/2} exp(-E_ion/kT) [1/m^3].
+ * Pinned by textbook case-B values and Saha equilibrium. */
+int orc_rates(const orc_cosmo* cp, double z, double T_b, double* out);
+
+/* Hydrogen Saha ionisation fraction per cell at redshift z (T_b = T_gamma). */
+int orc_saha_xe(const orc_cosmo* cp, double z, int64_t n3, const double* delta, double* x_out);
+
+/* One recombination step z_from -> z_to in n_sub substeps (Sec. IV, Eq.
+ * dotne-mix; Eq. Tb-evolution; Eq. alpha-def).  mixing: 0 = TALLY (local 2s
+ * population from the absorbed-Ly-alpha tallies), 1 = FULL (the paper's
+ * full-mixing limit).  In/out: x (ionisation fraction), T (K), U ([n^3][3],
+ * km/s, may be NULL).  tally may be NULL in FULL mode.  emis (may be NULL)
+ * receives alpha_e n_e^2 at the end state.  stats[0]=lambda, [1]=C_mix,
+ * [2]=X_e, [3]=Newton iterations of the last substep, [4]=S_1s used,
+ * [5]=dt of the last substep.  Pinned by Saha, the standard TLA ODE, the
+ * two-zone ODE system and the global-rate identity. */
+int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_from, double z_to,
+                 const double* delta, double* x, double* T, double* U, const uint32_t* tally,
+                 double* emis, double* stats);
+
+/* Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11).  Pinned by
+ * statistical tests (uniformity, bit balance, avalanche). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Transport scalars at redshift z for an n^3 box: out[0] = kappa, cells of
+ * Hubble drift per km/s of velocity; out[1] = cth, so that the thermal
+ * velocity in cells is sqrt(T * cth). */
+int orc_transport_params(const orc_cosmo* cp, int n, double z, double* out);
+
+/* Packet allocation (binary32 or binary64 emission weights): P[0..n^3] is
+ * the exclusive prefix of packets per cell, P[n^3] = n_packets.  Pinned by
+ * exact totals and the expected count per cell. */
+int orc_allocate_f32(int n, const float* emis, uint64_t n_packets, uint64_t seed, uint32_t step,
+                     uint32_t box, uint32_t* P);
+int orc_allocate_f64(int n, const double* emis, uint64_t n_packets, uint64_t seed, uint32_t step,
+                     uint32_t box, uint32_t* P);
+
+/* One emitted packet, for the closed-form and brute-force checks. */
+typedef struct {
+  uint32_t home, j, absorb, crossings;
+  double f[3];     /* offset of the emission point inside the home cell */
+  double dir[3];   /* unit direction */
+  double xi;       /* emission frequency offset, Doppler units */
+  double u0;       /* resonance distance in cells of Hubble drift at emission */
+} orc_packet;
+
+/* Ballistic Ly-alpha packet transport (binary32 / binary64 arithmetic).
+ * counters[0]=emitted, [1]=absorbed, [2]=packets stopped by the crossing cap,
+ * [3]=total face crossings.  dump (may be NULL) receives up to dump_cap
+ * packets in emission order.  Pinned by the closed-form resonance cell with
+ * U = 0, conservation, and a brute-force crossing enumeration. */
+int orc_transport_f32(const orc_cosmo* cp, int n, double z, uint64_t seed, uint32_t step, uint32_t box,
+                      uint64_t n_packets, const float* emis, const float* vel4, const float* T,
+                      const float* quant, int M, uint32_t* tally, uint64_t* counters,
+                      orc_packet* dump, int64_t dump_cap);
+int orc_transport_f64(const orc_cosmo* cp, int n, double z, uint64_t seed, uint32_t step, uint32_t box,
+                      uint64_t n_packets, const double* emis, const double* vel4, const double* T,
+                      const double* quant, int M, uint32_t* tally, uint64_t* counters,
+                      orc_packet* dump, int64_t dump_cap);
+
+/* Objective over a trajectory of n_steps steps through the node redshifts
+ * zs[0..n_steps] with fixed per-step tallies ([n_steps][n^3], NULL in FULL
+ * mode).  objective: 1 = volume-averaged X_e at the node nearest z_star,
+ * 2 = visibility g = (d tau/dz) exp(-tau) at that node, tau integrated from
+ * the last node.  a_pert (may be NULL) is added to every step's absorbed
+ * fraction.  Xe_hist (may be NULL) receives X_e at every node. */
+int orc_traj_objective(const orc_cosmo* cp, int n, int mixing, int n_sub, int n_steps, const double* zs,
+                       const uint32_t* tallies, const double* delta, const double* x0, const double* T0,
+                       const double* a_pert, int objective, double z_star, double* J, double* Xe_hist);
+
+/* Forward-mode tangent of the same objective along the direction
+ * (d_delta, d_T0, d_a): J[0] = objective, J[1] = its directional derivative. */
+int orc_traj_tangent(const orc_cosmo* cp, int n, int mixing, int n_sub, int n_steps, const double* zs,
+                     const uint32_t* tallies, const double* delta, const double* x0, const double* T0,
+                     const double* d_delta, const double* d_T0, const double* d_a, int objective,
+                     double z_star, double* J);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,132 @@
+"""Oracle pins: background cosmology, rate coefficients, detailed balance, Saha.
+
+Each check compares the oracle with something it does not compute itself:
+closed forms, textbook values (tests/golden/textbook_values.json) or numbers
+printed in the paper (tests/golden/paper_values.json).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+TB = json.load(open(os.path.join(GOLD, "textbook_values.json")))
+PV = json.load(open(os.path.join(GOLD, "paper_values.json")))
+
+
+def test_hubble_today_and_radiation(cosmo):
+    bg = O.background(cosmo, 0.0)
+    # H0 = 67 km/s/Mpc
+    assert bg["H"] == pytest.approx(67.0e3 / 3.0856775814913673e22, rel=1e-12)
+    # Omega_r h^2 = Omega_gamma h^2 (1 + N_eff * 0.2271)
+    orh2 = TB["Omega_gamma_h2"]["value"] * (1 + 3.046 * TB["neutrino_factor"]["value"])
+    assert bg["Omega_r"] * 0.67 ** 2 == pytest.approx(orh2, rel=3e-3)
+    # flat: Omega_m + Omega_r + Omega_L = 1
+    om = (0.0224 + 0.12) / 0.67 ** 2
+    assert om + bg["Omega_r"] + bg["Omega_L"] == pytest.approx(1.0, abs=1e-14)
+
+
+def test_hubble_scaling_and_density(cosmo):
+    b0 = O.background(cosmo, 0.0)
+    om = (0.0224 + 0.12) / 0.67 ** 2
+    for z in (600.0, 1100.0, 1800.0):
+        bg = O.background(cosmo, z)
+        a1 = 1 + z
+        expect = b0["H"] * math.sqrt(om * a1 ** 3 + b0["Omega_r"] * a1 ** 4 + b0["Omega_L"])
+        assert bg["H"] == pytest.approx(expect, rel=1e-13)
+        assert bg["nH"] == pytest.approx(b0["nH"] * a1 ** 3, rel=1e-13)
+        assert bg["Tg"] == pytest.approx(2.7255 * a1, rel=1e-15)
+    # n_H today from rho_crit: (1 - Y_p) Omega_b rho_crit / m_H with rho_crit = 1.87834e-26 h^2 kg/m^3
+    nH0 = 0.76 * 0.0224 * 1.87834e-26 / TB["m_H_kg"]
+    assert b0["nH"] == pytest.approx(nH0, rel=2e-5)
+
+
+def test_dt_matches_matter_radiation_closed_form(cosmo):
+    """Cosmic time between two redshifts vs the closed form of a matter+radiation
+    universe, t(a) = [(2/3) u^{3/2} - 2 Omega_r u^{1/2}] / (H0 Omega_m^2),
+    u = Omega_m a + Omega_r (Lambda is below 1e-7 of H^2 at z > 500)."""
+    b0 = O.background(cosmo, 0.0)
+    om, orr, H0 = (0.0224 + 0.12) / 0.67 ** 2, b0["Omega_r"], b0["H"]
+
+    def t_of(z):
+        u = om / (1 + z) + orr
+        return ((2.0 / 3.0) * u ** 1.5 - 2 * orr * u ** 0.5) / (H0 * om ** 2)
+
+    for za, zb in ((1800.0, 1790.0), (1100.0, 1097.0), (700.0, 690.0)):
+        assert O.dt(cosmo, za, zb) == pytest.approx(t_of(zb) - t_of(za), rel=1e-6)
+
+
+def test_case_b_coefficient_vs_textbook(cosmo):
+    tb = TB["case_B_alpha_cm3_s"]
+    for T, a in zip(tb["T_K"], tb["alpha_B"]):
+        alpha = O.rates(cosmo, 1000.0, T)["alpha"] / PV["fudge"]["value"]  # m^3/s, fudge removed
+        assert alpha * 1e6 == pytest.approx(a, rel=tb["rel_tol"])
+
+
+def test_fudge_and_constants_printed_in_paper(cosmo):
+    r = O.rates(cosmo, 1100.0, 3000.0)
+    r0 = O.rates(O.default_cosmo(fudge=1.0), 1100.0, 3000.0)
+    assert r["alpha"] / r0["alpha"] == pytest.approx(1.14, rel=1e-14)
+    assert r["Lambda"] == PV["Lambda_2gamma"]["value"]
+    Tg = O.background(cosmo, 1100.0)["Tg"]
+    E_alpha_eV = -TB["k_B"] * Tg * math.log(r["e_alpha"]) / TB["eV_J"]
+    assert E_alpha_eV == pytest.approx(PV["E_alpha_eV"]["value"], rel=PV["E_alpha_eV"]["rel_tol"])
+    # E_alpha = hc / lambda_alpha within the fine-structure spread
+    lam_nm = TB["h_planck"] * TB["c_m_s"] / (E_alpha_eV * TB["eV_J"]) * 1e9
+    assert lam_nm == pytest.approx(TB["Lyman_alpha_nm"]["value"], rel=2e-5)
+    # R_alpha = 8 pi H / (lambda_alpha^3 n_1s): K_R * lambda^3 / (8 pi H) = 1
+    H = O.background(cosmo, 1100.0)["H"]
+    assert r["K_R"] * (lam_nm * 1e-9) ** 3 / (8 * math.pi * H) == pytest.approx(1.0, rel=1e-4)
+
+
+def _saha_textbook(T, nH):
+    """Hydrogen Saha equation x^2/(1-x) = (2 pi m_e k T/h^2)^{3/2} exp(-E_ion/kT) / n_H."""
+    me, k, h, eV = TB["m_e_kg"], TB["k_B"], TB["h_planck"], TB["eV_J"]
+    S = (2 * math.pi * me * k * T / h ** 2) ** 1.5 * math.exp(-TB["H_ionisation_eV"]["value"] * eV / (k * T))
+    r = S / nH
+    return 2.0 / (1.0 + math.sqrt(1.0 + 4.0 / r))
+
+
+def test_detailed_balance_gives_saha(cosmo):
+    """beta_e is fixed by detailed balance (Sec. III.A.1): the net rate of
+    Eq. (rec) vanishes at Saha equilibrium when T_b = T_gamma, i.e.
+    beta e_alpha / alpha(T_gamma) must equal the Saha factor."""
+    for z in (1000.0, 1400.0, 1800.0):
+        bg = O.background(cosmo, z)
+        r = O.rates(cosmo, z, bg["Tg"])
+        lhs = r["beta"] * r["e_alpha"] / r["alpha"]
+        me, k, h, eV = TB["m_e_kg"], TB["k_B"], TB["h_planck"], TB["eV_J"]
+        T = bg["Tg"]
+        rhs = (2 * math.pi * me * k * T / h ** 2) ** 1.5 * math.exp(-TB["H_ionisation_eV"]["value"] * eV / (k * T))
+        assert lhs == pytest.approx(rhs, rel=2e-5)
+
+
+def test_saha_initial_state(cosmo):
+    delta = np.array([0.1, 1.0, 3.0, 30.0])
+    for z in (1600.0, 1800.0, 1400.0):
+        x = O.saha_xe(cosmo, z, delta)
+        nH = O.background(cosmo, z)["nH"]
+        Tg = O.background(cosmo, z)["Tg"]
+        for xi, d in zip(x, delta):
+            assert xi == pytest.approx(_saha_textbook(Tg, nH * d), rel=1e-6)
+    # around 0.99 at z = 1600 for mean density (rough hand estimate of the blueprint)
+    assert 0.98 < O.saha_xe(cosmo, 1600.0, np.ones(1))[0] < 0.995
+
+
+def test_trajectory_tracks_saha_at_high_redshift(cosmo):
+    """Recombination follows Saha equilibrium closely at z >~ 1600."""
+    from paper_2312_11448_gb300.inputs import z_schedule
+    zs = z_schedule(1800.0, 1650.0, 40)
+    d = np.ones(1)
+    x = O.saha_xe(cosmo, 1800.0, d)
+    T = np.array([O.background(cosmo, 1800.0)["Tg"]])
+    for s in range(40):
+        x, T, _, _, _ = O.rec_step(cosmo, 1, zs[s], zs[s + 1], d, x, T, mixing="full")
+        xs = _saha_textbook(O.background(cosmo, zs[s + 1])["Tg"], O.background(cosmo, zs[s + 1])["nH"])
+        assert abs(x[0] - xs) < 2e-4
+        # the neutral fraction lags Saha (recombination is slower) by a modest amount
+        assert 1.0 <= (1 - xs) / (1 - x[0]) < 1.15
