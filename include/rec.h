@@ -1,0 +1,186 @@
+/*
+ * rec.h -- C ABI of the GB300 recombination hot path.
+ *
+ * Implements, for a periodic box of n^3 cells, the two data-parallel parts of
+ * the recombination step of Jedamzik, Abel & Ali-Haimoud, "Cosmic
+ * Recombination in the Presence of Primordial Magnetic Fields"
+ * (arXiv:2312.11448):
+ *
+ *   lya_transport  Monte-Carlo Ly-alpha packets emitted per cell in proportion
+ *                  to the local recombination rate alpha_e n_e^2 (Sec. III.B and
+ *                  its footnote on the global loss-rate integral), streamed along
+ *                  isotropic directions while the Hubble expansion redshifts them
+ *                  (Appendix A, step (4): dx = -H dl / v_th) with the bulk-flow
+ *                  Doppler shift omega_r = omega (1 - U_par) (Appendix A), and
+ *                  absorbed into integer per-cell tallies where they come back
+ *                  into line resonance.
+ *   rec_step       the per-cell effective three-level-atom update of x_e
+ *                  (Eq. rec0 with the 2s population of Eq. n2s-sol; full-mixing
+ *                  rate Eq. dotne-mix, Sec. IV.B) and of T_b (Eq. Tb-evolution),
+ *                  plus Compton drag on the peculiar velocity (Eq. alpha-def in
+ *                  Eq. momentum).
+ *   rec_step_adjoint  the reverse (adjoint) of rec_step with the tallies held
+ *                  fixed, for gradients of X_e (Sec. II.A) and of the visibility
+ *                  function.
+ *
+ * Conventions (all entry points)
+ *   - Every call returns a rec_status; no C++ exception crosses the ABI.
+ *     On failure, rec_last_error(ctx) describes the cause.
+ *   - Field buffers are DEVICE pointers owned by the caller.  They must stay
+ *     valid until rec_free.  The context owns its own scratch (packet prefix,
+ *     reduction partials, device scalars, the emission-profile table).
+ *   - Cells are indexed c = (iz*n + iy)*n + ix; the box is periodic.
+ *   - All work is enqueued on the stream given to rec_init; calls return
+ *     without synchronising (results are valid once the stream reaches them).
+ *     Device-side counters and statistics go to a device rec_stats record.
+ *   - Precision forms: REC_PREC_FP64 stores delta, vel4, T, emis in double and
+ *     runs all arithmetic in binary64; REC_PREC_MIXED stores them in float,
+ *     streams packets in binary32, and keeps x_e, the net
+ *     recombination-minus-photoionisation difference and the volume sums in
+ *     binary64.  x_e is double in both forms.
+ */
+#ifndef REC_H
+#define REC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rec_ctx rec_ctx; /* opaque; created by rec_init, owned by the library */
+
+typedef enum {
+  REC_OK = 0,
+  REC_EINVAL = 1,   /* invalid argument: NULL pointer, bad size or mode */
+  REC_ENOMEM = 2,   /* device or host allocation failed */
+  REC_ECUDA = 3,    /* a CUDA call failed; message in rec_last_error */
+  REC_ETIMEOUT = 4, /* a bounded device-side wait expired */
+  REC_ESTATE = 5    /* call out of order (e.g. transport before emission weights exist) */
+} rec_status;
+
+typedef enum { REC_PREC_FP64 = 0, REC_PREC_MIXED = 1 } rec_precision;
+
+/* REC_MIX_TALLY: the local 2s population follows the Ly-alpha packets absorbed
+ *   in each cell during this step's transport (J_i proportional to absorptions
+ *   per neutral atom).  REC_MIX_FULL: the paper's full-mixing limit,
+ *   Eq. dotne-mix (tallies unused). */
+typedef enum { REC_MIX_TALLY = 0, REC_MIX_FULL = 1 } rec_mixing;
+
+typedef struct {
+  /* Cosmology, Sec. II.C defaults: 0.67, 0.0224, 0.12, 0.24. */
+  double h, omega_b_h2, omega_c_h2, Y_p;
+  double T_cmb0;     /* K; not printed in the paper (2.7255 is the usual value) */
+  double N_eff;      /* not printed in the paper (3.046) */
+  double L_box_kpc;  /* comoving box side; 24 in Sec. II.C */
+  double fudge;      /* 1.14, multiplies the case-B coefficient (Sec. III.A.1) */
+  double heating;    /* uniform heating Gamma (Sec. VI) per mean hydrogen atom, eV/s; 0 = off */
+  uint64_t seed;     /* Philox key for the packet streams */
+  int32_t n_sub;     /* backward-Euler substeps per rec_step (>= 1) */
+  int32_t precision; /* rec_precision */
+  int32_t mixing;    /* rec_mixing */
+  int32_t n_quantiles;               /* >= 2 */
+  const double* emission_quantiles;  /* HOST array [n_quantiles]: inverse CDF of the
+                                        emission-frequency profile in Doppler units at
+                                        (k+1/2)/n_quantiles; copied at rec_init */
+} rec_params;
+
+typedef struct {
+  int32_t n;          /* cube side, 1 <= n <= 1024 */
+  void* delta;        /* overdensity rho_b/<rho_b> [n^3]: float (MIXED) | double (FP64); read-only */
+  void* vel4;         /* peculiar velocity {Ux,Uy,Uz,unused} km/s [n^3]: float4 | double4;
+                         updated by rec_step (Compton drag) */
+  double* x_e;        /* ionisation fraction n_e/n_H [n^3]; updated by rec_step */
+  void* T;            /* baryon temperature K [n^3]: float | double; updated by rec_step */
+  uint32_t* tally;    /* absorbed packets per cell [n^3]; lya_transport adds, rec_step zeroes */
+  void* emis;         /* emission weight alpha_e n_e^2 [n^3]: float | double; written by
+                         rec_state_init / rec_refresh / rec_step, read by lya_transport */
+  uint64_t n_packets; /* packets emitted per lya_transport call, < 2^32 */
+} rec_box;
+
+/* Device-side statistics record (caller-owned device memory). */
+typedef struct {
+  uint64_t emitted, absorbed, capped, crossings; /* transport counters of the last call */
+  double X_e;     /* <rho_b x_e>/<rho_b> after the last rec_step (Sec. II.A) */
+  double lambda;  /* <alpha_e n_e^2>/<n_1s> at the end state, 1/s */
+  double C_mix;   /* Peebles factor with R_alpha -> R_alpha^mix (Eq. Cfactor, Sec. IV.B) */
+  double S1s;     /* sum over cells of delta (1 - x_e) at the end state */
+  int32_t newton_passes; /* Newton evaluations of the last substep */
+  int32_t flags;         /* bit 0: Newton did not converge; bit 1: packets hit the crossing cap;
+                            bit 2: non-finite or negative emission weight */
+} rec_stats;
+
+/* Create a context for n_boxes boxes (only n_boxes == 1 is supported here).
+ * Validates params and buffers, copies the emission-profile table, allocates
+ * scratch.  Does not touch the field buffers.
+ * Errors: REC_EINVAL, REC_ENOMEM, REC_ECUDA. */
+rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_boxes, void* cuda_stream,
+                    rec_ctx** out);
+
+/* Initial state at redshift z: T = T_gamma(z) and x_e from the hydrogen Saha
+ * equation per cell (T_b = T_gamma), then the emission weights as rec_refresh. */
+rec_status rec_state_init(rec_ctx* ctx, double z);
+
+/* Recompute the emission weights alpha_e(T) n_e^2 and the volume sums from the
+ * current x_e, T at redshift z.  Needed once after the caller writes x_e or T
+ * directly; rec_step keeps them current otherwise. */
+rec_status rec_refresh(rec_ctx* ctx, double z);
+
+/* Ly-alpha packet transport at redshift z for step index `step` (keys the
+ * random streams).  Emits n_packets packets (allocation proportional to emis),
+ * marches each to its resonance cell and adds it to tally.  Counters go to
+ * dev_stats (device pointer, may be NULL).
+ * Errors: REC_ESTATE if emission weights were never computed; REC_ECUDA. */
+rec_status lya_transport(rec_ctx* ctx, int32_t step, double z, rec_stats* dev_stats);
+
+/* One recombination step z_from -> z_to (z_from > z_to) in n_sub backward-Euler
+ * substeps, using the tallies of this step (TALLY mode); zeroes the tallies and
+ * writes the emission weights for the next transport.  Statistics go to
+ * dev_stats (device pointer, may be NULL).
+ * Errors: REC_EINVAL (z order), REC_ESTATE, REC_ECUDA. */
+rec_status rec_step(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
+
+/* Reverse of rec_step (FP64 form only), tallies held fixed.
+ *   x_in, T_in, vel4_in: the state BEFORE the step (device, FP64 layouts);
+ *   tally_in: this step's tallies (device u32 [n^3], may be NULL in FULL mode).
+ *   xbar, Tbar: in = adjoint of the state after the step, out = before (device f64 [n^3]);
+ *   Ubar: adjoint of vel4 (device double4 [n^3], in/out) or NULL if zero;
+ *   g_delta, g_a: accumulated (+=) gradients with respect to the overdensity and to
+ *   the absorbed-Ly-alpha fraction a_i = tally_i / sum(tally) of this step
+ *   (device f64 [n^3]);
+ *   Xe_bar_out: adjoint of X_e at the step's end node (added before reversing).
+ * Errors: REC_EINVAL (precision or z order), REC_ECUDA. */
+rec_status rec_step_adjoint(rec_ctx* ctx, int32_t step, double z_from, double z_to, const double* x_in,
+                            const double* T_in, const double* vel4_in, const uint32_t* tally_in, double* xbar,
+                            double* Tbar, double* Ubar, double* g_delta, double* g_a, double Xe_bar_out);
+
+/* Adds the adjoint of X_e = sum(delta x)/sum(delta) at a node to xbar and g_delta
+ * (the start node of a trajectory; rec_step_adjoint handles its end node). */
+rec_status rec_xe_adjoint(rec_ctx* ctx, const double* x, double Xe_bar, double* xbar, double* g_delta);
+
+/* Objective on an X_e history over node redshifts zs[0..n_nodes-1] (decreasing),
+ * host computation.  objective 1: X_e at the node nearest z_star.  objective 2:
+ * the visibility function g = (d tau/dz) exp(-tau) at that node, with the Thomson
+ * optical depth tau(z) = int sigma_T c nbar_H X_e / ((1+z) H) dz from the last
+ * node (trapezoid on the nodes).  Writes J and dJ/dX_e at every node.
+ * Errors: REC_EINVAL. */
+rec_status rec_objective(const rec_params* params, const double* zs, const double* Xe, int32_t n_nodes,
+                         int32_t objective, double z_star, double* J, double* dJ_dXe);
+
+/* Transport scalars at redshift z for an n^3 box (host computation, no GPU
+ * needed): out[0] = kappa = n / (H a L), cells of Hubble drift per km/s of
+ * velocity; out[1] = cth = kappa^2 2 k_B / m_H, so that the thermal velocity
+ * v_th = sqrt(2 k T / m_H) of Appendix A is sqrt(T cth) cells.
+ * Errors: REC_EINVAL. */
+rec_status rec_transport_params(const rec_params* params, int32_t n, double z, double* out);
+
+/* Release the context and its scratch (NULL-safe).  Synchronises the stream. */
+void rec_free(rec_ctx* ctx);
+
+/* Last error message of ctx, or of the last failed rec_init when ctx is NULL. */
+const char* rec_last_error(const rec_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REC_H */

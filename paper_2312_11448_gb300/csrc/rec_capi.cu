@@ -1,0 +1,256 @@
+// C ABI of the recombination library (declared in include/rec.h).
+//
+// Each entry point validates its arguments, enqueues kernels on the context
+// stream and returns a rec_status; no exception crosses the boundary.  The
+// context owns its scratch; field buffers belong to the caller.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rec_internal.cuh"
+
+namespace {
+
+thread_local std::string g_init_error;
+
+rec_status fail(rec_ctx* c, rec_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_init_error = msg;
+  return s;
+}
+
+rec_status cuda_fail(rec_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(c, REC_ECUDA, m);
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+rec_status check_params(const rec_params* p, std::string* why) {
+  if (!p) { *why = "params is NULL"; return REC_EINVAL; }
+  if (!(p->h > 0) || !(p->omega_b_h2 > 0) || !(p->omega_c_h2 >= 0) || !(p->Y_p >= 0 && p->Y_p < 1) ||
+      !(p->T_cmb0 > 0) || !(p->N_eff >= 0) || !(p->L_box_kpc > 0) || !(p->fudge > 0) || !is_finite(p->heating) ||
+      p->heating < 0) {
+    *why = "cosmological parameters out of range";
+    return REC_EINVAL;
+  }
+  if (p->n_sub < 1 || p->n_sub > 4096) { *why = "n_sub must be in [1, 4096]"; return REC_EINVAL; }
+  if (p->precision != REC_PREC_FP64 && p->precision != REC_PREC_MIXED) { *why = "unknown precision"; return REC_EINVAL; }
+  if (p->mixing != REC_MIX_TALLY && p->mixing != REC_MIX_FULL) { *why = "unknown mixing mode"; return REC_EINVAL; }
+  if (p->n_quantiles < 2 || !p->emission_quantiles) { *why = "emission profile table missing"; return REC_EINVAL; }
+  for (int i = 0; i < p->n_quantiles; ++i) {
+    if (!is_finite(p->emission_quantiles[i]) || (i > 0 && p->emission_quantiles[i] < p->emission_quantiles[i - 1])) {
+      *why = "emission profile table must be finite and non-decreasing";
+      return REC_EINVAL;
+    }
+  }
+  return REC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_boxes, void* cuda_stream,
+                    rec_ctx** out) {
+  g_init_error.clear();
+  if (!out) return fail(nullptr, REC_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  rec_status s = check_params(params, &why);
+  if (s != REC_OK) return fail(nullptr, s, why);
+  if (!boxes || n_boxes != 1) return fail(nullptr, REC_EINVAL, "exactly one box is supported");
+  const rec_box& b = boxes[0];
+  if (b.n < 1 || b.n > 1024) return fail(nullptr, REC_EINVAL, "box side n must be in [1, 1024]");
+  if (!b.delta || !b.vel4 || !b.x_e || !b.T || !b.tally || !b.emis)
+    return fail(nullptr, REC_EINVAL, "a field buffer is NULL");
+  if (b.n_packets >= (1ull << 32)) return fail(nullptr, REC_EINVAL, "n_packets must be below 2^32");
+
+  rec_ctx* c = new (std::nothrow) rec_ctx();
+  if (!c) return fail(nullptr, REC_ENOMEM, "host allocation failed");
+  c->params = *params;
+  c->params.emission_quantiles = nullptr;  // copied to the device below
+  c->box = b;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->n3 = (int64_t)b.n * b.n * b.n;
+  c->cosmo = rec::make_cosmo(*params);
+  c->sc = nullptr; c->sc_adj = nullptr; c->part = nullptr; c->P = nullptr; c->partQ = nullptr; c->quant = nullptr;
+  c->emis_ready = false;
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) { rec_status r = cuda_fail(nullptr, e, "device query"); delete c; return r; }
+  // streaming passes: a fixed grid (several blocks per SM) for reproducible sums
+  int64_t want = (c->n3 + rec::kPassThreads - 1) / rec::kPassThreads;
+  c->grid = (int)std::min<int64_t>(want, (int64_t)c->sm_count * 8);
+  if (c->grid < 1) c->grid = 1;
+  c->alloc_blocks = (int)((c->n3 + rec::kAllocChunk - 1) / rec::kAllocChunk);
+  c->transport_blocks = c->sm_count * 8;
+
+  size_t qbytes = (size_t)params->n_quantiles * (params->precision == REC_PREC_MIXED ? 4 : 8);
+  e = cudaMalloc(&c->sc, sizeof(rec::DevScalars));
+  if (e == cudaSuccess) e = cudaMalloc(&c->sc_adj, sizeof(rec::DevScalars));
+  if (e == cudaSuccess) e = cudaMalloc(&c->part, sizeof(double) * rec::kMaxSums * (size_t)c->grid);
+  if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(uint32_t) * (size_t)(c->n3 + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->partQ, sizeof(unsigned long long) * (size_t)c->alloc_blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&c->quant, qbytes);
+  if (e != cudaSuccess) {
+    rec_status r = (e == cudaErrorMemoryAllocation) ? fail(nullptr, REC_ENOMEM, "device allocation failed")
+                                                    : cuda_fail(nullptr, e, "cudaMalloc");
+    rec_free(c);
+    return r;
+  }
+  // emission-profile table in the working precision of the transport
+  std::vector<char> hq(qbytes);
+  for (int i = 0; i < params->n_quantiles; ++i) {
+    if (params->precision == REC_PREC_MIXED) ((float*)hq.data())[i] = (float)params->emission_quantiles[i];
+    else ((double*)hq.data())[i] = params->emission_quantiles[i];
+  }
+  rec::DevScalars zero;
+  std::memset(&zero, 0, sizeof(zero));
+  zero.lam_prev = -1.0;
+  e = cudaMemcpyAsync(c->quant, hq.data(), qbytes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->sc, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->sc_adj, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream);
+  // the host staging buffers go out of scope: wait for the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    rec_status r = cuda_fail(nullptr, e, "rec_init upload");
+    rec_free(c);
+    return r;
+  }
+  *out = c;
+  return REC_OK;
+}
+
+rec_status rec_state_init(rec_ctx* c, double z) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  if (!(z > 0) || !is_finite(z)) return fail(c, REC_EINVAL, "z must be positive");
+  cudaError_t e = rec::launch_state_init(c, z);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_state_init");
+  c->emis_ready = true;
+  return REC_OK;
+}
+
+rec_status rec_refresh(rec_ctx* c, double z) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  if (!(z > 0) || !is_finite(z)) return fail(c, REC_EINVAL, "z must be positive");
+  cudaError_t e = rec::launch_refresh(c, z);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_refresh");
+  c->emis_ready = true;
+  return REC_OK;
+}
+
+rec_status lya_transport(rec_ctx* c, int32_t step, double z, rec_stats* st) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  if (!(z > 0) || !is_finite(z)) return fail(c, REC_EINVAL, "z must be positive");
+  if (step < 0) return fail(c, REC_EINVAL, "step must be non-negative");
+  cudaError_t e = rec::launch_transport(c, step, z, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lya_transport");
+  return REC_OK;
+}
+
+rec_status rec_step(rec_ctx* c, int32_t step, double z_from, double z_to, rec_stats* st) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  (void)step;
+  if (!(z_from > z_to) || !(z_to > 0) || !is_finite(z_from)) return fail(c, REC_EINVAL, "need z_from > z_to > 0");
+  if (!c->emis_ready) return fail(c, REC_ESTATE, "state sums unknown: call rec_state_init or rec_refresh first");
+  cudaError_t e = rec::launch_rec_step(c, z_from, z_to, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_step");
+  return REC_OK;
+}
+
+rec_status rec_step_adjoint(rec_ctx* c, int32_t step, double z_from, double z_to, const double* x_in,
+                            const double* T_in, const double* vel4_in, const uint32_t* tally_in, double* xbar,
+                            double* Tbar, double* Ubar, double* g_delta, double* g_a, double Xe_bar_out) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  (void)step;
+  if (c->params.precision != REC_PREC_FP64) return fail(c, REC_EINVAL, "the adjoint needs the FP64 form");
+  if (c->params.n_sub != 1) return fail(c, REC_EINVAL, "the adjoint supports n_sub == 1");
+  if (!(z_from > z_to) || !(z_to > 0)) return fail(c, REC_EINVAL, "need z_from > z_to > 0");
+  if (!x_in || !T_in || !xbar || !Tbar || !g_delta) return fail(c, REC_EINVAL, "a required buffer is NULL");
+  if (Ubar && !vel4_in) return fail(c, REC_EINVAL, "Ubar needs vel4_in");
+  if (c->params.mixing == REC_MIX_TALLY && !tally_in) return fail(c, REC_EINVAL, "tally mode needs tally_in");
+  cudaError_t e = rec::launch_rec_step_adjoint(c, z_from, z_to, x_in, T_in, vel4_in, tally_in, xbar, Tbar, Ubar,
+                                               g_delta, g_a, Xe_bar_out);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_step_adjoint");
+  return REC_OK;
+}
+
+rec_status rec_xe_adjoint(rec_ctx* c, const double* x, double Xe_bar, double* xbar, double* g_delta) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  if (c->params.precision != REC_PREC_FP64) return fail(c, REC_EINVAL, "the adjoint needs the FP64 form");
+  if (!x || !xbar || !g_delta) return fail(c, REC_EINVAL, "a required buffer is NULL");
+  cudaError_t e = rec::launch_xe_adjoint(c, x, Xe_bar, xbar, g_delta);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_xe_adjoint");
+  return REC_OK;
+}
+
+rec_status rec_transport_params(const rec_params* p, int32_t n, double z, double* out) {
+  std::string why;
+  rec_status s = check_params(p, &why);
+  if (s != REC_OK) return fail(nullptr, s, why);
+  if (n < 1 || !out || !(z > 0)) return fail(nullptr, REC_EINVAL, "bad n, z or out");
+  rec::Cosmo cm = rec::make_cosmo(*p);
+  rec::transport_scalars(cm, n, z, &out[0], &out[1]);
+  return REC_OK;
+}
+
+rec_status rec_objective(const rec_params* p, const double* zs, const double* Xe, int32_t n_nodes,
+                         int32_t objective, double z_star, double* J, double* dJ) {
+  std::string why;
+  rec_status s = check_params(p, &why);
+  if (s != REC_OK) return fail(nullptr, s, why);
+  if (!zs || !Xe || !J || !dJ || n_nodes < 1 || (objective != 1 && objective != 2))
+    return fail(nullptr, REC_EINVAL, "bad objective arguments");
+  rec::Cosmo cm = rec::make_cosmo(*p);
+  int ks = 0;
+  for (int k = 1; k < n_nodes; ++k)
+    if (std::fabs(zs[k] - z_star) < std::fabs(zs[ks] - z_star)) ks = k;
+  for (int k = 0; k < n_nodes; ++k) dJ[k] = 0.0;
+  if (objective == 1) {
+    *J = Xe[ks];
+    dJ[ks] = 1.0;
+    return REC_OK;
+  }
+  // d tau/dz = c_k X_e,k with c_k = sigma_T c nbar_H / ((1+z) H)
+  std::vector<double> ck(n_nodes);
+  for (int k = 0; k < n_nodes; ++k)
+    ck[k] = rec::thomson_sigma_c() * rec::nH_bar(cm, zs[k]) / ((1.0 + zs[k]) * rec::hubble(cm, zs[k]));
+  double tau = 0.0;
+  for (int m = ks; m < n_nodes - 1; ++m) tau += 0.5 * (ck[m] * Xe[m] + ck[m + 1] * Xe[m + 1]) * (zs[m] - zs[m + 1]);
+  double e = std::exp(-tau);
+  double g = ck[ks] * Xe[ks] * e;
+  *J = g;
+  dJ[ks] += ck[ks] * e;
+  for (int m = ks; m < n_nodes - 1; ++m) {
+    double h = 0.5 * (zs[m] - zs[m + 1]);
+    dJ[m] -= g * h * ck[m];
+    dJ[m + 1] -= g * h * ck[m + 1];
+  }
+  return REC_OK;
+}
+
+void rec_free(rec_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->sc);
+  cudaFree(c->sc_adj);
+  cudaFree(c->part);
+  cudaFree(c->P);
+  cudaFree(c->partQ);
+  cudaFree(c->quant);
+  delete c;
+}
+
+const char* rec_last_error(const rec_ctx* c) {
+  if (!c) return g_init_error.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations of the GB300 recombination library (not part of the
+// ABI).  Host-side scalar physics lives in rec_cosmo.h; kernels are in
+// rec_transport.cu, rec_step.cu and rec_adjoint.cu; the C ABI in rec_capi.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "rec.h"
+
+namespace rec {
+
+// Launch geometry of the streaming passes: a fixed grid so that the
+// fixed-order reductions are bit-reproducible from run to run.
+constexpr int kPassThreads = 256;
+constexpr int kMaxSums = 8;            // block partials per reduction
+constexpr int kNewtonMaxPasses = 10;   // Newton evaluations launched per substep
+constexpr uint32_t kMaxCrossings = 1u << 20;  // per-packet cap on face crossings
+constexpr int kAllocThreads = 256;
+constexpr int kAllocItems = 16;        // consecutive cells per thread in the allocation scan
+constexpr int kAllocChunk = kAllocThreads * kAllocItems;
+
+// Device-resident scalars of one box.  Everything data-dependent stays on the
+// device so that calls never synchronise with the host.
+struct DevScalars {
+  // sums of the current state (end of the last rec_step, or rec_refresh)
+  double S1s;        // sum delta (1 - x)
+  double Sdx;        // sum delta x
+  double Sd;         // sum delta
+  double lam_state;  // <alpha n_e^2>/<n_1s> of the current state
+  double lam_prev;   // lambda of the previous step (<= 0: none)
+  double rmax;       // largest emission weight
+  // Newton iteration of the current substep
+  double lam;        // current iterate
+  double C;          // Peebles factor with R_alpha^mix
+  double omC;        // 1 - C
+  double G0;         // C beta e_alpha
+  double last_step;  // |last Newton step| / lambda
+  int32_t conv;      // 1 once converged
+  int32_t passes;    // Newton evaluations so far
+  int32_t flags;     // rec_stats.flags bits
+  uint32_t counter;  // last-block-done counter of the streaming passes
+  // transport
+  unsigned long long emitted, absorbed, capped, crossings;
+  unsigned long long tally_total;  // packets absorbed in the current tallies
+  unsigned long long sumQ;         // sum of quantised emission weights
+  unsigned long long alloc_u;      // systematic-sampling offset in [0, sumQ)
+  uint32_t alloc_counter;
+  int32_t emis_valid;
+};
+
+// Per-substep coefficients, computed on the host from the redshifts (no
+// data dependence), passed by value.
+struct StepCoef {
+  double dt;      // cosmic time of the substep, s
+  double H;       // Hubble rate at the substep end, 1/s
+  double nH;      // mean hydrogen density at the substep end, 1/m^3
+  double Tg;      // photon temperature at the substep end, K
+  double kc;      // Compton heating coefficient 8 sigma_T a_R T^4/(3 m_e c), 1/s
+  double kd;      // Compton drag coefficient per unit x: 4 sigma_T a_R T^4 (1-Y_p)/(3 c m_H), 1/s
+  double hq;      // heating term numerator 2 Gamma_per_H/(3k), K/s
+  double fHe;     // n_He/n_H
+  double beta;    // photo-ionisation rate per 2s atom at T_gamma, 1/s
+  double ea;      // exp(-E_alpha/kT_gamma)
+  double KR;      // 8 pi H / lambda_alpha^3 (R_alpha = KR / n_1s)
+  double L2g;     // two-photon rate
+  double fa;      // fudge * 1e-19 * a of the case-B fit (m^3/s)
+  double pb, pc, pd;  // remaining case-B fit constants
+  int32_t mixing;
+  int32_t last;   // 1 on the last substep of a rec_step
+};
+
+// Host-side cosmology of one context.
+struct Cosmo {
+  double H0, Om, Or, OL, nH0, T0, fHe, Yp, L_m, fudge, heat;
+};
+
+}  // namespace rec
+
+struct rec_ctx {
+  rec_params params;
+  rec_box box;
+  cudaStream_t stream;
+  int64_t n3;
+  rec::Cosmo cosmo;
+  // device scratch owned by the context
+  rec::DevScalars* sc;       // device scalars of the forward sweep
+  rec::DevScalars* sc_adj;   // device scalars of the reverse sweep
+  double* part;              // block partials [grid * kMaxSums]
+  uint32_t* P;               // packet prefix [n3 + 1]
+  unsigned long long* partQ; // allocation block sums / offsets [alloc blocks]
+  void* quant;               // emission-profile table (float or double) [n_quantiles]
+  int grid;                  // blocks of the streaming passes
+  int alloc_blocks;
+  int transport_blocks;
+  int sm_count;
+  bool emis_ready;
+  std::string err;
+};
+
+namespace rec {
+
+// rec_cosmo.h
+Cosmo make_cosmo(const rec_params& p);
+double hubble(const Cosmo& c, double z);
+double nH_bar(const Cosmo& c, double z);
+double T_gamma(const Cosmo& c, double z);
+double cosmic_dt(const Cosmo& c, double z_from, double z_to);
+void transport_scalars(const Cosmo& c, int n, double z, double* kappa, double* cth);
+StepCoef step_coef(const Cosmo& c, const rec_params& p, double z_from, double z_to, int last);
+double saha_S(double T);  // (2 pi m_e k T/h^2)^{3/2} exp(-E_ion/kT), 1/m^3
+double thomson_sigma_c(); // sigma_T c, m^3/s
+
+// rec_step.cu
+cudaError_t launch_state_init(rec_ctx* c, double z);
+cudaError_t launch_refresh(rec_ctx* c, double z);
+cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* st);
+// Newton passes for lambda of a substep on an arbitrary FP64 state (used by the adjoint).
+void enqueue_newton_passes(rec_ctx* c, DevScalars* sc, const StepCoef& k, const double* x, const double* T,
+                           const uint32_t* tally);
+
+// rec_transport.cu
+cudaError_t launch_transport(rec_ctx* c, int step, double z, rec_stats* st);
+
+// rec_adjoint.cu
+cudaError_t launch_rec_step_adjoint(rec_ctx* c, double z_from, double z_to, const double* x_in, const double* T_in,
+                                    const double* vel4_in, const uint32_t* tally_in, double* xbar, double* Tbar,
+                                    double* Ubar, double* g_delta, double* g_a, double Xe_bar_out);
+cudaError_t launch_xe_adjoint(rec_ctx* c, const double* x, double Xe_bar, double* xbar, double* g_delta);
+
+}  // namespace rec

@@ -1,0 +1,231 @@
+"""Thin Python binding of the C ABI in include/rec.h (argument marshalling only).
+
+Device buffers are torch tensors on the current CUDA device; every step of
+the path runs in the CUDA kernels of librec.so.  There is no CPU fallback:
+constructing a Box without a CUDA device or without the built library raises.
+
+    box = Box(n, delta, U, n_packets, precision="mixed")   # uploads the fields
+    box.state_init(z0)                                     # Saha x_e, T = T_gamma
+    for s, (za, zb) in enumerate(zip(zs[:-1], zs[1:])):
+        box.transport(s, za)                               # Ly-alpha packets -> tallies
+        box.step(s, za, zb)                                # x_e, T, U update
+    stats = box.stats()                                    # last rec_stats record
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+REC_OK, REC_EINVAL, REC_ENOMEM, REC_ECUDA, REC_ETIMEOUT, REC_ESTATE = range(6)
+PREC = {"fp64": 0, "mixed": 1}
+MIXING = {"tally": 0, "full": 1}
+_lib = None
+
+
+class Params(C.Structure):
+    _fields_ = [("h", C.c_double), ("omega_b_h2", C.c_double), ("omega_c_h2", C.c_double), ("Y_p", C.c_double),
+                ("T_cmb0", C.c_double), ("N_eff", C.c_double), ("L_box_kpc", C.c_double), ("fudge", C.c_double),
+                ("heating", C.c_double), ("seed", C.c_uint64), ("n_sub", C.c_int32), ("precision", C.c_int32),
+                ("mixing", C.c_int32), ("n_quantiles", C.c_int32),
+                ("emission_quantiles", C.POINTER(C.c_double))]
+
+
+class BoxDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("delta", C.c_void_p), ("vel4", C.c_void_p), ("x_e", C.c_void_p),
+                ("T", C.c_void_p), ("tally", C.c_void_p), ("emis", C.c_void_p), ("n_packets", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("emitted", C.c_uint64), ("absorbed", C.c_uint64), ("capped", C.c_uint64),
+                ("crossings", C.c_uint64), ("X_e", C.c_double), ("lambda_", C.c_double), ("C_mix", C.c_double),
+                ("S1s", C.c_double), ("newton_passes", C.c_int32), ("flags", C.c_int32)]
+
+
+class RecError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load (building first if needed) the in-tree CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P, d, i32, u32, vp = C.POINTER, C.c_double, C.c_int32, C.c_uint32, C.c_void_p
+        L.rec_init.argtypes = [P(Params), P(BoxDesc), i32, vp, P(vp)]
+        L.rec_state_init.argtypes = [vp, d]
+        L.rec_refresh.argtypes = [vp, d]
+        L.lya_transport.argtypes = [vp, i32, d, vp]
+        L.rec_step.argtypes = [vp, i32, d, d, vp]
+        L.rec_step_adjoint.argtypes = [vp, i32, d, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, d]
+        L.rec_xe_adjoint.argtypes = [vp, vp, d, vp, vp]
+        L.rec_transport_params.argtypes = [P(Params), i32, d, P(d)]
+        L.rec_objective.argtypes = [P(Params), P(d), P(d), i32, i32, d, P(d), P(d)]
+        L.rec_free.argtypes = [vp]
+        L.rec_free.restype = None
+        L.rec_last_error.argtypes = [vp]
+        L.rec_last_error.restype = C.c_char_p
+        for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_adjoint",
+                  "rec_xe_adjoint", "rec_transport_params", "rec_objective"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def make_params(precision="mixed", mixing="tally", seed=1, n_sub=1, quantiles=None, **cosmo) -> tuple:
+    """rec_params with the Sec. II.C defaults; returns (Params, quantile array kept alive)."""
+    if quantiles is None:
+        from .inputs import doppler_quantiles
+        quantiles = doppler_quantiles()
+    q = np.ascontiguousarray(quantiles, dtype=np.float64)
+    base = dict(h=0.67, omega_b_h2=0.0224, omega_c_h2=0.12, Y_p=0.24, T_cmb0=2.7255, N_eff=3.046, L_box_kpc=24.0,
+                fudge=1.14, heating=0.0)
+    base.update(cosmo)
+    p = Params(**base, seed=seed, n_sub=n_sub, precision=PREC[precision], mixing=MIXING[mixing],
+               n_quantiles=q.size, emission_quantiles=q.ctypes.data_as(C.POINTER(C.c_double)))
+    return p, q
+
+
+def transport_params(n: int, z: float, **kw):
+    """(kappa, cth) as the library computes them (host only)."""
+    p, _q = make_params(**kw)
+    out = (C.c_double * 2)()
+    rc = lib().rec_transport_params(C.byref(p), n, z, out)
+    if rc != REC_OK:
+        raise RecError(lib().rec_last_error(None).decode())
+    return out[0], out[1]
+
+
+def objective(zs, Xe, objective=1, z_star=1100.0, **kw):
+    """(J, dJ/dX_e per node) of an X_e history (host computation in the library)."""
+    p, _q = make_params(**kw)
+    z = np.ascontiguousarray(zs, dtype=np.float64)
+    X = np.ascontiguousarray(Xe, dtype=np.float64)
+    J = C.c_double()
+    dJ = np.zeros(z.size)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    rc = lib().rec_objective(C.byref(p), dp(z), dp(X), z.size, int(objective), float(z_star), C.byref(J), dp(dJ))
+    if rc != REC_OK:
+        raise RecError(lib().rec_last_error(None).decode())
+    return J.value, dJ
+
+
+class Box:
+    """One periodic box and its context.  Fields live in torch CUDA tensors."""
+
+    def __init__(self, n, delta, U, n_packets, precision="mixed", mixing="tally", seed=1, n_sub=1, quantiles=None,
+                 stream=None, n_stats=1, **cosmo):
+        import torch
+        if not torch.cuda.is_available():
+            raise RecError("a CUDA device is required (there is no CPU fallback)")
+        self.torch = torch
+        self.n = int(n)
+        self.n3 = self.n ** 3
+        self.precision = precision
+        self.mixing = mixing
+        fdt = torch.float32 if precision == "mixed" else torch.float64
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream or torch.cuda.current_stream(dev)
+        d = torch.as_tensor(np.asarray(delta).ravel(), dtype=torch.float64)
+        if d.numel() != self.n3:
+            raise RecError("delta must have n^3 cells")
+        u = torch.as_tensor(np.asarray(U).reshape(-1, 3), dtype=torch.float64)
+        v4 = torch.zeros(self.n3, 4, dtype=torch.float64)
+        v4[:, :3] = u
+        with torch.cuda.stream(self.stream):
+            self.delta = d.to(dev, fdt)
+            self.vel4 = v4.to(dev, fdt).contiguous()
+            self.x = torch.zeros(self.n3, dtype=torch.float64, device=dev)
+            self.T = torch.zeros(self.n3, dtype=fdt, device=dev)
+            self.tally = torch.zeros(self.n3, dtype=torch.int32, device=dev)  # read as uint32
+            self.emis = torch.zeros(self.n3, dtype=fdt, device=dev)
+            self._stats = torch.zeros(max(1, int(n_stats)), C.sizeof(Stats), dtype=torch.uint8, device=dev)
+        self.n_packets = int(n_packets)
+        self._params, self._q = make_params(precision, mixing, seed, n_sub, quantiles, **cosmo)
+        desc = BoxDesc(self.n, self.delta.data_ptr(), self.vel4.data_ptr(), self.x.data_ptr(), self.T.data_ptr(),
+                       self.tally.data_ptr(), self.emis.data_ptr(), self.n_packets)
+        ctx = C.c_void_p()
+        self.stream.synchronize()
+        rc = lib().rec_init(C.byref(self._params), C.byref(desc), 1, C.c_void_p(self.stream.cuda_stream),
+                            C.byref(ctx))
+        if rc != REC_OK:
+            raise RecError(f"rec_init: {lib().rec_last_error(None).decode()} (status {rc})")
+        self.ctx = ctx
+
+    # ---- calls -----------------------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != REC_OK:
+            raise RecError(f"{what}: {lib().rec_last_error(self.ctx).decode()} (status {rc})")
+
+    def state_init(self, z):
+        self._check(lib().rec_state_init(self.ctx, z), "rec_state_init")
+
+    def refresh(self, z):
+        self._check(lib().rec_refresh(self.ctx, z), "rec_refresh")
+
+    def ensure_stats(self, n_slots):
+        """Grow the device statistics array to at least n_slots records."""
+        if self._stats.shape[0] < n_slots:
+            self.stream.synchronize()
+            new = self.torch.zeros(n_slots, C.sizeof(Stats), dtype=self.torch.uint8, device=self._stats.device)
+            new[: self._stats.shape[0]] = self._stats
+            self._stats = new
+
+    def _slot(self, slot):
+        return C.c_void_p(self._stats[int(slot)].data_ptr())
+
+    def transport(self, step, z, slot=0):
+        self._check(lib().lya_transport(self.ctx, int(step), z, self._slot(slot)), "lya_transport")
+
+    def step(self, step, z_from, z_to, slot=0):
+        self._check(lib().rec_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_step")
+
+    def step_adjoint(self, step, z_from, z_to, x_in, T_in, vel4_in, tally_in, xbar, Tbar, Ubar, g_delta, g_a,
+                     Xe_bar_out=0.0):
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._check(lib().rec_step_adjoint(self.ctx, int(step), z_from, z_to, ptr(x_in), ptr(T_in), ptr(vel4_in),
+                                           ptr(tally_in), ptr(xbar), ptr(Tbar), ptr(Ubar), ptr(g_delta), ptr(g_a),
+                                           float(Xe_bar_out)), "rec_step_adjoint")
+
+    def xe_adjoint(self, x, Xe_bar, xbar, g_delta):
+        self._check(lib().rec_xe_adjoint(self.ctx, C.c_void_p(x.data_ptr()), float(Xe_bar),
+                                         C.c_void_p(xbar.data_ptr()), C.c_void_p(g_delta.data_ptr())),
+                    "rec_xe_adjoint")
+
+    # ---- host views (synchronising) -------------------------------------------------------
+    def stats(self, slot=0) -> dict:
+        return self.stats_all()[int(slot)]
+
+    def stats_all(self) -> list:
+        self.stream.synchronize()
+        raw = self._stats.cpu().numpy()
+        out = []
+        for row in raw:
+            s = Stats.from_buffer_copy(row.tobytes())
+            out.append(dict(emitted=s.emitted, absorbed=s.absorbed, capped=s.capped, crossings=s.crossings,
+                            X_e=s.X_e, lam=s.lambda_, C=s.C_mix, S1s=s.S1s, newton_passes=s.newton_passes,
+                            flags=s.flags))
+        return out
+
+    def tally_np(self) -> np.ndarray:
+        self.stream.synchronize()
+        return self.tally.cpu().numpy().view(np.uint32)
+
+    def host(self, name) -> np.ndarray:
+        self.stream.synchronize()
+        return getattr(self, name).cpu().numpy()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().rec_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,123 @@
+"""GPU rec_step vs the oracle, element by element, on the same seeded inputs:
+x_e and T within 1e-9 relative for the FP64 form and 1e-4 for the mixed form
+(the tolerances of the method's specification), in full-mixing and tally
+modes, on ragged boxes, over multi-step trajectories, at 256^3 and on the
+degenerate cases."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import new_box, oracle_fields, set_state
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "mixed": 1e-4}
+
+
+def _state(cosmo, d, z, rng, scale=0.97):
+    x = O.saha_xe(cosmo, z, d) * scale
+    T = O.background(cosmo, z)["Tg"] * (1.0 + 0.01 * rng.standard_normal(d.size))
+    return x, T
+
+
+def _check_step(cosmo, box, x0, T0, tally, z_from, z_to):
+    n = box.n
+    set_state(box, x0, T0, tally=tally)
+    T_in = box.host("T").astype(np.float64)  # the bytes the GPU starts from
+    d, U, v4 = oracle_fields(box)
+    box.refresh(z_from)
+    box.step(0, z_from, z_to)
+    st = box.stats()
+    xg, Tg = box.host("x"), box.host("T").astype(np.float64)
+    Ug = box.host("vel4")[:, :3].astype(np.float64)
+    eg = box.host("emis").astype(np.float64)
+    x1, T1, U1, e1, so = O.rec_step(cosmo, n, z_from, z_to, d, x0, T_in, U=U, tally=tally, mixing=box.mixing)
+    tol = TOL[box.precision]
+    np.testing.assert_allclose(xg, x1, rtol=tol, atol=0)
+    np.testing.assert_allclose(Tg, T1, rtol=tol, atol=0)
+    np.testing.assert_allclose(Ug, U1, rtol=tol, atol=1e-12)
+    np.testing.assert_allclose(eg, e1, rtol=max(tol, 1e-6) * (3 if box.precision == "mixed" else 1), atol=0)
+    assert st["X_e"] == pytest.approx(so["Xe"], rel=tol)
+    assert st["lam"] == pytest.approx(so["lam"], rel=max(tol, 1e-9) * 10)
+    assert st["C"] == pytest.approx(so["C"], rel=tol)
+    assert st["flags"] & 1 == 0
+    if box.mixing == "tally":
+        assert box.tally_np().sum() == 0  # consumed
+    return st
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mixing", ["full", "tally"])
+@pytest.mark.parametrize("n", [13, 32])
+@pytest.mark.parametrize("z_from,z_to", [(1600.0, 1590.0), (1250.0, 1240.0), (900.0, 895.0)])
+def test_single_step_matches_oracle(cosmo, precision, mixing, n, z_from, z_to):
+    box = new_box(n, precision, mixing)
+    rng = np.random.default_rng(n)
+    d, _, _ = oracle_fields(box)
+    x0, T0 = _state(cosmo, d, z_from, rng)
+    tally = rng.poisson(20 * d ** 1.5).astype(np.uint32)
+    _check_step(cosmo, box, x0, T0, tally, z_from, z_to)
+    box.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_mixing_trajectory_matches_oracle(cosmo, precision):
+    """30 chained steps 1600 -> 900 starting from the GPU's own Saha state;
+    the oracle starts from its own Saha state (no GPU data enters the oracle)."""
+    from paper_2312_11448_gb300.inputs import z_schedule
+    n = 16
+    box = new_box(n, precision, "full", sigma=1.0)
+    zs = z_schedule(1600.0, 900.0, 30)
+    d, U, _ = oracle_fields(box)
+    box.state_init(zs[0])
+    x = O.saha_xe(cosmo, zs[0], d)
+    T = np.full(n ** 3, O.background(cosmo, zs[0])["Tg"])
+    np.testing.assert_allclose(box.host("x"), x, rtol=1e-12)
+    tol = TOL[precision]
+    for s in range(30):
+        box.step(s, zs[s], zs[s + 1])
+        x, T, U, _, so = O.rec_step(cosmo, n, zs[s], zs[s + 1], d, x, T, U=U, mixing="full")
+        np.testing.assert_allclose(box.host("x"), x, rtol=tol)
+        np.testing.assert_allclose(box.host("T").astype(np.float64), T, rtol=tol)
+        assert box.stats()["X_e"] == pytest.approx(so["Xe"], rel=tol)
+    box.close()
+
+
+def test_one_cell_box(cosmo):
+    box = new_box(1, "fp64", "full")
+    rng = np.random.default_rng(0)
+    d, _, _ = oracle_fields(box)
+    x0, T0 = _state(cosmo, d, 1300.0, rng)
+    _check_step(cosmo, box, x0, T0, np.zeros(1, np.uint32), 1300.0, 1290.0)
+    box.close()
+
+
+def test_substeps_match_oracle(cosmo):
+    from gpu_helpers import new_box as nb
+    box = nb(12, "fp64", "tally", n_sub=4)
+    rng = np.random.default_rng(5)
+    d, U, _ = oracle_fields(box)
+    x0, T0 = _state(cosmo, d, 1150.0, rng)
+    tally = rng.poisson(10 * d).astype(np.uint32)
+    set_state(box, x0, T0, tally=tally)
+    box.refresh(1150.0)
+    box.step(0, 1150.0, 1120.0)
+    x1, T1, _, _, _ = O.rec_step(cosmo, 12, 1150.0, 1120.0, d, x0, T0, U=U, tally=tally, mixing="tally", n_sub=4)
+    np.testing.assert_allclose(box.host("x"), x1, rtol=1e-9)
+    np.testing.assert_allclose(box.host("T"), T1, rtol=1e-9)
+    box.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_256_cubed_step(cosmo, precision):
+    """One tally-mode step of the 256^3 benchmark box, all cells against the oracle."""
+    n = 256
+    box = new_box(n, precision, "tally", n_packets=100_000_000, sigma=0.8)
+    rng = np.random.default_rng(11)
+    d, _, _ = oracle_fields(box)
+    x0, T0 = _state(cosmo, d, 1100.0, rng, scale=1.0)
+    x0 = np.minimum(x0, 0.2)
+    tally = rng.poisson(6.0 * d * d / (d * d).mean()).astype(np.uint32)
+    _check_step(cosmo, box, x0, T0, tally, 1100.0, 1097.0)
+    box.close()
