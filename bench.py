@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the recombination hot path on GB300.
+
+Workload: one periodic (24 kpc)^3 box of 256^3 cells (log-normal density,
+sigma_lnrho = 0.8, k^2 spectrum; Gaussian peculiar velocities, sigma_v =
+1 km/s), 1e8 Ly-alpha packets per step, the 400-step schedule z = 1800 -> 600.
+A step is one pass of the whole hot path: packet allocation, transport
+(lya_transport) and the per-cell update (rec_step, tally mode).  The state is
+advanced untimed to step 170 (z ~ 1140, mid-recombination), then W warm-up
+steps and K timed steps run; inputs (0.7-1.2 GB of fields) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+Prints one JSON line: cell-steps/s of the mixed form (value) with packets/s,
+the plain FP64 form beside it, the HBM roofline of the dominant kernel
+(packet march), the oracle timed on the host cores, an end-to-end number
+through the public API with host buffers, clocks and the kernel count.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own box (different seed): weak scaling, no
+data-path collective; the timing is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s & Lyα packets/s at 256^3: mixed vs FP64 form, % HBM roofline"
+N_SIDE, N_PACKETS, N_STEPS, Z0, Z1 = 256, 100_000_000, 400, 1800.0, 600.0
+S0 = 170  # first warm-up step (z ~ 1140)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--packets", type=int, default=N_PACKETS)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--prep", type=int, default=S0, help="untimed steps before the warm-up (profiling: 0)")
+    return ap.parse_args()
+
+
+def workload(n, packets):
+    from paper_2312_11448_gb300.inputs import BoxConfig, make_box, z_schedule
+    cfg = BoxConfig("box256", n, 0.8, 1.0, packets, N_STEPS, Z0, Z1, None, "mixed")
+    return cfg, z_schedule(Z0, Z1, N_STEPS)
+
+
+def describe(cfg, form):
+    return (f"{cfg.n}^3 periodic box (24 kpc), sigma_lnrho={cfg.sigma_lnrho}, sigma_v={cfg.sigma_v} km/s, "
+            f"{cfg.n_packets:.0e} Lya packets/step, tally mixing, {form} form, steps {S0}+ of {N_STEPS} "
+            f"(z {Z0:.0f}->{Z1:.0f})")
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples every 200 ms in the background."""
+
+    def __init__(self, gpu_index):
+        self.path = os.path.join("/tmp", f"rec_bench_clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms",
+                                       "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        self.windows = []
+
+    def mark(self):
+        return time.time()
+
+    def window(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: above half the peak observed power
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples_under_load": len(load), "power_w_max": pmax}
+
+
+# ------------------------------------------------------------------------------ GPU arm
+_FIELDS = {}
+
+
+def fields_of(cfg, seed):
+    from paper_2312_11448_gb300.inputs import make_box as fields
+    if (cfg, seed) not in _FIELDS:
+        _FIELDS[(cfg, seed)] = fields(cfg, seed=seed)
+    return _FIELDS[(cfg, seed)]
+
+
+def make_box(cfg, precision, seed):
+    from paper_2312_11448_gb300 import rec
+    delta, U = fields_of(cfg, seed)
+    return rec.Box(cfg.n, delta, U, cfg.n_packets, precision=precision, mixing="tally", seed=seed), delta, U
+
+
+def advance(box, zs, s_from, s_to):
+    for s in range(s_from, s_to):
+        box.transport(s, zs[s])
+        box.step(s, zs[s], zs[s + 1])
+
+
+def algorithmic_bytes(precision, n3, emitted, queued, crossings, newton_passes):
+    """Algorithmic bytes (each datum counted once per use) of the kernel groups.
+    emit:  per packet its packet-prefix entry, home temperature and velocity;
+           a tally increment if resonant at home, else a queue entry written.
+    march: per queued packet its queue entry and tally increment, one velocity
+           per cell visited after the home cell (one per face crossing).
+    rec_step: per Newton pass delta, x_e, T, tally; final pass reads delta,
+           x_e, T, tally, velocity and writes x_e, T, velocity, emission, tally."""
+    if precision == "mixed":
+        v, t, d, e, qe = 16, 4, 4, 4, 32
+    else:
+        v, t, d, e, qe = 32, 8, 8, 8, 64
+    home = emitted - queued
+    emit = emitted * (4 + t + v) + home * 4 + queued * qe
+    march = queued * (qe + 4) + crossings * v
+    pass_b = d + 8 + t + 4
+    final_b = (d + 8 + t + 4 + v) + (8 + t + v + e + 4)
+    step = n3 * (pass_b * newton_passes + final_b)
+    alloc = n3 * (3 * e + 4)
+    return dict(emit=emit, march=march, rec_step=step, alloc=alloc)
+
+
+def time_form(cfg, zs, precision, W, K, seed, dist, clocks, prep=S0):
+    import torch
+    box, delta, U = make_box(cfg, precision, seed)
+    box.state_init(zs[0])
+    advance(box, zs, 0, prep)
+    s_timed = prep + W
+    advance(box, zs, prep, s_timed)
+    box.ensure_stats(K)
+    box.timing(True)
+    stream = box.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = clocks.mark()
+    e0.record(stream)
+    for k in range(K):
+        s = s_timed + k
+        box.transport(s, zs[s], slot=k)
+        box.step(s, zs[s], zs[s + 1], slot=k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.window(t0, clocks.mark())
+    ms = e0.elapsed_time(e1)
+    kt = box.kernel_times()
+    box.timing(False)
+    st = box.stats_all()[:K]
+    emitted = sum(r["emitted"] for r in st) / K
+    queued = sum(r["queued"] for r in st) / K
+    crossings = sum(r["crossings"] for r in st) / K
+    passes = sum(r["newton_passes"] for r in st) / K
+    flags = 0
+    for r in st:
+        flags |= r["flags"]
+    ab = algorithmic_bytes(precision, box.n3, emitted, queued, crossings, passes)
+    out = dict(ms=ms, kt=kt, emitted=emitted, queued=queued, crossings=crossings, passes=passes, flags=flags, ab=ab,
+               Xe=st[-1]["X_e"], box=box, delta=delta, U=U)
+    return out
+
+
+def time_e2e(cfg, zs, res, K):
+    """Same step through the public API with host buffers: per step the fields
+    (delta, velocity) come from pinned host memory and x_e, T go back."""
+    import torch
+    box = res["box"]
+    stream = box.stream
+    h_delta = box.delta.cpu().pin_memory()
+    h_vel = box.vel4.cpu().pin_memory()
+    h_x = torch.empty_like(box.x, device="cpu").pin_memory()
+    h_T = torch.empty_like(box.T, device="cpu").pin_memory()
+    s_base = S0 + 3 + K  # continue after the timed window (any in-range steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            s = min(s_base + k, N_STEPS - 1)
+            box.delta.copy_(h_delta, non_blocking=True)
+            box.vel4.copy_(h_vel, non_blocking=True)
+            box.transport(s, zs[s])
+            box.step(s, zs[s], zs[s + 1])
+            h_x.copy_(box.x, non_blocking=True)
+            h_T.copy_(box.T, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h2d = h_delta.numel() * h_delta.element_size() + h_vel.numel() * h_vel.element_size()
+    d2h = h_x.numel() * h_x.element_size() + h_T.numel() * h_T.element_size()
+    return ms, h2d, d2h
+
+
+# ------------------------------------------------------------------------ oracle (CPU)
+def oracle_sample(cfg, zs, sample_packets):
+    """The oracle as it stands on one host core: one rec_step over every cell and
+    the transport of `sample_packets` packets of the step; returns seconds."""
+    import oracle as O
+    from paper_2312_11448_gb300.inputs import doppler_quantiles, pack_vel4
+    cp = O.default_cosmo()
+    delta, U = fields_of(cfg, 1)
+    z = zs[S0]
+    x = O.saha_xe(cp, z, delta)
+    T = np.full(delta.size, O.background(cp, z)["Tg"])
+    emis = O.rates(cp, z, T[0])["alpha"] * (O.background(cp, z)["nH"] * delta * x) ** 2
+    v4 = pack_vel4(U, np.float32)
+    t0 = time.perf_counter()
+    tally, cnt, _ = O.transport(cp, cfg.n, z, 1, S0, sample_packets, emis.astype(np.float32), v4,
+                                T.astype(np.float32), doppler_quantiles().astype(np.float32), precision="f32")
+    t_tr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.rec_step(cp, cfg.n, zs[S0], zs[S0 + 1], delta, x, T, U=U, tally=tally, mixing="tally")
+    t_st = time.perf_counter() - t0
+    return t_tr, t_st
+
+
+def cpu_baseline(cfg, zs, sample_packets=4_000_000):
+    sample_packets = min(sample_packets, cfg.n_packets)
+    t_tr, t_st = oracle_sample(cfg, zs, sample_packets)
+    t_step = t_st + t_tr * (cfg.n_packets / sample_packets)
+    return {"value": cfg.n ** 3 / t_step, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "packets_per_s": sample_packets / t_tr,
+            "sample": (f"one oracle rec_step over all {cfg.n}^3 cells ({t_st:.2f} s) + oracle transport of "
+                       f"{sample_packets:.0e} of the {cfg.n_packets:.0e} packets ({t_tr:.2f} s), transport time "
+                       f"scaled linearly to the full packet count; single-threaded, {os.cpu_count()} host cores "
+                       f"present ({platform_name()})")}
+
+
+def platform_name():
+    import platform
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return f"{platform.machine()} {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(group):
+    """dram bytes per launch of a kernel from its committed ncu summary
+    (profiles/<kernel>_256.md), valid only while the kernel source is unchanged
+    (its hash is recorded beside the figure)."""
+    import hashlib
+    files = {"march": ("k_march_256.md", "rec_transport.cu"), "emit": ("k_emit_256.md", "rec_transport.cu"),
+             "rec_step": ("rec_step_passes_256.md", "rec_step.cu")}
+    if group not in files:
+        return None
+    f = os.path.join(ROOT, "profiles", files[group][0])
+    src = os.path.join(ROOT, "paper_2312_11448_gb300", "csrc", files[group][1])
+    if not os.path.exists(f):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(f):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256_16")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != h:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------- arms
+def run_ours(args):
+    import torch
+    rank, world, local = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(
+        os.environ.get("LOCAL_RANK", 0))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    cfg, zs = workload(args.n, args.packets)
+    K, W = args.steps, max(3, args.warmup)
+    clocks = Clocks(local)
+    mixed = time_form(cfg, zs, "mixed", W, K, seed=1 + rank, dist=dist, clocks=clocks, prep=args.prep)
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = time_form(cfg, zs, "fp64", W, max(5, K // 3), seed=1 + rank, dist=dist, clocks=clocks,
+                         prep=args.prep)
+    e2e = None if args.no_e2e else time_e2e(cfg, zs, mixed, K)
+    clk = clocks.summary()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_mixed = max_over_ranks(mixed["ms"])
+    ms_fp64 = max_over_ranks(fp64["ms"]) if fp64 else None
+    ms_e2e = max_over_ranks(e2e[0]) if e2e else None
+    n3 = cfg.n ** 3
+    K64 = max(5, K // 3)
+    if rank != 0:
+        dist.barrier() if dist else None
+        return
+    value = world * n3 * K / (ms_mixed * 1e-3)
+    peak, peak_kind = measured_peaks()
+    groups = {g: v for g, v in mixed["kt"].items() if v[1]}
+    dominant = max(("emit", "march", "rec_step", "alloc"), key=lambda g: groups.get(g, (0, 0))[0])
+    names = {"emit": "k_emit<float> (packet emission + home-cell test)",
+             "march": "k_march<float> (march of queued packets)",
+             "rec_step": "rec_step passes (k_newton<1> + k_final<1>)", "alloc": "allocation (3 kernels)"}
+
+    def roof(g):
+        ms_g = groups[g][0] / K
+        ach = mixed["ab"][g] / (ms_g * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": names[g], "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
+                "algorithmic_bytes_per_launch": mixed["ab"][g], "avg_launch_ms": ms_g}
+
+    launches = sum(v[1] for v in mixed["kt"].values())
+    out = {
+        "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_mixed / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: f32 transport + f32 per-cell coefficients, f64 x_e state/residual/sums", "data": "synthetic",
+        "config": {"workload": describe(cfg, "mixed"), "n": cfg.n, "packets_per_step": cfg.n_packets,
+                   "parallelism": f"{world} independent boxes (one per GPU)" if world > 1 else "single GPU",
+                   "l2": "working set 0.74 GB (mixed) / 1.2 GB (fp64) > 129 MB L2, no flush needed"},
+        "packets_per_s": world * mixed["emitted"] * K / (ms_mixed * 1e-3),
+        "kernel_ms_per_step": {g: v[0] / K for g, v in mixed["kt"].items() if v[1]},
+        "crossings_per_packet": mixed["crossings"] / max(mixed["emitted"], 1),
+        "newton_passes": mixed["passes"], "X_e": mixed["Xe"], "flags": mixed["flags"],
+        "roofline": dict(roof(dominant), traffic=profiled_traffic(dominant)),
+        "roofline_other": {g: roof(g) for g in ("emit", "march", "rec_step", "alloc") if g in groups and g != dominant},
+        "queued_fraction": mixed["queued"] / max(mixed["emitted"], 1),
+        "gpu_launches": launches,
+    }
+    if fp64:
+        out["fp64_form"] = {"value": world * n3 * K64 / (ms_fp64 * 1e-3), "unit": "cell-steps/s",
+                            "ms_per_step": ms_fp64 / K64, "steps": K64,
+                            "packets_per_s": world * fp64["emitted"] * K64 / (ms_fp64 * 1e-3),
+                            "kernel_ms_per_step": {g: v[0] / K64 for g, v in fp64["kt"].items() if v[1]},
+                            "mixed_over_fp64": (ms_fp64 / K64) / (ms_mixed / K)}
+    if e2e:
+        out["e2e"] = {"value": world * n3 * K / (ms_e2e * 1e-3), "unit": "cell-steps/s", "h2d_bytes_per_step": e2e[1],
+                      "d2h_bytes_per_step": e2e[2],
+                      "api": "rec.Box: H2D of delta and velocity, lya_transport, rec_step, D2H of x_e and T per step"}
+    out["clocks"] = clk
+    if world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(cfg, zs)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+
+
+def run_reference(args):
+    """The oracle (CPU, single-threaded) on the same workload and metric; each
+    step is a bounded sample: one rec_step over every cell plus the transport
+    of a fraction of the packets, scaled to the full packet count."""
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if rank != 0:
+        return
+    cfg, zs = workload(args.n, args.packets)
+    sample = min(2_000_000, cfg.n_packets)
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        oracle_sample(cfg, zs, sample)
+    tot = 0.0
+    for _ in range(K):
+        t_tr, t_st = oracle_sample(cfg, zs, sample)
+        tot += t_st + t_tr * (cfg.n_packets / sample)
+    ms = tot / K * 1e3
+    value = cfg.n ** 3 / (ms * 1e-3)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": 0, "steps": K,
+           "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (oracle; binary32 transport arithmetic)", "data": "synthetic",
+           "config": {"workload": describe(cfg, "oracle"), "n": cfg.n, "packets_per_step": cfg.n_packets},
+           "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                            "sample": f"per step: oracle rec_step over all cells + transport of {sample:.0e} packets "
+                                      f"scaled to {cfg.n_packets:.0e}; {platform_name()}"},
+           "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -101,6 +101,7 @@ typedef struct {
 /* Device-side statistics record (caller-owned device memory). */
 typedef struct {
   uint64_t emitted, absorbed, capped, crossings; /* transport counters of the last call */
+  uint64_t queued;  /* packets that left their home cell (marched by the second kernel) */
   double X_e;     /* <rho_b x_e>/<rho_b> after the last rec_step (Sec. II.A) */
   double lambda;  /* <alpha_e n_e^2>/<n_1s> at the end state, 1/s */
   double C_mix;   /* Peebles factor with R_alpha -> R_alpha^mix (Eq. Cfactor, Sec. IV.B) */
@@ -173,6 +174,22 @@ rec_status rec_objective(const rec_params* params, const double* zs, const doubl
  * v_th = sqrt(2 k T / m_H) of Appendix A is sqrt(T cth) cells.
  * Errors: REC_EINVAL. */
 rec_status rec_transport_params(const rec_params* params, int32_t n, double z, double* out);
+
+/* Kernel timing, a measurement aid.  rec_timing(ctx, 1) clears the counters and
+ * starts recording CUDA events on the context stream around each kernel group;
+ * rec_timing(ctx, 0) stops.  rec_kernel_times synchronises the stream and
+ * writes, per group, the summed device time in ms and the number of kernels
+ * launched since the last clear (arrays of REC_T_COUNT).  Groups:
+ *   0  packet allocation (3 kernels per lya_transport)
+ *   1  packet emission and home-cell test (1 kernel)
+ *   2  march of the queued packets (1 kernel)
+ *   3  transport bookkeeping (1 kernel)
+ *   4  rec_step passes (begin, Newton, final per substep)
+ *   5  rec_step_adjoint passes
+ *   6  rec_state_init / rec_refresh / rec_xe_adjoint */
+#define REC_T_COUNT 7
+rec_status rec_timing(rec_ctx* ctx, int32_t enable);
+rec_status rec_kernel_times(rec_ctx* ctx, double* ms_out, int64_t* launches_out);
 
 /* Release the context and its scratch (NULL-safe).  Synchronises the stream. */
 void rec_free(rec_ctx* ctx);

@@ -290,6 +290,7 @@ cudaError_t launch_rec_step_adjoint(rec_ctx* c, double z_from, double z_to, cons
   a.sc = c->sc_adj;
   a.part = c->part;
   a.k = k;
+  GroupTimer t(c, kTAdj, kNewtonMaxPasses + 5);
   adj::k_adj_prep<<<c->grid, adj::NT, 0, c->stream>>>(a);
   enqueue_newton_passes(c, c->sc_adj, k, x_in, T_in, tally_in);
   adj::k_adj_r1<<<c->grid, adj::NT, 0, c->stream>>>(a);
@@ -300,6 +301,7 @@ cudaError_t launch_rec_step_adjoint(rec_ctx* c, double z_from, double z_to, cons
 
 cudaError_t launch_xe_adjoint(rec_ctx* c, const double* x, double Xe_bar, double* xbar, double* g_delta) {
   const double* delta = (const double*)c->box.delta;
+  GroupTimer t(c, kTOther, 2);
   adj::k_xe_sum<<<c->grid, adj::NT, 0, c->stream>>>(delta, x, c->n3, c->sc_adj, c->part);
   adj::k_xe_apply<<<c->grid, adj::NT, 0, c->stream>>>(delta, x, c->n3, c->sc_adj, Xe_bar, xbar, g_delta);
   return cudaGetLastError();

@@ -79,6 +79,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   c->n3 = (int64_t)b.n * b.n * b.n;
   c->cosmo = rec::make_cosmo(*params);
   c->sc = nullptr; c->sc_adj = nullptr; c->part = nullptr; c->P = nullptr; c->partQ = nullptr; c->quant = nullptr;
+  c->queue = nullptr;
   c->emis_ready = false;
 
   int dev = 0;
@@ -91,6 +92,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   if (c->grid < 1) c->grid = 1;
   c->alloc_blocks = (int)((c->n3 + rec::kAllocChunk - 1) / rec::kAllocChunk);
   c->transport_blocks = c->sm_count * 8;
+  c->march_blocks = c->sm_count * 4;
 
   size_t qbytes = (size_t)params->n_quantiles * (params->precision == REC_PREC_MIXED ? 4 : 8);
   e = cudaMalloc(&c->sc, sizeof(rec::DevScalars));
@@ -99,6 +101,9 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(uint32_t) * (size_t)(c->n3 + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->partQ, sizeof(unsigned long long) * (size_t)c->alloc_blocks);
   if (e == cudaSuccess) e = cudaMalloc(&c->quant, qbytes);
+  // march queue: two float4 (mixed) or double4 (FP64) per packet, worst case all packets
+  size_t qentry = params->precision == REC_PREC_MIXED ? 32 : 64;
+  if (e == cudaSuccess) e = cudaMalloc(&c->queue, qentry * (size_t)std::max<uint64_t>(b.n_packets, 1));
   if (e != cudaSuccess) {
     rec_status r = (e == cudaErrorMemoryAllocation) ? fail(nullptr, REC_ENOMEM, "device allocation failed")
                                                     : cuda_fail(nullptr, e, "cudaMalloc");
@@ -236,15 +241,52 @@ rec_status rec_objective(const rec_params* p, const double* zs, const double* Xe
   return REC_OK;
 }
 
+rec_status rec_timing(rec_ctx* c, int32_t enable) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  if (enable) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rec_timing");
+    for (int g = 0; g < REC_T_COUNT; ++g) {
+      for (auto& pr : c->ev[g]) { c->pool.push_back(pr.first); c->pool.push_back(pr.second); }
+      c->ev[g].clear();
+      c->launches[g] = 0;
+    }
+  }
+  c->timing = enable != 0;
+  return REC_OK;
+}
+
+rec_status rec_kernel_times(rec_ctx* c, double* ms_out, int64_t* launches_out) {
+  if (!c || !ms_out) return fail(c, REC_EINVAL, "bad arguments");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_kernel_times");
+  for (int g = 0; g < REC_T_COUNT; ++g) {
+    double tot = 0.0;
+    for (auto& pr : c->ev[g]) {
+      float ms = 0.0f;
+      e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
+      tot += ms;
+    }
+    ms_out[g] = tot;
+    if (launches_out) launches_out[g] = c->launches[g];
+  }
+  return REC_OK;
+}
+
 void rec_free(rec_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (int g = 0; g < REC_T_COUNT; ++g)
+    for (auto& pr : c->ev[g]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   cudaFree(c->sc);
   cudaFree(c->sc_adj);
   cudaFree(c->part);
   cudaFree(c->P);
   cudaFree(c->partQ);
   cudaFree(c->quant);
+  cudaFree(c->queue);
   delete c;
 }
 

@@ -7,6 +7,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "rec.h"
 
@@ -47,6 +49,7 @@ struct DevScalars {
   unsigned long long tally_total;  // packets absorbed in the current tallies
   unsigned long long sumQ;         // sum of quantised emission weights
   unsigned long long alloc_u;      // systematic-sampling offset in [0, sumQ)
+  unsigned long long qtail;        // packets queued for the march
   uint32_t alloc_counter;
   int32_t emis_valid;
 };
@@ -95,12 +98,46 @@ struct rec_ctx {
   int grid;                  // blocks of the streaming passes
   int alloc_blocks;
   int transport_blocks;
+  int march_blocks;
+  void* queue;               // queued packets of the march (2 x 16|32 B each) [n_packets]
   int sm_count;
   bool emis_ready;
   std::string err;
+  // optional kernel timing (rec_timing / rec_kernel_times)
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[REC_T_COUNT];
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[REC_T_COUNT] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace rec {
+
+enum TimerGroup { kTAlloc = 0, kTEmit = 1, kTMarch = 2, kTEnd = 3, kTStep = 4, kTAdj = 5, kTOther = 6 };
+
+// Scoped timer of one kernel group: records an event pair on the context
+// stream when timing is on and counts the launches of the group.
+struct GroupTimer {
+  rec_ctx* c;
+  int g;
+  cudaEvent_t e0 = nullptr;
+  GroupTimer(rec_ctx* ctx, int group, int n_launches) : c(ctx), g(group) {
+    c->launches[g] += n_launches;
+    if (c->timing) { e0 = take(); cudaEventRecord(e0, c->stream); }
+  }
+  ~GroupTimer() {
+    if (e0) {
+      cudaEvent_t e1 = take();
+      cudaEventRecord(e1, c->stream);
+      c->ev[g].emplace_back(e0, e1);
+    }
+  }
+  cudaEvent_t take() {
+    if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
 
 // rec_cosmo.h
 Cosmo make_cosmo(const rec_params& p);

@@ -431,6 +431,7 @@ void enqueue_newton_passes(rec_ctx* c, DevScalars* sc, const StepCoef& k, const 
 cudaError_t launch_refresh(rec_ctx* c, double z) {
   StepCoef k = step_coef(c->cosmo, c->params, z + 1e-6 * (1.0 + z), z, 0);
   PassArgs a = pass_args(c, k);
+  GroupTimer t(c, kTOther, 1);
   if (c->params.precision == REC_PREC_MIXED) k_refresh<true><<<c->grid, NT, 0, c->stream>>>(a);
   else k_refresh<false><<<c->grid, NT, 0, c->stream>>>(a);
   return cudaGetLastError();
@@ -440,6 +441,7 @@ cudaError_t launch_state_init(rec_ctx* c, double z) {
   StepCoef k = step_coef(c->cosmo, c->params, z + 1e-6 * (1.0 + z), z, 0);
   PassArgs a = pass_args(c, k);
   double S = saha_S(k.Tg);
+  GroupTimer t(c, kTOther, 1);
   if (c->params.precision == REC_PREC_MIXED) k_state_init<true><<<c->grid, NT, 0, c->stream>>>(a, k.nH / S, k.Tg);
   else k_state_init<false><<<c->grid, NT, 0, c->stream>>>(a, k.nH / S, k.Tg);
   cudaError_t e = cudaGetLastError();
@@ -451,6 +453,7 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
   const int ns = c->params.n_sub;
   const bool mixed = c->params.precision == REC_PREC_MIXED;
   double ya = std::log1p(z_from), yb = std::log1p(z_to);
+  GroupTimer t(c, kTStep, ns * (kNewtonMaxPasses + 2));
   for (int s = 0; s < ns; ++s) {
     double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
     double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);

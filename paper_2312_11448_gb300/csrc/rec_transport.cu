@@ -15,9 +15,11 @@
 //                   them and draws the systematic-sampling offset u
 //   k_alloc_prefix  packet prefix P_i = floor((N prefixQ_i + u) / sum Q), exact
 //                   128-bit integer arithmetic
-//   k_transport     one packet per thread: warp-cooperative cell lookup in P,
-//                   Philox draws, emission, Amanatides-Woo march, warp-aggregated
-//                   tally atomics
+//   k_emit          one packet per thread: warp-cooperative cell lookup in P,
+//                   Philox draws, emission, resonance test in the home cell
+//                   (warp-aggregated tally); the others step once and are queued
+//   k_march         persistent warps march the queued packets (Amanatides-Woo),
+//                   refilling idle lanes from the queue; tally atomics
 //   k_transport_end counters to the statistics record
 // The march is written operation by operation with round-to-nearest
 // intrinsics (never contracted into FMA), in binary32 for the mixed form and
@@ -217,6 +219,7 @@ __global__ void __launch_bounds__(AT) k_alloc_sum(const R* emis, int64_t n3, uin
     sc->absorbed = 0;
     sc->capped = 0;
     sc->crossings = 0;
+    sc->qtail = 0;
     sc->alloc_counter = 0;
     if (sumQ == 0 && n_packets > 0) sc->flags |= 4;
   }
@@ -260,6 +263,10 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
 }
 
 // ---- transport ----------------------------------------------------------------------
+// A queued packet: the march state right after it left its home cell.
+//   q0 = {cell bits, tMax_x, tMax_y, tMax_z}, q1 = {n_x, n_y, n_z, u0}
+// The remaining traversal constants (tDelta, steps, kappa n) are recomputed
+// from n with the same operations, so the march continues bit for bit.
 template <class R>
 struct TransportArgs {
   const uint32_t* P;
@@ -273,6 +280,7 @@ struct TransportArgs {
   Stream strm;
   uint32_t* tally;
   DevScalars* sc;
+  typename Vec4<R>::T* queue;  // 2 entries per queued packet
 };
 
 // First index k in [lo, hi] with P[k] > key (P[hi] > key holds).
@@ -285,19 +293,87 @@ __device__ __forceinline__ uint32_t upper_bound(const uint32_t* P, uint32_t lo, 
   return lo;
 }
 
+template <class R> __device__ __forceinline__ R bits_to(uint32_t v);
+template <> __device__ __forceinline__ float bits_to<float>(uint32_t v) { return __uint_as_float(v); }
+template <> __device__ __forceinline__ double bits_to<double>(uint32_t v) { return __longlong_as_double((long long)v); }
+template <class R> __device__ __forceinline__ uint32_t to_bits(R v);
+template <> __device__ __forceinline__ uint32_t to_bits<float>(float v) { return __float_as_uint(v); }
+template <> __device__ __forceinline__ uint32_t to_bits<double>(double v) { return (uint32_t)__double_as_longlong(v); }
+
+// Traversal state of one packet.
 template <class R>
-__global__ void __launch_bounds__(TT) k_transport(TransportArgs<R> a) {
+struct Ray {
+  uint32_t ix, iy, iz, kc;
+  R tMx, tMy, tMz, tDx, tDy, tDz, knx, kny, knz, u0;
+  int sx, sy, sz;
+};
+
+// tDelta and step of one axis from the direction cosine (Amanatides-Woo).
+template <class R>
+__device__ __forceinline__ void axis_setup(R nd, R* tD, int* st) {
   using A = Ar<R>;
-  using V = typename Vec4<R>::T;
+  if (nd > (R)0) { *st = 1; *tD = A::div((R)1, nd); }
+  else if (nd < (R)0) { *st = -1; *tD = A::div((R)1, -nd); }
+  else { *st = 0; *tD = A::inf(); }
+}
+
+// One cell of the march: resonance test in the current cell, then a step
+// across the nearest face (ties x < y < z, periodic wrap).  Returns 1 when
+// absorbed in the current cell, 2 when the crossing cap is hit, 0 otherwise.
+template <class R, class V>
+__device__ __forceinline__ int march_cell(Ray<R>& r, const V& Uc, uint32_t n) {
+  using A = Ar<R>;
+  R dc = A::add(A::add(A::mul(r.knx, Uc.x), A::mul(r.kny, Uc.y)), A::mul(r.knz, Uc.z));
+  int ax;
+  R s_exit;
+  if (r.tMx <= r.tMy && r.tMx <= r.tMz) { ax = 0; s_exit = r.tMx; }
+  else if (r.tMy <= r.tMz) { ax = 1; s_exit = r.tMy; }
+  else { ax = 2; s_exit = r.tMz; }
+  // resonance in this cell at path length u0 - kappa n.U_c: absorb unless beyond the exit
+  if (A::sub(r.u0, dc) <= s_exit) return 1;
+  if (r.kc >= kMaxCrossings) return 2;
+  if (ax == 0) { r.ix = (r.sx > 0) ? (r.ix + 1 == n ? 0 : r.ix + 1) : (r.ix == 0 ? n - 1 : r.ix - 1); r.tMx = A::add(r.tMx, r.tDx); }
+  else if (ax == 1) { r.iy = (r.sy > 0) ? (r.iy + 1 == n ? 0 : r.iy + 1) : (r.iy == 0 ? n - 1 : r.iy - 1); r.tMy = A::add(r.tMy, r.tDy); }
+  else { r.iz = (r.sz > 0) ? (r.iz + 1 == n ? 0 : r.iz + 1) : (r.iz == 0 ? n - 1 : r.iz - 1); r.tMz = A::add(r.tMz, r.tDz); }
+  ++r.kc;
+  return 0;
+}
+
+__device__ __forceinline__ void add_counters(DevScalars* sc, uint64_t ab, uint64_t cap, uint64_t cross) {
   __shared__ unsigned long long s_abs, s_cap, s_cross;
   if (threadIdx.x == 0) { s_abs = 0; s_cap = 0; s_cross = 0; }
   __syncthreads();
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ab += __shfl_down_sync(0xffffffffu, ab, off);
+    cap += __shfl_down_sync(0xffffffffu, cap, off);
+    cross += __shfl_down_sync(0xffffffffu, cross, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_abs, (unsigned long long)ab);
+    atomicAdd(&s_cap, (unsigned long long)cap);
+    atomicAdd(&s_cross, (unsigned long long)cross);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_abs) atomicAdd(&sc->absorbed, s_abs);
+    if (s_cap) atomicAdd(&sc->capped, s_cap);
+    if (s_cross) atomicAdd(&sc->crossings, s_cross);
+  }
+}
+
+// Emission: one packet per thread.  Packets resonant in their home cell are
+// tallied here; the others take their first step and are queued.
+template <class R>
+__global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
+  using A = Ar<R>;
+  using V = typename Vec4<R>::T;
   const int lane = threadIdx.x & 31;
   const uint32_t N = __ldg(a.P + a.n3);  // packets actually allocated
   const uint32_t n = (uint32_t)a.n;
   const uint32_t n3 = (uint32_t)a.n3;
   const R one = (R)1, two = (R)2, zero = (R)0;
-  uint64_t my_abs = 0, my_cap = 0, my_cross = 0;
+  uint64_t my_abs = 0, my_cross = 0;
   const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
   for (uint64_t base = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 32; base < N;
        base += warps_total * 32) {
@@ -323,16 +399,15 @@ __global__ void __launch_bounds__(TT) k_transport(TransportArgs<R> a) {
       cell = upper_bound(a.P, c0 + 32u, n3, p) - 1u;
       Pc = __ldg(a.P + cell);
     }
-    bool done = false;
-    uint32_t kc = 0;
-    uint32_t acell = cell;
+    bool home = false, queued = false;
+    Ray<R> r;
+    R nx = zero, ny = zero, nz = one;
     if (act) {
       const uint32_t j = p - Pc;
       // (1) injection point uniform in the cell, frequency quantile
       R f[3], uq;
       Draws<R>::position(a.strm, cell, j, f, &uq);
       // isotropic direction (Marsaglia 1972)
-      R nx = zero, ny = zero, nz = one;
       for (int t = 0; t < 32; ++t) {
         R ua, ub;
         Draws<R>::pair(a.strm, cell, j, t, &ua, &ub);
@@ -352,70 +427,122 @@ __global__ void __launch_bounds__(TT) k_transport(TransportArgs<R> a) {
       R q0 = __ldg(a.quant + k), q1 = __ldg(a.quant + k + 1);
       R xi = A::add(q0, A::mul(fr, A::sub(q1, q0)));
       R vt = A::sqr(A::mul(__ldg(a.T + cell), a.cth));
-      R knx = A::mul(a.kappa, nx), kny = A::mul(a.kappa, ny), knz = A::mul(a.kappa, nz);
+      r.knx = A::mul(a.kappa, nx); r.kny = A::mul(a.kappa, ny); r.knz = A::mul(a.kappa, nz);
       V Uh = a.vel[cell];
-      R dh = A::add(A::add(A::mul(knx, Uh.x), A::mul(kny, Uh.y)), A::mul(knz, Uh.z));
-      R u0 = A::add(A::mul(xi, vt), dh);
-      // Amanatides-Woo traversal
-      uint32_t ix = cell % n, iy = (cell / n) % n, iz = cell / (n * n);
-      R tMx, tMy, tMz, tDx, tDy, tDz;
-      int sx, sy, sz;
-      if (nx > zero) { sx = 1; tDx = A::div(one, nx); tMx = A::mul(A::sub(one, f[0]), tDx); }
-      else if (nx < zero) { sx = -1; tDx = A::div(one, -nx); tMx = A::mul(f[0], tDx); }
-      else { sx = 0; tDx = A::inf(); tMx = A::inf(); }
-      if (ny > zero) { sy = 1; tDy = A::div(one, ny); tMy = A::mul(A::sub(one, f[1]), tDy); }
-      else if (ny < zero) { sy = -1; tDy = A::div(one, -ny); tMy = A::mul(f[1], tDy); }
-      else { sy = 0; tDy = A::inf(); tMy = A::inf(); }
-      if (nz > zero) { sz = 1; tDz = A::div(one, nz); tMz = A::mul(A::sub(one, f[2]), tDz); }
-      else if (nz < zero) { sz = -1; tDz = A::div(one, -nz); tMz = A::mul(f[2], tDz); }
-      else { sz = 0; tDz = A::inf(); tMz = A::inf(); }
-      uint32_t c = cell;
-      V Uc = Uh;
-      for (;;) {
-        R dc = A::add(A::add(A::mul(knx, Uc.x), A::mul(kny, Uc.y)), A::mul(knz, Uc.z));
-        int ax;
-        R s_exit;
-        if (tMx <= tMy && tMx <= tMz) { ax = 0; s_exit = tMx; }
-        else if (tMy <= tMz) { ax = 1; s_exit = tMy; }
-        else { ax = 2; s_exit = tMz; }
-        // resonance in this cell at path length u0 - kappa n.U_c: absorb if not beyond the exit
-        if (A::sub(u0, dc) <= s_exit) { done = true; break; }
-        if (kc >= kMaxCrossings) break;
-        if (ax == 0) { ix = (sx > 0) ? (ix + 1 == n ? 0 : ix + 1) : (ix == 0 ? n - 1 : ix - 1); tMx = A::add(tMx, tDx); }
-        else if (ax == 1) { iy = (sy > 0) ? (iy + 1 == n ? 0 : iy + 1) : (iy == 0 ? n - 1 : iy - 1); tMy = A::add(tMy, tDy); }
-        else { iz = (sz > 0) ? (iz + 1 == n ? 0 : iz + 1) : (iz == 0 ? n - 1 : iz - 1); tMz = A::add(tMz, tDz); }
-        ++kc;
-        c = (iz * n + iy) * n + ix;
-        Uc = a.vel[c];
-      }
-      acell = c;
-      my_cross += kc;
-      if (done) ++my_abs;
-      else ++my_cap;
+      R dh = A::add(A::add(A::mul(r.knx, Uh.x), A::mul(r.kny, Uh.y)), A::mul(r.knz, Uh.z));
+      r.u0 = A::add(A::mul(xi, vt), dh);
+      r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+      axis_setup<R>(nx, &r.tDx, &r.sx);
+      axis_setup<R>(ny, &r.tDy, &r.sy);
+      axis_setup<R>(nz, &r.tDz, &r.sz);
+      r.tMx = r.sx > 0 ? A::mul(A::sub(one, f[0]), r.tDx) : (r.sx < 0 ? A::mul(f[0], r.tDx) : A::inf());
+      r.tMy = r.sy > 0 ? A::mul(A::sub(one, f[1]), r.tDy) : (r.sy < 0 ? A::mul(f[1], r.tDy) : A::inf());
+      r.tMz = r.sz > 0 ? A::mul(A::sub(one, f[2]), r.tDz) : (r.sz < 0 ? A::mul(f[2], r.tDz) : A::inf());
+      r.kc = 0;
+      int res = march_cell<R>(r, Uh, n);  // home cell (res == 2 impossible with kc = 0)
+      home = res == 1;
+      queued = res == 0;
+      my_cross += r.kc;
+      if (home) ++my_abs;
     }
-    // warp-aggregated tally: one atomic per distinct absorbing cell in the warp
-    const bool absd = act && done;
-    const uint32_t key = absd ? acell : 0xffffffffu;
+    // warp-aggregated tally of the packets resonant at home (mostly one cell per warp)
+    const uint32_t key = home ? cell : 0xffffffffu;
     const unsigned m = __match_any_sync(0xffffffffu, key);
-    if (absd && lane == __ffs(m) - 1) atomicAdd(a.tally + acell, (uint32_t)__popc(m));
+    if (home && lane == __ffs(m) - 1) atomicAdd(a.tally + cell, (uint32_t)__popc(m));
+    // queue the others after their first step
+    const unsigned qm = __ballot_sync(0xffffffffu, queued);
+    if (qm) {
+      unsigned long long qb = 0;
+      if (lane == __ffs(qm) - 1) qb = atomicAdd(&a.sc->qtail, (unsigned long long)__popc(qm));
+      qb = __shfl_sync(0xffffffffu, qb, __ffs(qm) - 1);
+      if (queued) {
+        uint64_t slot = qb + __popc(qm & ((1u << lane) - 1u));
+        uint32_t c1 = (r.iz * n + r.iy) * n + r.ix;
+        V q0v, q1v;
+        q0v.x = bits_to<R>(c1); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
+        q1v.x = nx; q1v.y = ny; q1v.z = nz; q1v.w = r.u0;
+        a.queue[2 * slot] = q0v;
+        a.queue[2 * slot + 1] = q1v;
+      }
+    }
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    my_abs += __shfl_down_sync(0xffffffffu, my_abs, off);
-    my_cap += __shfl_down_sync(0xffffffffu, my_cap, off);
-    my_cross += __shfl_down_sync(0xffffffffu, my_cross, off);
+  add_counters(a.sc, my_abs, 0, my_cross);
+}
+
+// March of the queued packets.  Persistent warps; each warp owns the queue
+// chunks w, w + W, w + 2W, ... (chunks of kChunk packets, so the warps advance
+// through the queue together and the cells they touch stay close in memory)
+// and refills idle lanes from them, so that lanes stay busy whatever the
+// spread of path lengths.
+constexpr int kChunk = 256;
+
+template <class R>
+__global__ void __launch_bounds__(TT, 4) k_march(TransportArgs<R> a) {
+  using A = Ar<R>;
+  using V = typename Vec4<R>::T;
+  const int lane = threadIdx.x & 31;
+  const uint32_t n = (uint32_t)a.n;
+  const uint64_t Q = a.sc->qtail;
+  const uint64_t W = (uint64_t)gridDim.x * (TT / 32);
+  uint64_t chunk = (uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5);
+  uint64_t pos = chunk * kChunk, end = min(pos + (uint64_t)kChunk, Q);
+  bool more = pos < Q;
+  bool active = false;
+  uint32_t cell = 0;
+  Ray<R> r;
+  r.kc = 0;
+  V Uc;
+  uint64_t my_abs = 0, my_cap = 0, my_cross = 0;
+  for (;;) {
+    unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (more && __popc(idle) >= 4) {
+      // refill idle lanes in lane order from the warp's current chunk(s)
+      while (idle && more) {
+        if (pos >= end) {
+          chunk += W;
+          pos = chunk * kChunk;
+          end = min(pos + (uint64_t)kChunk, Q);
+          if (pos >= Q) { more = false; break; }
+        }
+        const uint32_t take = (uint32_t)min((uint64_t)__popc(idle), end - pos);
+        const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
+        if (!active && ((idle >> lane) & 1u) && rank < take) {
+          const uint64_t slot = pos + rank;
+          V q0v = a.queue[2 * slot], q1v = a.queue[2 * slot + 1];
+          cell = to_bits<R>(q0v.x);
+          r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+          r.tMx = q0v.y; r.tMy = q0v.z; r.tMz = q0v.w;
+          r.u0 = q1v.w;
+          axis_setup<R>(q1v.x, &r.tDx, &r.sx);
+          axis_setup<R>(q1v.y, &r.tDy, &r.sy);
+          axis_setup<R>(q1v.z, &r.tDz, &r.sz);
+          r.knx = A::mul(a.kappa, q1v.x); r.kny = A::mul(a.kappa, q1v.y); r.knz = A::mul(a.kappa, q1v.z);
+          r.kc = 1;  // the step out of the home cell
+          Uc = a.vel[cell];
+          active = true;
+        }
+        // lanes taken this round leave the idle set (the lowest `take` idle lanes)
+        unsigned taken = 0, m = idle;
+        for (uint32_t t = 0; t < take; ++t) { unsigned b = m & (0u - m); taken |= b; m ^= b; }
+        idle &= ~taken;
+        pos += take;
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active) {
+      int res = march_cell<R>(r, Uc, n);
+      if (res == 0) {
+        cell = (r.iz * n + r.iy) * n + r.ix;
+        Uc = a.vel[cell];
+      } else {
+        active = false;
+        my_cross += r.kc - 1;  // the first crossing was counted at emission
+        if (res == 1) { atomicAdd(a.tally + cell, 1u); ++my_abs; }
+        else ++my_cap;
+      }
+    }
   }
-  if (lane == 0) {
-    atomicAdd(&s_abs, (unsigned long long)my_abs);
-    atomicAdd(&s_cap, (unsigned long long)my_cap);
-    atomicAdd(&s_cross, (unsigned long long)my_cross);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicAdd(&a.sc->absorbed, s_abs);
-    atomicAdd(&a.sc->capped, s_cap);
-    atomicAdd(&a.sc->crossings, s_cross);
-  }
+  add_counters(a.sc, my_abs, my_cap, my_cross);
 }
 
 __global__ void k_transport_end(DevScalars* sc, rec_stats* st) {
@@ -427,6 +554,7 @@ __global__ void k_transport_end(DevScalars* sc, rec_stats* st) {
     st->absorbed = sc->absorbed;
     st->capped = sc->capped;
     st->crossings = sc->crossings;
+    st->queued = sc->qtail;
     st->flags = sc->flags;
   }
 }
@@ -435,11 +563,14 @@ template <class R>
 cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   const rec_box& b = c->box;
   Stream s{(uint32_t)c->params.seed, (uint32_t)(c->params.seed >> 32) ^ (uint32_t)step, 0u};
-  k_alloc_max<R><<<c->grid, kPassThreads, 0, c->stream>>>((const R*)b.emis, c->n3, c->sc, c->part);
-  k_alloc_sum<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, s, c->sc, c->partQ,
-                                                        c->P);
-  k_alloc_prefix<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, c->sc, c->partQ,
-                                                           c->P);
+  {
+    GroupTimer t(c, kTAlloc, 3);
+    k_alloc_max<R><<<c->grid, kPassThreads, 0, c->stream>>>((const R*)b.emis, c->n3, c->sc, c->part);
+    k_alloc_sum<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, s, c->sc,
+                                                          c->partQ, c->P);
+    k_alloc_prefix<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, c->sc,
+                                                             c->partQ, c->P);
+  }
   double kappa, cth;
   transport_scalars(c->cosmo, b.n, z, &kappa, &cth);
   TransportArgs<R> a;
@@ -455,8 +586,19 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.strm = s;
   a.tally = b.tally;
   a.sc = c->sc;
-  k_transport<R><<<c->transport_blocks, TT, 0, c->stream>>>(a);
-  k_transport_end<<<1, 32, 0, c->stream>>>(c->sc, st);
+  a.queue = (typename Vec4<R>::T*)c->queue;
+  {
+    GroupTimer t(c, kTEmit, 1);
+    k_emit<R><<<c->transport_blocks, TT, 0, c->stream>>>(a);
+  }
+  {
+    GroupTimer t(c, kTMarch, 1);
+    k_march<R><<<c->march_blocks, TT, 0, c->stream>>>(a);
+  }
+  {
+    GroupTimer t(c, kTEnd, 1);
+    k_transport_end<<<1, 32, 0, c->stream>>>(c->sc, st);
+  }
   return cudaGetLastError();
 }
 

@@ -41,7 +41,7 @@ class BoxDesc(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("emitted", C.c_uint64), ("absorbed", C.c_uint64), ("capped", C.c_uint64),
-                ("crossings", C.c_uint64), ("X_e", C.c_double), ("lambda_", C.c_double), ("C_mix", C.c_double),
+                ("crossings", C.c_uint64), ("queued", C.c_uint64), ("X_e", C.c_double), ("lambda_", C.c_double), ("C_mix", C.c_double),
                 ("S1s", C.c_double), ("newton_passes", C.c_int32), ("flags", C.c_int32)]
 
 
@@ -65,12 +65,14 @@ def lib():
         L.rec_xe_adjoint.argtypes = [vp, vp, d, vp, vp]
         L.rec_transport_params.argtypes = [P(Params), i32, d, P(d)]
         L.rec_objective.argtypes = [P(Params), P(d), P(d), i32, i32, d, P(d), P(d)]
+        L.rec_timing.argtypes = [vp, i32]
+        L.rec_kernel_times.argtypes = [vp, P(d), P(C.c_int64)]
         L.rec_free.argtypes = [vp]
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
         L.rec_last_error.restype = C.c_char_p
         for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_adjoint",
-                  "rec_xe_adjoint", "rec_transport_params", "rec_objective"):
+                  "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -196,6 +198,18 @@ class Box:
                                          C.c_void_p(xbar.data_ptr()), C.c_void_p(g_delta.data_ptr())),
                     "rec_xe_adjoint")
 
+    TIMER_GROUPS = ("alloc", "emit", "march", "transport_end", "rec_step", "adjoint", "other")
+
+    def timing(self, enable=True):
+        self._check(lib().rec_timing(self.ctx, 1 if enable else 0), "rec_timing")
+
+    def kernel_times(self) -> dict:
+        """{group: (ms, launches)} since timing(True)."""
+        ms = (C.c_double * 7)()
+        ln = (C.c_int64 * 7)()
+        self._check(lib().rec_kernel_times(self.ctx, ms, ln), "rec_kernel_times")
+        return {g: (ms[i], ln[i]) for i, g in enumerate(self.TIMER_GROUPS)}
+
     # ---- host views (synchronising) -------------------------------------------------------
     def stats(self, slot=0) -> dict:
         return self.stats_all()[int(slot)]
@@ -207,6 +221,7 @@ class Box:
         for row in raw:
             s = Stats.from_buffer_copy(row.tobytes())
             out.append(dict(emitted=s.emitted, absorbed=s.absorbed, capped=s.capped, crossings=s.crossings,
+                            queued=s.queued,
                             X_e=s.X_e, lam=s.lambda_, C=s.C_mix, S1s=s.S1s, newton_passes=s.newton_passes,
                             flags=s.flags))
         return out
