@@ -144,8 +144,9 @@ def algorithmic_bytes(precision, n3, emitted, queued, crossings, newton_passes):
            a tally increment if resonant at home, else a queue entry written.
     march: per queued packet its queue entry and tally increment, one velocity
            per cell visited after the home cell (one per face crossing).
-    rec_step: per Newton pass delta, x_e, T, tally; final pass reads delta,
-           x_e, T, tally, velocity and writes x_e, T, velocity, emission, tally."""
+    rec_step: per Newton pass delta, x_e (mixed: its binary32 (x, 1-x) cache),
+           T, tally; final pass reads delta, x_e (+ cache), T, tally, velocity and
+           writes x_e (+ cache), T, velocity, emission, tally."""
     if precision == "mixed":
         v, t, d, e, qe = 16, 4, 4, 4, 32
     else:
@@ -153,8 +154,12 @@ def algorithmic_bytes(precision, n3, emitted, queued, crossings, newton_passes):
     home = emitted - queued
     emit = emitted * (4 + t + v) + home * 4 + queued * qe
     march = queued * (qe + 4) + crossings * v
-    pass_b = d + 8 + t + 4
-    final_b = (d + 8 + t + 4 + v) + (8 + t + v + e + 4)
+    if precision == "mixed":
+        pass_b = d + 8 + t + 4  # the binary32 (x, 1-x) cache replaces x
+        final_b = (d + 8 + 8 + t + 4 + v) + (8 + 8 + t + v + e + 4)
+    else:
+        pass_b = d + 8 + t + 4
+        final_b = (d + 8 + t + 4 + v) + (8 + t + v + e + 4)
     step = n3 * (pass_b * newton_passes + final_b)
     alloc = n3 * (3 * e + 4)
     return dict(emit=emit, march=march, rec_step=step, alloc=alloc)
@@ -194,6 +199,8 @@ def time_form(cfg, zs, precision, W, K, seed, dist, clocks, prep=S0):
     flags = 0
     for r in st:
         flags |= r["flags"]
+    if flags & 4 or not math.isfinite(st[-1]["X_e"]) or emitted < cfg.n_packets:
+        raise RuntimeError(f"{precision} form: invalid state (flags={flags}, X_e={st[-1]['X_e']}, emitted={emitted})")
     ab = algorithmic_bytes(precision, box.n3, emitted, queued, crossings, passes)
     out = dict(ms=ms, kt=kt, emitted=emitted, queued=queued, crossings=crossings, passes=passes, flags=flags, ab=ab,
                Xe=st[-1]["X_e"], box=box, delta=delta, U=U)

@@ -34,11 +34,11 @@ struct AdjArgs {
   const double* delta;
   const double* x;
   const double* T;
-  const double4* U;
+  const double4_32a* U;
   const uint32_t* tally;
   double* xbar;
   double* Tbar;
-  double4* Ubar;
+  double4_32a* Ubar;
   double* g_delta;
   double* g_a;
   double Xe_bar;
@@ -85,7 +85,7 @@ __device__ __forceinline__ Fwd forward_cell(const StepCoef& k, double d, double 
 __device__ __forceinline__ double xbar_out(const AdjArgs& a, int64_t i, const Fwd& f, double d, double Sd) {
   double xb = a.xbar[i] + a.Xe_bar * d / Sd;
   if (a.Ubar) {
-    double4 ub = a.Ubar[i], u = a.U[i];
+    double4_32a ub = a.Ubar[i], u = a.U[i];
     double E = exp(-(a.k.kd * f.xr + a.k.H) * a.k.dt);
     double dot = (ub.x * u.x + ub.y * u.y + ub.z * u.z) * E;  // Ubar' . U'
     xb += -a.k.kd * a.k.dt * dot;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(NT) k_adj_r2(AdjArgs a) {
     db += a.Xe_bar * (f.xr - Xe1) / Sd;
     if (a.Ubar) {
       double E = exp(-(k.kd * f.xr + k.H) * k.dt);
-      double4 ub = a.Ubar[i];
+      double4_32a ub = a.Ubar[i];
       ub.x *= E; ub.y *= E; ub.z *= E;
       a.Ubar[i] = ub;
     }
@@ -279,11 +279,11 @@ cudaError_t launch_rec_step_adjoint(rec_ctx* c, double z_from, double z_to, cons
   a.delta = (const double*)c->box.delta;
   a.x = x_in;
   a.T = T_in;
-  a.U = (const double4*)vel4_in;
+  a.U = (const double4_32a*)vel4_in;
   a.tally = tally_in;
   a.xbar = xbar;
   a.Tbar = Tbar;
-  a.Ubar = (double4*)Ubar;
+  a.Ubar = (double4_32a*)Ubar;
   a.g_delta = g_delta;
   a.g_a = g_a;
   a.Xe_bar = Xe_bar_out;

@@ -80,6 +80,9 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   c->cosmo = rec::make_cosmo(*params);
   c->sc = nullptr; c->sc_adj = nullptr; c->part = nullptr; c->P = nullptr; c->partQ = nullptr; c->quant = nullptr;
   c->queue = nullptr;
+  c->first = nullptr;
+  c->xy = nullptr;
+  c->bcap = nullptr; c->bfill = nullptr; c->bpre = nullptr;
   c->emis_ready = false;
 
   int dev = 0;
@@ -97,11 +100,20 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   size_t qbytes = (size_t)params->n_quantiles * (params->precision == REC_PREC_MIXED ? 4 : 8);
   e = cudaMalloc(&c->sc, sizeof(rec::DevScalars));
   if (e == cudaSuccess) e = cudaMalloc(&c->sc_adj, sizeof(rec::DevScalars));
-  if (e == cudaSuccess) e = cudaMalloc(&c->part, sizeof(double) * rec::kMaxSums * (size_t)c->grid);
+  // block partials, double-buffered for the cooperative substep
+  if (e == cudaSuccess) e = cudaMalloc(&c->part, 2 * sizeof(double) * rec::kMaxSums * (size_t)c->grid);
   if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(uint32_t) * (size_t)(c->n3 + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->partQ, sizeof(unsigned long long) * (size_t)c->alloc_blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&c->first, sizeof(uint32_t) * (size_t)(b.n_packets / 32 + 2));
+  if (e == cudaSuccess && params->precision == REC_PREC_MIXED) e = cudaMalloc(&c->xy, sizeof(float) * 2 * (size_t)c->n3);
+  {
+    size_t nt = (size_t)((b.n + 31) / 32), nb = nt * nt * nt;  // 32^3 super-tiles of the march queue
+    if (e == cudaSuccess) e = cudaMalloc(&c->bcap, sizeof(unsigned long long) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->bfill, sizeof(unsigned long long) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->bpre, sizeof(unsigned long long) * (nb + 1));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&c->quant, qbytes);
-  // march queue: two float4 (mixed) or double4 (FP64) per packet, worst case all packets
+  // march queue: two float4 (mixed) or double4_32a (FP64) per packet, worst case all packets
   size_t qentry = params->precision == REC_PREC_MIXED ? 32 : 64;
   if (e == cudaSuccess) e = cudaMalloc(&c->queue, qentry * (size_t)std::max<uint64_t>(b.n_packets, 1));
   if (e != cudaSuccess) {
@@ -287,6 +299,11 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->partQ);
   cudaFree(c->quant);
   cudaFree(c->queue);
+  cudaFree(c->first);
+  cudaFree(c->xy);
+  cudaFree(c->bcap);
+  cudaFree(c->bfill);
+  cudaFree(c->bpre);
   delete c;
 }
 

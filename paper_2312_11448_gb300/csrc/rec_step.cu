@@ -22,9 +22,15 @@
 // root, binary64 state x, net-rate residual correction and volume sums).
 
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include <cooperative_groups.h>
 
 #include "rec_internal.cuh"
 #include "rec_reduce.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rec {
 namespace {
@@ -36,6 +42,7 @@ struct PassArgs {
   const void* delta;
   void* vel4;
   double* x;
+  float2* xy;  // mixed form: binary32 (x, 1 - x) of the state
   void* T;
   uint32_t* tally;
   void* emis;
@@ -100,41 +107,55 @@ struct CellF32 {
   float Tn, al, n, A, s, xf, yf;
 };
 
+// Binary32 arithmetic of the mixed form.  The per-cell coefficients only need
+// a few ulp (the form's tolerance is 1e-4), so divisions, square roots and
+// exponentials use the approximate hardware instructions.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return a * rsqrtf(a); }  // a > 0
+__device__ __forceinline__ float fexp2(float a) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
 // Binary32 coefficients; x and y = 1 - x both carried with full relative
-// precision (y from the binary64 state).
-__device__ __forceinline__ CellF32 cell_f32(const CoefF32& f, int mixing, float d, double x, float T, uint32_t tal,
+// precision (the binary32 cache of the binary64 state).
+__device__ __forceinline__ CellF32 cell_f32(const CoefF32& f, int mixing, float d, float2 xy, float T, uint32_t tal,
                                             float wscale) {
   CellF32 c;
-  c.xf = __double2float_rn(x);
-  c.yf = __double2float_rn(1.0 - x);
+  c.xf = xy.x;
+  c.yf = xy.y;
   float opx = f.opf + c.xf;
-  float g = f.kc * c.xf / opx;
-  float hh = f.hq / (d * opx);
-  c.Tn = (T + f.dt * (g * f.Tg + hh)) / (1.0f + f.dt * (f.H2 + g));
+  float inv = fdiv(1.0f, d * opx);  // 1 / (Delta (1 + f_He + x))
+  float g = f.kc * c.xf * d * inv;  // x / (1 + f_He + x)
+  float hh = f.hq * inv;
+  c.Tn = fdiv(T + f.dt * (g * f.Tg + hh), 1.0f + f.dt * (f.H2 + g));
   float lt = __log2f(c.Tn * 1.0e-4f);
-  c.al = f.fa * exp2f(f.pb * lt) / (1.0f + f.pc * exp2f(f.pd * lt));
+  c.al = fdiv(f.fa * fexp2(f.pb * lt), 1.0f + f.pc * fexp2(f.pd * lt));
   c.n = f.nH * d;
   c.A = f.dt * c.al * c.n;
   float w = 1.0f;
   if (mixing == REC_MIX_TALLY && wscale > 0.0f) {
     float n1s_rel = d * c.yf;
-    if (n1s_rel > 0.0f) w = (float)tal * wscale / n1s_rel;
+    if (n1s_rel > 0.0f) w = fdiv((float)tal * wscale, n1s_rel);
   }
   c.s = f.dt * w;
   return c;
 }
 
 // Roots in both forms: x' = 2c/(B + sqrt(D)) and y' = 1 - x' = 2(A + y)/(2A + B + sqrt(D)),
-// D = B^2 + 4Ac; neither subtracts.
+// D = B^2 + 4Ac; neither subtracts.  d x'/dG = s (1 - x') / (2 A x' + B) = s y' / sqrt(D).
+// These feed the Newton sums, whose difference F = S0 - lambda S1 cancels, so
+// they use correctly rounded division and square root.
 __device__ __forceinline__ void root_f32(float A, float s, float G, float x, float y, float* xr, float* yr,
                                          float* dxdG) {
   float sG = s * G;
   float B = 1.0f + sG;
   float cc = x + sG;
-  float sq = sqrtf(B * B + 4.0f * A * cc);
-  *xr = 2.0f * cc / (B + sq);
-  *yr = 2.0f * (A + y) / (2.0f * A + B + sq);
-  if (dxdG) *dxdG = s * (*yr) / (2.0f * A * (*xr) + B);
+  float sq = __fsqrt_rn(B * B + 4.0f * A * cc);
+  *xr = __fdiv_rn(2.0f * cc, B + sq);
+  *yr = __fdiv_rn(2.0f * (A + y), 2.0f * A + B + sq);
+  if (dxdG) *dxdG = __fdiv_rn(s * (*yr), sq);
 }
 
 // -------------------------------------------------------------- kernels
@@ -148,7 +169,8 @@ __global__ void k_substep_begin(DevScalars* sc, StepCoef k, double n3) {
   sc->omC = 1.0 - C;
   sc->G0 = C * k.beta * k.ea;
   double guess = sc->lam_state;
-  if (sc->lam_prev > 0.0 && sc->lam_state > 0.0) guess = sc->lam_state * (sc->lam_state / sc->lam_prev);
+  if (sc->lam_prev > 0.0 && sc->lam_state > 0.0)  // extrapolate the last substep's change (at most 2x)
+    guess = sc->lam_state * fmin(2.0, fmax(0.5, sc->lam_state / sc->lam_prev));
   if (!(guess > 0.0)) guess = 1e-30;
   sc->lam = guess;
   sc->conv = 0;
@@ -166,24 +188,22 @@ __device__ void newton_update(DevScalars* sc, double S0, double S1, double S2, d
   double lnew = lam - step;
   if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
   double rel = fabs(step) / lam;
+  const double prev = sc->passes > 0 ? sc->last_step : HUGE_VAL;
   sc->lam = lnew;
   sc->passes += 1;
   sc->last_step = rel;
-  // quadratic convergence: a step below tol leaves an error of order tol^2 in lnew
-  if (rel <= tol && Fp < 0.0) sc->conv = 1;
+  // quadratic convergence: a step below tol leaves an error of order tol^2 in lnew;
+  // a small step that no longer shrinks is the rounding floor of F
+  if (Fp < 0.0 && (rel <= tol || (rel <= 1e-3 && rel >= 0.5 * prev))) sc->conv = 1;
   else if (sc->passes >= kNewtonMaxPasses) sc->flags |= 1;
 }
 
+// Per-block partial sums of one Newton evaluation at lambda (result in thread 0):
+// v0 = sum alpha n^2 x'^2, v1 = sum n (1 - x'), v2 = sum (2 alpha n^2 x' + lambda n) dx'/dG.
 template <bool MIXED>
-__global__ void __launch_bounds__(NT) k_newton(PassArgs a) {
-  DevScalars* sc = a.sc;
-  if (ld_flag(&sc->conv)) return;
-  const double lam = sc->lam;
-  const double G = sc->omC * lam + sc->G0;
-  const double tot = (double)sc->tally_total;
-  const double S1s = sc->S1s;
+__device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam, double G, double tot, double S1s,
+                                                  double (&v)[3]) {
   const int64_t stride = (int64_t)gridDim.x * NT;
-  double v[3];
   if (!MIXED) {
     v[0] = v[1] = v[2] = 0.0;
     const double* delta = (const double*)a.delta;
@@ -208,7 +228,7 @@ __global__ void __launch_bounds__(NT) k_newton(PassArgs a) {
     const float* T = (const float*)a.T;
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
-      CellF32 c = cell_f32(f, a.k.mixing, delta[i], a.x[i], T[i], tal, wscale);
+      CellF32 c = cell_f32(f, a.k.mixing, delta[i], a.xy[i], T[i], tal, wscale);
       float xr, yr, dxdG;
       root_f32(c.A, c.s, Gf, c.xf, c.yf, &xr, &yr, &dxdG);
       float an2 = c.al * c.n * c.n;
@@ -219,43 +239,28 @@ __global__ void __launch_bounds__(NT) k_newton(PassArgs a) {
     v[0] = s0.value(); v[1] = s1.value(); v[2] = s2.value();
   }
   block_sum<3, NT>(v);
-  if (threadIdx.x == 0) {
-    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
-    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
-  }
-  if (!last_block_done(&sc->counter)) return;
-  double S[3];
-  combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
-  if (threadIdx.x == 0) {
-    newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
-    sc->counter = 0;
-  }
 }
 
-// Final pass: new state at the converged lambda, emission weights, sums.
+// Per-block final update at the converged lambda: writes x, T, U, emission
+// weights (zeroes the tallies on the last substep); partial sums (thread 0):
+// v0 = sum delta (1 - x'), v1 = sum delta x', v2 = sum delta.
 template <bool MIXED>
-__global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st) {
-  DevScalars* sc = a.sc;
-  const double lam = sc->lam;
-  const double G = sc->omC * lam + sc->G0;
-  const double tot = (double)sc->tally_total;
-  const double S1s = sc->S1s;
+__device__ __forceinline__ void final_block(const PassArgs& a, double G, double tot, double S1s, double (&v)[3]) {
   const int64_t stride = (int64_t)gridDim.x * NT;
   const bool zero_tally = a.k.last != 0;
-  double v[3];  // sum delta(1-x'), sum delta x', sum delta
   if (!MIXED) {
     v[0] = v[1] = v[2] = 0.0;
     const double* delta = (const double*)a.delta;
     double* T = (double*)a.T;
-    double4* U = (double4*)a.vel4;
+    double4_32a* U = (double4_32a*)a.vel4;
     double* emis = (double*)a.emis;
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
       double d = delta[i], x = a.x[i];
-      uint32_t tal = a.tally[i];
+      uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF64 c = cell_f64(a.k, d, x, T[i], tal, tot, S1s);
       double xr = root_f64(c.A, c.s, G, x, nullptr);
       double damp = exp(-(a.k.kd * xr + a.k.H) * a.k.dt);
-      double4 u = U[i];
+      double4_32a u = U[i];
       u.x *= damp; u.y *= damp; u.z *= damp;
       U[i] = u;
       a.x[i] = xr;
@@ -280,38 +285,73 @@ __global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st) {
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
       float d = delta[i];
       double x = a.x[i];
-      uint32_t tal = a.tally[i];
-      CellF32 c = cell_f32(f, a.k.mixing, d, x, T[i], tal, wscale);
-      float xr, yr, dxdG;
-      root_f32(c.A, c.s, Gf, c.xf, c.yf, &xr, &yr, &dxdG);
-      // binary64 state: the binary32 root (x' or 1 - y', whichever is exact),
-      // then one Newton correction of the backward-Euler residual
-      //   q = (x' - x) + dt (alpha n_H x'^2 - w G (1 - x'))
-      // whose rate difference (recombination minus photo-ionisation) is formed
-      // in binary64.
-      double xn = (yr < 0.5f) ? 1.0 - (double)yr : (double)xr;
-      double sG = (double)c.s * G;
-      double q = (xn - x) + (double)c.A * xn * xn - sG * (1.0 - xn);
-      float Dq = 2.0f * c.A * xr + 1.0f + c.s * Gf;
-      xn -= (double)(__double2float_rn(q) / Dq);
-      float xnf = __double2float_rn(xn);
-      float damp = __expf(-(kdf * xnf + Hf) * dtf);
+      uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
+      CellF32 c = cell_f32(f, a.k.mixing, d, a.xy[i], T[i], tal, wscale);
+      // binary32 roots x' and y' = 1 - x' (both without cancellation) and the
+      // discriminant D = B^2 + 4 A c
+      float sGf = c.s * Gf;
+      float B = 1.0f + sGf;
+      float sq = __fsqrt_rn(B * B + 4.0f * c.A * (c.xf + sGf));
+      float xr = __fdiv_rn(2.0f * (c.xf + sGf), B + sq);
+      float yr = __fdiv_rn(2.0f * (c.A + c.yf), 2.0f * c.A + B + sq);
+      // binary64 state update by its increment: with x' = x + dx the backward-Euler
+      // equation reads A dx^2 + (2Ax + B) dx + r0 = 0, where
+      //   r0 = A x^2 - sG (1 - x)
+      // is dt times the net rate (recombination minus photo-ionisation) at the old
+      // state, formed in binary64 since near Saha equilibrium the two terms cancel.
+      // The discriminant of this equation is D again.
+      double y = 1.0 - x;
+      double r0 = fma((double)c.A, x * x, -((double)c.s * G) * y);
+      float dx = fdiv(-2.0f * __double2float_rn(r0), 2.0f * c.A * c.xf + B + sq);
+      double xn = x + (double)dx;
+      float damp = __expf(-(kdf * xr + Hf) * dtf);
       float4 u = U[i];
       u.x *= damp; u.y *= damp; u.z *= damp;
       U[i] = u;
       a.x[i] = xn;
+      a.xy[i] = make_float2(xr, yr);
       T[i] = c.Tn;
-      float ne = c.n * xnf;
+      float ne = c.n * xr;
       float r = c.al * ne * ne;
       emis[i] = r;
       if (zero_tally) a.tally[i] = 0u;
-      s0.add(d * __double2float_rn(1.0 - xn));
-      s1.add(d * xnf);
+      s0.add(d * yr);
+      s1.add(d * xr);
       s2.add(d);
     }
     v[0] = s0.value(); v[1] = s1.value(); v[2] = s2.value();
   }
   block_sum<3, NT>(v);
+}
+
+// End-of-substep bookkeeping on the device scalars (one thread).
+__device__ __forceinline__ void finish_substep(DevScalars* sc, const StepCoef& k, const double (&S)[3], double lam,
+                                               rec_stats* st) {
+  sc->S1s = S[0];
+  sc->Sdx = S[1];
+  sc->Sd = S[2];
+  sc->lam_prev = sc->lam_state;
+  sc->lam_state = lam;
+  if (k.last) sc->tally_total = 0ull;
+  sc->emis_valid = 1;
+  sc->counter = 0;
+  if (st) {
+    st->X_e = S[1] / S[2];
+    st->lambda = lam;
+    st->C_mix = sc->C;
+    st->S1s = S[0];
+    st->newton_passes = sc->passes;
+    st->flags = sc->flags;
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_newton(PassArgs a) {
+  DevScalars* sc = a.sc;
+  if (ld_flag(&sc->conv)) return;
+  const double lam = sc->lam;
+  double v[3];
+  newton_block_sums<MIXED>(a, lam, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, v);
   if (threadIdx.x == 0) {
     double* p = a.part + (size_t)blockIdx.x * kMaxSums;
     p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
@@ -320,22 +360,102 @@ __global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st) {
   double S[3];
   combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
   if (threadIdx.x == 0) {
-    sc->S1s = S[0];
-    sc->Sdx = S[1];
-    sc->Sd = S[2];
-    sc->lam_prev = sc->lam_state;
-    sc->lam_state = lam;
-    if (zero_tally) sc->tally_total = 0ull;
-    sc->emis_valid = 1;
+    newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
     sc->counter = 0;
-    if (st) {
-      st->X_e = S[1] / S[2];
-      st->lambda = lam;
-      st->C_mix = sc->C;
-      st->S1s = S[0];
-      st->newton_passes = sc->passes;
-      st->flags = sc->flags;
+  }
+}
+
+// Final pass: new state at the converged lambda, emission weights, sums.
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st) {
+  DevScalars* sc = a.sc;
+  const double lam = sc->lam;
+  double v[3];
+  final_block<MIXED>(a, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, v);
+  if (threadIdx.x == 0) {
+    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+  }
+  if (!last_block_done(&sc->counter)) return;
+  double S[3];
+  combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
+  if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st);
+}
+
+// A whole substep in one cooperative launch: Newton evaluations separated by
+// grid barriers until converged, then the final pass.  Every block combines
+// the block partials itself, in the same fixed order, so all blocks take the
+// same Newton steps without another barrier; the partials are double-buffered
+// because a fast block may start the next evaluation while a slow one is
+// still reading the previous partials.
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_substep_coop(PassArgs a, rec_stats* st, double n3d) {
+  cg::grid_group grid = cg::this_grid();
+  DevScalars* sc = a.sc;
+  const StepCoef& k = a.k;
+  __shared__ double s_lam, s_rel;
+  __shared__ int s_conv;
+  const double S1s = sc->S1s, tot = (double)sc->tally_total;
+  // R_alpha^mix from the substep-start <n_1s> (Eq. R-alpha), C from Eq. Cfactor
+  const double R = k.KR / (k.nH * S1s / n3d);
+  const double C = (k.L2g + R) / (k.beta + k.L2g + R);
+  const double omC = 1.0 - C, G0 = C * k.beta * k.ea;
+  const double tol = MIXED ? 1e-5 : 1e-8;
+  double lam = sc->lam_state;
+  if (sc->lam_prev > 0.0 && sc->lam_state > 0.0)
+    lam = sc->lam_state * fmin(2.0, fmax(0.5, sc->lam_state / sc->lam_prev));
+  if (!(lam > 0.0)) lam = 1e-30;
+  int passes = 0;
+  bool conv = false;
+  double prev_rel = HUGE_VAL;
+  while (passes < kNewtonMaxPasses && !conv) {
+    double v[3];
+    newton_block_sums<MIXED>(a, lam, omC * lam + G0, tot, S1s, v);
+    double* part = a.part + (size_t)(passes & 1) * gridDim.x * kMaxSums;
+    if (threadIdx.x == 0) {
+      double* p = part + (size_t)blockIdx.x * kMaxSums;
+      p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
     }
+    grid.sync();
+    double S[3];
+    combine_partials<3, NT>(part, gridDim.x, kMaxSums, S);
+    if (threadIdx.x == 0) {
+      double F = S[0] - lam * S[1];
+      double Fp = omC * S[2] - S[1];
+      double step = F / Fp;
+      double lnew = lam - step;
+      if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
+      double rel = fabs(step) / lam;
+      s_conv = (Fp < 0.0 && (rel <= tol || (rel <= 1e-3 && rel >= 0.5 * prev_rel))) ? 1 : 0;
+      s_lam = lnew;
+      s_rel = rel;
+    }
+    __syncthreads();
+    lam = s_lam;
+    conv = s_conv != 0;
+    prev_rel = s_rel;
+    ++passes;
+  }
+  double v[3];
+  final_block<MIXED>(a, omC * lam + G0, tot, S1s, v);
+  double* part = a.part + (size_t)(passes & 1) * gridDim.x * kMaxSums;
+  if (threadIdx.x == 0) {
+    double* p = part + (size_t)blockIdx.x * kMaxSums;
+    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+  }
+  grid.sync();
+  if (blockIdx.x != 0) return;
+  double S[3];
+  combine_partials<3, NT>(part, gridDim.x, kMaxSums, S);
+  if (threadIdx.x == 0) {
+    sc->C = C;
+    sc->omC = omC;
+    sc->G0 = G0;
+    sc->lam = lam;
+    sc->passes = passes;
+    sc->conv = conv ? 1 : 0;
+    if (!conv) sc->flags |= 1;
+    finish_substep(sc, k, S, lam, st);
   }
 }
 
@@ -356,8 +476,12 @@ __global__ void __launch_bounds__(NT) k_refresh(PassArgs a) {
     double al = a.k.fa * exp(a.k.pb * lt) / (1.0 + a.k.pc * exp(a.k.pd * lt));
     double n = a.k.nH * d;
     double r = al * (n * x) * (n * x);
-    if (MIXED) ((float*)a.emis)[i] = (float)r;
-    else ((double*)a.emis)[i] = r;
+    if (MIXED) {
+      ((float*)a.emis)[i] = (float)r;
+      a.xy[i] = make_float2(__double2float_rn(x), __double2float_rn(1.0 - x));
+    } else {
+      ((double*)a.emis)[i] = r;
+    }
     v[0] += d * (1.0 - x);
     v[1] += d * x;
     v[2] += d;
@@ -405,6 +529,7 @@ PassArgs pass_args(rec_ctx* c, const StepCoef& k) {
   a.delta = c->box.delta;
   a.vel4 = c->box.vel4;
   a.x = c->box.x_e;
+  a.xy = (float2*)c->xy;
   a.T = c->box.T;
   a.tally = c->box.tally;
   a.emis = c->box.emis;
@@ -453,12 +578,36 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
   const int ns = c->params.n_sub;
   const bool mixed = c->params.precision == REC_PREC_MIXED;
   double ya = std::log1p(z_from), yb = std::log1p(z_to);
-  GroupTimer t(c, kTStep, ns * (kNewtonMaxPasses + 2));
+  // grid of the cooperative substep: every block must be resident
+  if (c->coop_grid == 0) {
+    // tuning: one launch per Newton evaluation (default, faster on GB300 at the
+    // 256^3 workload) or REC_SUBSTEP=coop for one cooperative launch per substep
+    const char* sel = std::getenv("REC_SUBSTEP");
+    if (!(sel && std::strcmp(sel, "coop") == 0)) c->coop_grid = -1;
+  }
+  if (c->coop_grid == 0) {
+    int per_sm = 0;
+    cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_substep_coop<true>, NT, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_substep_coop<false>, NT, 0);
+    if (e != cudaSuccess) return e;
+    int attr = 0;
+    cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, 0);
+    c->coop_grid = (attr && per_sm > 0) ? std::min(c->grid, per_sm * c->sm_count) : -1;
+  }
+  GroupTimer t(c, kTStep, c->coop_grid > 0 ? ns : ns * (kNewtonMaxPasses + 2));
   for (int s = 0; s < ns; ++s) {
     double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
     double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
     StepCoef k = step_coef(c->cosmo, c->params, za, zb, s == ns - 1);
     PassArgs a = pass_args(c, k);
+    if (c->coop_grid > 0) {
+      double n3d = (double)c->n3;
+      void* args[] = {&a, &st, &n3d};
+      cudaError_t e = cudaLaunchCooperativeKernel(mixed ? (void*)k_substep_coop<true> : (void*)k_substep_coop<false>,
+                                                  c->coop_grid, NT, args, 0, c->stream);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     k_substep_begin<<<1, 32, 0, c->stream>>>(c->sc, k, (double)c->n3);
     for (int it = 0; it < kNewtonMaxPasses; ++it) {
       if (mixed) k_newton<true><<<c->grid, NT, 0, c->stream>>>(a);

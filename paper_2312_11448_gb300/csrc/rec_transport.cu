@@ -15,9 +15,13 @@
 //                   them and draws the systematic-sampling offset u
 //   k_alloc_prefix  packet prefix P_i = floor((N prefixQ_i + u) / sum Q), exact
 //                   128-bit integer arithmetic
+//   k_alloc_index   cell of every 32nd packet; packets per 32^3 super-tile
+//   k_bucket_offsets  queue bucket offsets (capacities) per super-tile
 //   k_emit          one packet per thread: warp-cooperative cell lookup in P,
 //                   Philox draws, emission, resonance test in the home cell
 //                   (warp-aggregated tally); the others step once and are queued
+//                   in their home super-tile's bucket
+//   k_bucket_scan   prefix of the queued counts (bucket order of the march)
 //   k_march         persistent warps march the queued packets (Amanatides-Woo),
 //                   refilling idle lanes from the queue; tally atomics
 //   k_transport_end counters to the statistics record
@@ -95,7 +99,7 @@ template <> struct Ar<double> {
 
 template <class R> struct Vec4;
 template <> struct Vec4<float> { using T = float4; };
-template <> struct Vec4<double> { using T = double4; };
+template <> struct Vec4<double> { using T = double4_32a; };
 
 // Per-precision draw layout.
 template <class R> struct Draws;
@@ -106,8 +110,12 @@ template <> struct Draws<float> {
     U4 r = draw(s, c, j, 0u);
     f[0] = u01f(r.a); f[1] = u01f(r.b); f[2] = u01f(r.c); *uq = u01f(r.d);
   }
-  static __device__ __forceinline__ void pair(const Stream& s, uint32_t c, uint32_t j, int t, float* a, float* b) {
-    U4 r = draw(s, c, j, 1u + (uint32_t)(t >> 1));
+  using Block = U4;
+  static __device__ __forceinline__ bool first_of_block(int t) { return (t & 1) == 0; }
+  static __device__ __forceinline__ U4 block(const Stream& s, uint32_t c, uint32_t j, int t) {
+    return draw(s, c, j, 1u + (uint32_t)(t >> 1));
+  }
+  static __device__ __forceinline__ void pair_from(const U4& r, int t, float* a, float* b) {
     if (t & 1) { *a = u01f(r.c); *b = u01f(r.d); }
     else { *a = u01f(r.a); *b = u01f(r.b); }
   }
@@ -119,8 +127,12 @@ template <> struct Draws<double> {
     U4 r = draw(s, c, j, 0u), q = draw(s, c, j, 1u);
     f[0] = u01d(r.a, r.b); f[1] = u01d(r.c, r.d); f[2] = u01d(q.a, q.b); *uq = u01d(q.c, q.d);
   }
-  static __device__ __forceinline__ void pair(const Stream& s, uint32_t c, uint32_t j, int t, double* a, double* b) {
-    U4 r = draw(s, c, j, 2u + (uint32_t)t);
+  using Block = U4;
+  static __device__ __forceinline__ bool first_of_block(int) { return true; }
+  static __device__ __forceinline__ U4 block(const Stream& s, uint32_t c, uint32_t j, int t) {
+    return draw(s, c, j, 2u + (uint32_t)t);
+  }
+  static __device__ __forceinline__ void pair_from(const U4& r, int, double* a, double* b) {
     *a = u01d(r.a, r.b); *b = u01d(r.c, r.d);
   }
 };
@@ -246,6 +258,7 @@ __device__ __forceinline__ uint32_t sys_floor(uint64_t N, uint64_t pre, uint64_t
   return (uint32_t)q;
 }
 
+// Packet prefix per cell.
 template <class R>
 __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, uint64_t n_packets, DevScalars* sc,
                                                      const unsigned long long* partQ, uint32_t* P) {
@@ -262,6 +275,91 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
   }
 }
 
+// Super-tiles of kTile^3 cells group the march queue: packets are queued in
+// the bucket of their home super-tile, and the march takes the buckets in
+// order, so the rays in flight at any time start in a compact region.
+constexpr uint32_t kTile = 32;
+
+struct Tiles {
+  uint32_t n, nt;  // box side, super-tiles per axis
+  __device__ __forceinline__ uint32_t of(uint32_t cell) const {
+    uint32_t ix = cell % n, iy = (cell / n) % n, iz = cell / (n * n);
+    return ((iz / kTile) * nt + iy / kTile) * nt + ix / kTile;
+  }
+};
+
+// From the packet prefix: the coarse index first[w] = cell of packet 32 w
+// (each cell writes the multiples of 32 in its packet range), which lets a warp
+// of 32 consecutive packets find its first cell with one load; and the number
+// of packets emitted per super-tile (the capacity of its queue bucket).
+__global__ void __launch_bounds__(kPassThreads) k_alloc_index(const uint32_t* P, int64_t n3, Tiles tl, uint32_t* first,
+                                                           unsigned long long* bcap) {
+  const int64_t stride = (int64_t)gridDim.x * kPassThreads;
+  const int64_t n_iter = (n3 + stride - 1) / stride;
+  for (int64_t it = 0; it < n_iter; ++it) {  // uniform trip count: the warp votes below need all lanes
+    int64_t i = it * stride + (int64_t)blockIdx.x * kPassThreads + threadIdx.x;
+    uint32_t cnt = 0, b = 0xffffffffu;
+    if (i < n3) {
+      uint32_t p0 = P[i], p1 = P[i + 1];
+      cnt = p1 - p0;
+      for (uint32_t w = (p0 + 31u) >> 5; 32ull * w < p1; ++w) first[w] = (uint32_t)i;
+      b = tl.of((uint32_t)i);
+    }
+    const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+    if (__all_sync(0xffffffffu, b == b0)) {
+      uint32_t tot = __reduce_add_sync(0xffffffffu, cnt);
+      if ((threadIdx.x & 31) == 0 && tot && b0 != 0xffffffffu) atomicAdd(&bcap[b0], (unsigned long long)tot);
+    } else if (cnt) {
+      atomicAdd(&bcap[b], (unsigned long long)cnt);
+    }
+  }
+}
+
+// One block: bucket capacities -> offsets (in place); fill counters cleared.
+__global__ void __launch_bounds__(1024) k_bucket_offsets(unsigned long long* bcap, unsigned long long* bfill, int nb) {
+  __shared__ unsigned long long part[1024];
+  const int per = (nb + 1023) / 1024;
+  unsigned long long s = 0;
+  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) s += bcap[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int t = 0; t < 1024; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; }
+  }
+  __syncthreads();
+  unsigned long long run = part[threadIdx.x];
+  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
+    unsigned long long v = bcap[b];
+    bcap[b] = run;
+    run += v;
+    bfill[b] = 0;
+  }
+}
+
+// One block: prefix of the packets actually queued per bucket; the total.
+__global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* bfill, unsigned long long* bpre, int nb,
+                                                      DevScalars* sc) {
+  __shared__ unsigned long long part[1024];
+  const int per = (nb + 1023) / 1024;
+  unsigned long long s = 0;
+  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) s += bfill[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int t = 0; t < 1024; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; }
+    bpre[nb] = run;
+    sc->qtail = run;
+  }
+  __syncthreads();
+  unsigned long long run = part[threadIdx.x];
+  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
+    bpre[b] = run;
+    run += bfill[b];
+  }
+}
+
 // ---- transport ----------------------------------------------------------------------
 // A queued packet: the march state right after it left its home cell.
 //   q0 = {cell bits, tMax_x, tMax_y, tMax_z}, q1 = {n_x, n_y, n_z, u0}
@@ -270,6 +368,7 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
 template <class R>
 struct TransportArgs {
   const uint32_t* P;
+  const uint32_t* first;  // cell of packet 32 w
   int64_t n3;
   int n;
   const typename Vec4<R>::T* vel;
@@ -281,6 +380,11 @@ struct TransportArgs {
   uint32_t* tally;
   DevScalars* sc;
   typename Vec4<R>::T* queue;  // 2 entries per queued packet
+  Tiles tl;
+  int nb;                          // buckets (super-tiles)
+  unsigned long long* boff;        // bucket start in the queue (capacity prefix)
+  unsigned long long* bfill;       // packets queued per bucket
+  const unsigned long long* bpre;  // prefix of bfill [nb + 1] (march)
 };
 
 // First index k in [lo, hi] with P[k] > key (P[hi] > key holds).
@@ -320,21 +424,30 @@ __device__ __forceinline__ void axis_setup(R nd, R* tD, int* st) {
 // One cell of the march: resonance test in the current cell, then a step
 // across the nearest face (ties x < y < z, periodic wrap).  Returns 1 when
 // absorbed in the current cell, 2 when the crossing cap is hit, 0 otherwise.
+// The step is written with selects rather than branches so that the lanes of
+// a warp stepping along different axes do not serialise.
 template <class R, class V>
 __device__ __forceinline__ int march_cell(Ray<R>& r, const V& Uc, uint32_t n) {
   using A = Ar<R>;
   R dc = A::add(A::add(A::mul(r.knx, Uc.x), A::mul(r.kny, Uc.y)), A::mul(r.knz, Uc.z));
-  int ax;
-  R s_exit;
-  if (r.tMx <= r.tMy && r.tMx <= r.tMz) { ax = 0; s_exit = r.tMx; }
-  else if (r.tMy <= r.tMz) { ax = 1; s_exit = r.tMy; }
-  else { ax = 2; s_exit = r.tMz; }
+  const bool ax0 = r.tMx <= r.tMy && r.tMx <= r.tMz;
+  const bool ax1 = !ax0 && r.tMy <= r.tMz;
+  const bool ax2 = !ax0 && !ax1;
+  const R s_exit = ax0 ? r.tMx : (ax1 ? r.tMy : r.tMz);
   // resonance in this cell at path length u0 - kappa n.U_c: absorb unless beyond the exit
   if (A::sub(r.u0, dc) <= s_exit) return 1;
   if (r.kc >= kMaxCrossings) return 2;
-  if (ax == 0) { r.ix = (r.sx > 0) ? (r.ix + 1 == n ? 0 : r.ix + 1) : (r.ix == 0 ? n - 1 : r.ix - 1); r.tMx = A::add(r.tMx, r.tDx); }
-  else if (ax == 1) { r.iy = (r.sy > 0) ? (r.iy + 1 == n ? 0 : r.iy + 1) : (r.iy == 0 ? n - 1 : r.iy - 1); r.tMy = A::add(r.tMy, r.tDy); }
-  else { r.iz = (r.sz > 0) ? (r.iz + 1 == n ? 0 : r.iz + 1) : (r.iz == 0 ? n - 1 : r.iz - 1); r.tMz = A::add(r.tMz, r.tDz); }
+  const uint32_t wx = r.sx > 0 ? (r.ix + 1 == n ? 0 : r.ix + 1) : (r.ix == 0 ? n - 1 : r.ix - 1);
+  const uint32_t wy = r.sy > 0 ? (r.iy + 1 == n ? 0 : r.iy + 1) : (r.iy == 0 ? n - 1 : r.iy - 1);
+  const uint32_t wz = r.sz > 0 ? (r.iz + 1 == n ? 0 : r.iz + 1) : (r.iz == 0 ? n - 1 : r.iz - 1);
+  r.ix = ax0 ? wx : r.ix;
+  r.iy = ax1 ? wy : r.iy;
+  r.iz = ax2 ? wz : r.iz;
+  const R tD = ax0 ? r.tDx : (ax1 ? r.tDy : r.tDz);
+  const R tn = A::add(s_exit, tD);
+  r.tMx = ax0 ? tn : r.tMx;
+  r.tMy = ax1 ? tn : r.tMy;
+  r.tMz = ax2 ? tn : r.tMz;
   ++r.kc;
   return 0;
 }
@@ -379,11 +492,9 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
        base += warps_total * 32) {
     const uint32_t p = (uint32_t)base + lane;
     const bool act = p < N;
-    // ---- cell of each packet: lane 0 searches for the warp's first packet,
-    // then a 32-cell window of P resolves the rest with ballots
-    uint32_t c0 = 0;
-    if (lane == 0) c0 = upper_bound(a.P, 0u, n3, (uint32_t)base) - 1u;
-    c0 = __shfl_sync(0xffffffffu, c0, 0);
+    // ---- cell of each packet: the coarse index gives the cell of the warp's
+    // first packet, then a 32-cell window of P resolves the rest with ballots
+    const uint32_t c0 = __ldg(a.first + (base >> 5));
     const uint32_t Pc0 = __ldg(a.P + c0);
     const uint32_t widx = c0 + 1u + lane;
     const uint32_t wv = (widx <= n3) ? __ldg(a.P + widx) : 0xffffffffu;
@@ -407,16 +518,21 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
       // (1) injection point uniform in the cell, frequency quantile
       R f[3], uq;
       Draws<R>::position(a.strm, cell, j, f, &uq);
-      // isotropic direction (Marsaglia 1972)
-      for (int t = 0; t < 32; ++t) {
-        R ua, ub;
-        Draws<R>::pair(a.strm, cell, j, t, &ua, &ub);
-        R v1 = A::sub(A::mul(two, ua), one), v2 = A::sub(A::mul(two, ub), one);
-        R s = A::add(A::mul(v1, v1), A::mul(v2, v2));
-        if (s < one && s > zero) {
-          R fac = A::mul(two, A::sqr(A::sub(one, s)));
-          nx = A::mul(v1, fac); ny = A::mul(v2, fac); nz = A::sub(one, A::mul(two, s));
-          break;
+      // isotropic direction (Marsaglia 1972): candidate pairs t = 0, 1, ...
+      // (each Philox block is computed once for the pairs it holds)
+      {
+        typename Draws<R>::Block blk;
+        for (int t = 0; t < 32; ++t) {
+          R ua, ub;
+          if (Draws<R>::first_of_block(t)) blk = Draws<R>::block(a.strm, cell, j, t);
+          Draws<R>::pair_from(blk, t, &ua, &ub);
+          R v1 = A::sub(A::mul(two, ua), one), v2 = A::sub(A::mul(two, ub), one);
+          R s = A::add(A::mul(v1, v1), A::mul(v2, v2));
+          if (s < one && s > zero) {
+            R fac = A::mul(two, A::sqr(A::sub(one, s)));
+            nx = A::mul(v1, fac); ny = A::mul(v2, fac); nz = A::sub(one, A::mul(two, s));
+            break;
+          }
         }
       }
       // emission frequency from the tabulated inverse CDF
@@ -449,14 +565,17 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
     const uint32_t key = home ? cell : 0xffffffffu;
     const unsigned m = __match_any_sync(0xffffffffu, key);
     if (home && lane == __ffs(m) - 1) atomicAdd(a.tally + cell, (uint32_t)__popc(m));
-    // queue the others after their first step
+    // queue the others after their first step, in their home super-tile's bucket
     const unsigned qm = __ballot_sync(0xffffffffu, queued);
     if (qm) {
+      const uint32_t bk = queued ? a.tl.of(cell) : 0xffffffffu;
+      const unsigned gm = __match_any_sync(0xffffffffu, bk) & qm;
       unsigned long long qb = 0;
-      if (lane == __ffs(qm) - 1) qb = atomicAdd(&a.sc->qtail, (unsigned long long)__popc(qm));
-      qb = __shfl_sync(0xffffffffu, qb, __ffs(qm) - 1);
+      const int leader = __ffs(gm) - 1;
+      if (queued && lane == leader) qb = atomicAdd(&a.bfill[bk], (unsigned long long)__popc(gm));
+      qb = __shfl_sync(0xffffffffu, qb, leader < 0 ? 0 : leader);
       if (queued) {
-        uint64_t slot = qb + __popc(qm & ((1u << lane) - 1u));
+        uint64_t slot = a.boff[bk] + qb + __popc(gm & ((1u << lane) - 1u));
         uint32_t c1 = (r.iz * n + r.iy) * n + r.ix;
         V q0v, q1v;
         q0v.x = bits_to<R>(c1); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
@@ -474,10 +593,12 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
 // through the queue together and the cells they touch stay close in memory)
 // and refills idle lanes from them, so that lanes stay busy whatever the
 // spread of path lengths.
-constexpr int kChunk = 256;
+constexpr int kChunk = 64;
+// Resident blocks per SM of the march (register budget 47 / 61 per thread).
+template <class R> constexpr int march_occupancy() { return sizeof(R) == 4 ? 5 : 4; }
 
 template <class R>
-__global__ void __launch_bounds__(TT, 4) k_march(TransportArgs<R> a) {
+__global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArgs<R> a) {
   using A = Ar<R>;
   using V = typename Vec4<R>::T;
   const int lane = threadIdx.x & 31;
@@ -507,7 +628,14 @@ __global__ void __launch_bounds__(TT, 4) k_march(TransportArgs<R> a) {
         const uint32_t take = (uint32_t)min((uint64_t)__popc(idle), end - pos);
         const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
         if (!active && ((idle >> lane) & 1u) && rank < take) {
-          const uint64_t slot = pos + rank;
+          const uint64_t L = pos + rank;  // position in bucket order
+          uint32_t lo = 0, hi = (uint32_t)a.nb;   // bucket: last b with bpre[b] <= L
+          while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(a.bpre + mid) <= L) lo = mid;
+            else hi = mid;
+          }
+          const uint64_t slot = a.boff[lo] + (L - __ldg(a.bpre + lo));
           V q0v = a.queue[2 * slot], q1v = a.queue[2 * slot + 1];
           cell = to_bits<R>(q0v.x);
           r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
@@ -571,10 +699,19 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
     k_alloc_prefix<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, c->sc,
                                                              c->partQ, c->P);
   }
+  Tiles tl{(uint32_t)b.n, (uint32_t)((b.n + kTile - 1) / kTile)};
+  const int nb = (int)(tl.nt * tl.nt * tl.nt);
+  {
+    GroupTimer t(c, kTAlloc, 2);
+    cudaMemsetAsync(c->bcap, 0, sizeof(unsigned long long) * nb, c->stream);
+    k_alloc_index<<<c->grid, kPassThreads, 0, c->stream>>>(c->P, c->n3, tl, c->first, c->bcap);
+    k_bucket_offsets<<<1, 1024, 0, c->stream>>>(c->bcap, c->bfill, nb);
+  }
   double kappa, cth;
   transport_scalars(c->cosmo, b.n, z, &kappa, &cth);
   TransportArgs<R> a;
   a.P = c->P;
+  a.first = c->first;
   a.n3 = c->n3;
   a.n = b.n;
   a.vel = (const typename Vec4<R>::T*)b.vel4;
@@ -587,13 +724,19 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.tally = b.tally;
   a.sc = c->sc;
   a.queue = (typename Vec4<R>::T*)c->queue;
+  a.tl = tl;
+  a.nb = nb;
+  a.boff = c->bcap;
+  a.bfill = c->bfill;
+  a.bpre = c->bpre;
   {
-    GroupTimer t(c, kTEmit, 1);
+    GroupTimer t(c, kTEmit, 2);
     k_emit<R><<<c->transport_blocks, TT, 0, c->stream>>>(a);
+    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->bpre, nb, c->sc);
   }
   {
     GroupTimer t(c, kTMarch, 1);
-    k_march<R><<<c->march_blocks, TT, 0, c->stream>>>(a);
+    k_march<R><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
   }
   {
     GroupTimer t(c, kTEnd, 1);
