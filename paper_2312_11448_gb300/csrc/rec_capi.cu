@@ -82,7 +82,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   c->queue = nullptr;
   c->first = nullptr;
   c->xy = nullptr;
-  c->bcap = nullptr; c->bfill = nullptr; c->bpre = nullptr;
+  c->bcap = nullptr; c->bfill = nullptr; c->cpre = nullptr;
   c->emis_ready = false;
 
   int dev = 0;
@@ -110,11 +110,11 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
     size_t nt = (size_t)((b.n + 31) / 32), nb = nt * nt * nt;  // 32^3 super-tiles of the march queue
     if (e == cudaSuccess) e = cudaMalloc(&c->bcap, sizeof(unsigned long long) * nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->bfill, sizeof(unsigned long long) * nb);
-    if (e == cudaSuccess) e = cudaMalloc(&c->bpre, sizeof(unsigned long long) * (nb + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->cpre, sizeof(unsigned long long) * (nb + 1));
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->quant, qbytes);
-  // march queue: two float4 (mixed) or double4_32a (FP64) per packet, worst case all packets
-  size_t qentry = params->precision == REC_PREC_MIXED ? 32 : 64;
+  // march queue: three float4 (mixed) or double4_32a (FP64) per packet, worst case all packets
+  size_t qentry = params->precision == REC_PREC_MIXED ? 48 : 96;
   if (e == cudaSuccess) e = cudaMalloc(&c->queue, qentry * (size_t)std::max<uint64_t>(b.n_packets, 1));
   if (e != cudaSuccess) {
     rec_status r = (e == cudaErrorMemoryAllocation) ? fail(nullptr, REC_ENOMEM, "device allocation failed")
@@ -303,7 +303,7 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->xy);
   cudaFree(c->bcap);
   cudaFree(c->bfill);
-  cudaFree(c->bpre);
+  cudaFree(c->cpre);
   delete c;
 }
 

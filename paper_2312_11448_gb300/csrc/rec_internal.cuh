@@ -97,7 +97,7 @@ struct rec_ctx {
   void* xy;                  // mixed form: binary32 (x, 1 - x) cache of the state [n3]
   unsigned long long* bcap;  // march-queue bucket capacities / offsets [super-tiles]
   unsigned long long* bfill; // packets queued per bucket [super-tiles]
-  unsigned long long* bpre;  // prefix of bfill [super-tiles + 1]
+  unsigned long long* cpre;  // first march chunk of each bucket [super-tiles + 1]
   unsigned long long* partQ; // allocation block sums / offsets [alloc blocks]
   void* quant;               // emission-profile table (float or double) [n_quantiles]
   int grid;                  // blocks of the streaming passes
@@ -105,7 +105,7 @@ struct rec_ctx {
   int transport_blocks;
   int march_blocks;
   int coop_grid = 0;         // blocks of the cooperative substep kernel (0: not yet queried, -1: unavailable)
-  void* queue;               // queued packets of the march (2 x 16|32 B each) [n_packets]
+  void* queue;               // queued packets of the march (3 x 16|32 B each) [n_packets]
   int sm_count;
   bool emis_ready;
   std::string err;

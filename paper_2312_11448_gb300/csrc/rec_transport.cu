@@ -14,8 +14,8 @@
 //   k_alloc_sum     Q_i = floor(2^31 r_i / r_max); block sums; last block scans
 //                   them and draws the systematic-sampling offset u
 //   k_alloc_prefix  packet prefix P_i = floor((N prefixQ_i + u) / sum Q), exact
-//                   128-bit integer arithmetic
-//   k_alloc_index   cell of every 32nd packet; packets per 32^3 super-tile
+//                   integer arithmetic; cell of every 32nd packet; packets per
+//                   32^3 super-tile
 //   k_bucket_offsets  queue bucket offsets (capacities) per super-tile
 //   k_emit          one packet per thread: warp-cooperative cell lookup in P,
 //                   Philox draws, emission, resonance test in the home cell
@@ -192,16 +192,54 @@ __device__ __forceinline__ uint64_t block_scan_incl(uint64_t v, uint64_t* incl) 
   return total;
 }
 
+// Super-tiles of kTile^3 cells group the march queue: packets are queued in
+// the bucket of their home super-tile, and the march takes the buckets in
+// order, so the rays in flight at any time start in a compact region.
+constexpr uint32_t kTile = 32;
+
+struct Tiles {
+  uint32_t n, nt;  // box side, super-tiles per axis
+  __device__ __forceinline__ uint32_t of(uint32_t cell) const {
+    uint32_t ix = cell % n, iy = (cell / n) % n, iz = cell / (n * n);
+    return ((iz / kTile) * nt + iy / kTile) * nt + ix / kTile;
+  }
+};
+
+// The allocation kernels give each thread kAllocItems consecutive cells.
+template <class R>
+__device__ __forceinline__ void load_items(const R* p, int64_t c0, int64_t n3, R (&v)[kAllocItems]) {
+  if (c0 + kAllocItems <= n3 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+    if (sizeof(R) == 4) {
+      const float4* q = reinterpret_cast<const float4*>(p + c0);
+#pragma unroll
+      for (int k = 0; k < kAllocItems / 4; ++k) {
+        float4 t = q[k];
+        v[4 * k] = (R)t.x; v[4 * k + 1] = (R)t.y; v[4 * k + 2] = (R)t.z; v[4 * k + 3] = (R)t.w;
+      }
+    } else {
+      const double2* q = reinterpret_cast<const double2*>(p + c0);
+#pragma unroll
+      for (int k = 0; k < kAllocItems / 2; ++k) {
+        double2 t = q[k];
+        v[2 * k] = (R)t.x; v[2 * k + 1] = (R)t.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kAllocItems; ++k) v[k] = (c0 + k < n3) ? p[c0 + k] : (R)0;
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(AT) k_alloc_sum(const R* emis, int64_t n3, uint64_t n_packets, Stream strm,
                                                   DevScalars* sc, unsigned long long* partQ, uint32_t* P) {
   const R rmax = (R)sc->rmax;
   uint64_t acc = 0;
   if (rmax > (R)0) {
-    for (int k = 0; k < kAllocItems; ++k) {
-      int64_t i = (int64_t)blockIdx.x * kAllocChunk + (int64_t)k * AT + threadIdx.x;
-      if (i < n3) acc += quantised<R>(emis[i], rmax);
-    }
+    R v[kAllocItems];
+    load_items<R>(emis, (int64_t)blockIdx.x * kAllocChunk + (int64_t)threadIdx.x * kAllocItems, n3, v);
+#pragma unroll
+    for (int k = 0; k < kAllocItems; ++k) acc += quantised<R>(v[k], rmax);
   }
   uint64_t incl;
   uint64_t tot = block_scan_incl(acc, &incl);
@@ -237,9 +275,9 @@ __global__ void __launch_bounds__(AT) k_alloc_sum(const R* emis, int64_t n3, uin
   }
 }
 
-// floor((N * pre + u) / S) for N < 2^32, pre <= S < 2^64, u < S: a binary64
-// estimate corrected with exact 128-bit products.
-__device__ __forceinline__ uint32_t sys_floor(uint64_t N, uint64_t pre, uint64_t u, uint64_t S) {
+// floor((N * pre + u) / S) and the remainder, for N < 2^32, pre <= S < 2^64,
+// u < S: a binary64 estimate corrected with exact 128-bit products.
+__device__ __forceinline__ uint32_t sys_floor(uint64_t N, uint64_t pre, uint64_t u, uint64_t S, uint64_t* rem) {
   uint64_t lo = N * pre, hi = __umul64hi(N, pre);
   uint64_t lo2 = lo + u;
   hi += (lo2 < lo);
@@ -253,67 +291,79 @@ __device__ __forceinline__ uint32_t sys_floor(uint64_t N, uint64_t pre, uint64_t
     // X - q S >= S ?
     uint64_t rlo = lo - plo, rhi = hi - phi - (lo < plo);
     if (rhi > 0 || rlo >= S) { ++q; continue; }
+    *rem = rlo;
     break;
   }
   return (uint32_t)q;
 }
 
-// Packet prefix per cell.
+// Packet prefix P_i = floor((N prefixQ_i + u) / S) of the thread's consecutive
+// cells: one 128-bit division for the first, then exact 64-bit remainder
+// updates, (R + N Q_i) / S.  The same pass writes the coarse index first[w] =
+// cell of packet 32 w (each cell writes the multiples of 32 in its packet
+// range, so a warp of 32 consecutive packets finds its first cell with one
+// load) and the packets per super-tile (the capacity of its march-queue bucket).
 template <class R>
 __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, uint64_t n_packets, DevScalars* sc,
-                                                     const unsigned long long* partQ, uint32_t* P) {
+                                                     const unsigned long long* partQ, uint32_t* P, uint32_t* first,
+                                                     Tiles tl, unsigned long long* bcap) {
   const R rmax = (R)sc->rmax;
   const uint64_t S = sc->sumQ, u = sc->alloc_u;
-  uint64_t run = partQ[blockIdx.x];
-  for (int k = 0; k < kAllocItems; ++k) {
-    int64_t i = (int64_t)blockIdx.x * kAllocChunk + (int64_t)k * AT + threadIdx.x;
-    uint64_t q = (i < n3 && rmax > (R)0) ? quantised<R>(emis[i], rmax) : 0;
-    uint64_t incl;
-    uint64_t tot = block_scan_incl(q, &incl);
-    if (i < n3) P[i] = (S > 0) ? sys_floor(n_packets, run + incl - q, u, S) : 0u;
-    run += tot;
+  const int64_t c0 = (int64_t)blockIdx.x * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+  uint64_t Q[kAllocItems];
+  uint64_t acc = 0;
+  {
+    R v[kAllocItems];
+    load_items<R>(emis, c0, n3, v);
+#pragma unroll
+    for (int k = 0; k < kAllocItems; ++k) {
+      Q[k] = (rmax > (R)0 && c0 + k < n3) ? quantised<R>(v[k], rmax) : 0;
+      acc += Q[k];
+    }
+  }
+  uint64_t incl;
+  block_scan_incl(acc, &incl);
+  if (c0 >= n3) return;
+  uint32_t out[kAllocItems];
+  if (S == 0) {
+#pragma unroll
+    for (int k = 0; k < kAllocItems; ++k) out[k] = 0u;
+  } else {
+    uint64_t rem;
+    uint32_t pk = sys_floor(n_packets, partQ[blockIdx.x] + incl - acc, u, S, &rem);
+    uint32_t bk = 0xffffffffu, bcount = 0;
+#pragma unroll
+    for (int k = 0; k < kAllocItems; ++k) {
+      out[k] = pk;
+      const uint64_t t = rem + n_packets * Q[k];
+      const uint64_t dq = t / S;
+      rem = t - dq * S;
+      const uint32_t p1 = pk + (uint32_t)dq;
+      if (p1 > pk && c0 + k < n3) {
+        for (uint32_t w = (pk + 31u) >> 5; 32ull * w < p1; ++w) first[w] = (uint32_t)(c0 + k);
+        const uint32_t b = tl.of((uint32_t)(c0 + k));
+        if (b != bk) {
+          if (bcount) atomicAdd(&bcap[bk], (unsigned long long)bcount);
+          bk = b;
+          bcount = 0;
+        }
+        bcount += p1 - pk;
+      }
+      pk = p1;
+    }
+    if (bcount) atomicAdd(&bcap[bk], (unsigned long long)bcount);
+  }
+  if (c0 + kAllocItems <= n3) {  // P is a 256-byte aligned allocation
+    uint4* q = reinterpret_cast<uint4*>(P + c0);
+#pragma unroll
+    for (int k = 0; k < kAllocItems / 4; ++k) q[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kAllocItems; ++k)
+      if (c0 + k < n3) P[c0 + k] = out[k];
   }
 }
 
-// Super-tiles of kTile^3 cells group the march queue: packets are queued in
-// the bucket of their home super-tile, and the march takes the buckets in
-// order, so the rays in flight at any time start in a compact region.
-constexpr uint32_t kTile = 32;
-
-struct Tiles {
-  uint32_t n, nt;  // box side, super-tiles per axis
-  __device__ __forceinline__ uint32_t of(uint32_t cell) const {
-    uint32_t ix = cell % n, iy = (cell / n) % n, iz = cell / (n * n);
-    return ((iz / kTile) * nt + iy / kTile) * nt + ix / kTile;
-  }
-};
-
-// From the packet prefix: the coarse index first[w] = cell of packet 32 w
-// (each cell writes the multiples of 32 in its packet range), which lets a warp
-// of 32 consecutive packets find its first cell with one load; and the number
-// of packets emitted per super-tile (the capacity of its queue bucket).
-__global__ void __launch_bounds__(kPassThreads) k_alloc_index(const uint32_t* P, int64_t n3, Tiles tl, uint32_t* first,
-                                                           unsigned long long* bcap) {
-  const int64_t stride = (int64_t)gridDim.x * kPassThreads;
-  const int64_t n_iter = (n3 + stride - 1) / stride;
-  for (int64_t it = 0; it < n_iter; ++it) {  // uniform trip count: the warp votes below need all lanes
-    int64_t i = it * stride + (int64_t)blockIdx.x * kPassThreads + threadIdx.x;
-    uint32_t cnt = 0, b = 0xffffffffu;
-    if (i < n3) {
-      uint32_t p0 = P[i], p1 = P[i + 1];
-      cnt = p1 - p0;
-      for (uint32_t w = (p0 + 31u) >> 5; 32ull * w < p1; ++w) first[w] = (uint32_t)i;
-      b = tl.of((uint32_t)i);
-    }
-    const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
-    if (__all_sync(0xffffffffu, b == b0)) {
-      uint32_t tot = __reduce_add_sync(0xffffffffu, cnt);
-      if ((threadIdx.x & 31) == 0 && tot && b0 != 0xffffffffu) atomicAdd(&bcap[b0], (unsigned long long)tot);
-    } else if (cnt) {
-      atomicAdd(&bcap[b], (unsigned long long)cnt);
-    }
-  }
-}
 
 // One block: bucket capacities -> offsets (in place); fill counters cleared.
 __global__ void __launch_bounds__(1024) k_bucket_offsets(unsigned long long* bcap, unsigned long long* bfill, int nb) {
@@ -337,34 +387,43 @@ __global__ void __launch_bounds__(1024) k_bucket_offsets(unsigned long long* bca
   }
 }
 
-// One block: prefix of the packets actually queued per bucket; the total.
-__global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* bfill, unsigned long long* bpre, int nb,
+// One block: the march works through the queue in chunks of kChunk packets that
+// never straddle a bucket; cpre[b] = first chunk of bucket b, cpre[nb] = all
+// chunks.  Also the total queued.
+constexpr int kChunk = 64;
+
+__global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* bfill, unsigned long long* cpre, int nb,
                                                       DevScalars* sc) {
-  __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long part[1024], qpart[1024];
   const int per = (nb + 1023) / 1024;
-  unsigned long long s = 0;
-  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) s += bfill[b];
+  unsigned long long s = 0, q = 0;
+  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
+    s += (bfill[b] + kChunk - 1) / kChunk;
+    q += bfill[b];
+  }
   part[threadIdx.x] = s;
+  qpart[threadIdx.x] = q;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int t = 0; t < 1024; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; }
-    bpre[nb] = run;
-    sc->qtail = run;
+    unsigned long long run = 0, qt = 0;
+    for (int t = 0; t < 1024; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; qt += qpart[t]; }
+    cpre[nb] = run;
+    sc->qtail = qt;
   }
   __syncthreads();
   unsigned long long run = part[threadIdx.x];
   for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
-    bpre[b] = run;
-    run += bfill[b];
+    cpre[b] = run;
+    run += (bfill[b] + kChunk - 1) / kChunk;
   }
 }
 
 // ---- transport ----------------------------------------------------------------------
-// A queued packet: the march state right after it left its home cell.
-//   q0 = {cell bits, tMax_x, tMax_y, tMax_z}, q1 = {n_x, n_y, n_z, u0}
-// The remaining traversal constants (tDelta, steps, kappa n) are recomputed
-// from n with the same operations, so the march continues bit for bit.
+// A queued packet: the march state right after it left its home cell,
+//   q0 = {cell bits, tMax_x, tMax_y, tMax_z}
+//   q1 = {tDelta_x, tDelta_y, tDelta_z (sign = step direction), u0}
+//   q2 = {kappa n_x, kappa n_y, kappa n_z, -}
+// so that the march continues bit for bit without recomputing anything.
 template <class R>
 struct TransportArgs {
   const uint32_t* P;
@@ -379,12 +438,12 @@ struct TransportArgs {
   Stream strm;
   uint32_t* tally;
   DevScalars* sc;
-  typename Vec4<R>::T* queue;  // 2 entries per queued packet
+  typename Vec4<R>::T* queue;  // 3 entries per queued packet
   Tiles tl;
   int nb;                          // buckets (super-tiles)
   unsigned long long* boff;        // bucket start in the queue (capacity prefix)
   unsigned long long* bfill;       // packets queued per bucket
-  const unsigned long long* bpre;  // prefix of bfill [nb + 1] (march)
+  const unsigned long long* cpre;  // first march chunk of each bucket [nb + 1]
 };
 
 // First index k in [lo, hi] with P[k] > key (P[hi] > key holds).
@@ -426,7 +485,14 @@ __device__ __forceinline__ void axis_setup(R nd, R* tD, int* st) {
 // absorbed in the current cell, 2 when the crossing cap is hit, 0 otherwise.
 // The step is written with selects rather than branches so that the lanes of
 // a warp stepping along different axes do not serialise.
-template <class R, class V>
+// Periodic neighbour index along one axis; a mask when the side is a power of two.
+template <bool P2>
+__device__ __forceinline__ uint32_t wrap_step(uint32_t i, int s, uint32_t n) {
+  if (P2) return (i + (uint32_t)s) & (n - 1u);
+  return s > 0 ? (i + 1 == n ? 0 : i + 1) : (i == 0 ? n - 1 : i - 1);
+}
+
+template <class R, bool P2 = false, class V>
 __device__ __forceinline__ int march_cell(Ray<R>& r, const V& Uc, uint32_t n) {
   using A = Ar<R>;
   R dc = A::add(A::add(A::mul(r.knx, Uc.x), A::mul(r.kny, Uc.y)), A::mul(r.knz, Uc.z));
@@ -437,9 +503,9 @@ __device__ __forceinline__ int march_cell(Ray<R>& r, const V& Uc, uint32_t n) {
   // resonance in this cell at path length u0 - kappa n.U_c: absorb unless beyond the exit
   if (A::sub(r.u0, dc) <= s_exit) return 1;
   if (r.kc >= kMaxCrossings) return 2;
-  const uint32_t wx = r.sx > 0 ? (r.ix + 1 == n ? 0 : r.ix + 1) : (r.ix == 0 ? n - 1 : r.ix - 1);
-  const uint32_t wy = r.sy > 0 ? (r.iy + 1 == n ? 0 : r.iy + 1) : (r.iy == 0 ? n - 1 : r.iy - 1);
-  const uint32_t wz = r.sz > 0 ? (r.iz + 1 == n ? 0 : r.iz + 1) : (r.iz == 0 ? n - 1 : r.iz - 1);
+  const uint32_t wx = wrap_step<P2>(r.ix, r.sx, n);
+  const uint32_t wy = wrap_step<P2>(r.iy, r.sy, n);
+  const uint32_t wz = wrap_step<P2>(r.iz, r.sz, n);
   r.ix = ax0 ? wx : r.ix;
   r.iy = ax1 ? wy : r.iy;
   r.iz = ax2 ? wz : r.iz;
@@ -498,12 +564,16 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
     const uint32_t Pc0 = __ldg(a.P + c0);
     const uint32_t widx = c0 + 1u + lane;
     const uint32_t wv = (widx <= n3) ? __ldg(a.P + widx) : 0xffffffffu;
+    // off = number of window entries <= p (the window is sorted): binary search
+    // over the 32 lane values with shuffles
     uint32_t off = 0;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      unsigned b = __ballot_sync(0xffffffffu, wv <= (uint32_t)base + (uint32_t)k);
-      if (lane == k) off = __popc(b);
+    for (uint32_t step = 16; step > 0; step >>= 1) {
+      const uint32_t probe = __shfl_sync(0xffffffffu, wv, (off + step - 1u) & 31u);
+      if (probe <= p) off += step;
     }
+    const uint32_t w31 = __shfl_sync(0xffffffffu, wv, 31);  // every lane takes part
+    if (off == 31u && w31 <= p) off = 32u;
     const uint32_t prev = __shfl_sync(0xffffffffu, wv, (off > 0 ? off - 1u : 0u) & 31u);
     uint32_t cell = c0 + off, Pc = (off == 0) ? Pc0 : prev;
     if (act && off >= 32) {
@@ -577,11 +647,14 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
       if (queued) {
         uint64_t slot = a.boff[bk] + qb + __popc(gm & ((1u << lane) - 1u));
         uint32_t c1 = (r.iz * n + r.iy) * n + r.ix;
-        V q0v, q1v;
+        V q0v, q1v, q2v;
         q0v.x = bits_to<R>(c1); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
-        q1v.x = nx; q1v.y = ny; q1v.z = nz; q1v.w = r.u0;
-        a.queue[2 * slot] = q0v;
-        a.queue[2 * slot + 1] = q1v;
+        q1v.x = r.sx < 0 ? -r.tDx : r.tDx; q1v.y = r.sy < 0 ? -r.tDy : r.tDy; q1v.z = r.sz < 0 ? -r.tDz : r.tDz;
+        q1v.w = r.u0;
+        q2v.x = r.knx; q2v.y = r.kny; q2v.z = r.knz; q2v.w = zero;
+        a.queue[3 * slot] = q0v;
+        a.queue[3 * slot + 1] = q1v;
+        a.queue[3 * slot + 2] = q2v;
       }
     }
   }
@@ -589,25 +662,26 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
 }
 
 // March of the queued packets.  Persistent warps; each warp owns the queue
-// chunks w, w + W, w + 2W, ... (chunks of kChunk packets, so the warps advance
-// through the queue together and the cells they touch stay close in memory)
-// and refills idle lanes from them, so that lanes stay busy whatever the
-// spread of path lengths.
-constexpr int kChunk = 64;
-// Resident blocks per SM of the march (register budget 47 / 61 per thread).
+// chunks w, w + W, w + 2W, ... (chunks of kChunk packets within one bucket, so
+// the warps advance through the buckets together and the cells they touch
+// stay close in memory) and refills idle lanes from them, so that lanes stay
+// busy whatever the spread of path lengths.
+// Resident blocks per SM of the march (register budget per thread).
 template <class R> constexpr int march_occupancy() { return sizeof(R) == 4 ? 5 : 4; }
 
-template <class R>
+// P2: the box side is a power of two (cell index by shifts and masks).
+template <class R, bool P2>
 __global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArgs<R> a) {
-  using A = Ar<R>;
   using V = typename Vec4<R>::T;
   const int lane = threadIdx.x & 31;
   const uint32_t n = (uint32_t)a.n;
-  const uint64_t Q = a.sc->qtail;
+  const uint32_t lg = P2 ? (uint32_t)(__ffs((int)n) - 1) : 0u;
+  const uint64_t n_chunks = a.cpre[a.nb];
   const uint64_t W = (uint64_t)gridDim.x * (TT / 32);
   uint64_t chunk = (uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5);
-  uint64_t pos = chunk * kChunk, end = min(pos + (uint64_t)kChunk, Q);
-  bool more = pos < Q;
+  uint64_t pos = 0, end = 0;  // queue slots [pos, end) left in the current chunk
+  bool have = false;          // a chunk is open
+  bool more = chunk < n_chunks;
   bool active = false;
   uint32_t cell = 0;
   Ray<R> r;
@@ -616,51 +690,57 @@ __global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArg
   uint64_t my_abs = 0, my_cap = 0, my_cross = 0;
   for (;;) {
     unsigned idle = __ballot_sync(0xffffffffu, !active);
-    if (more && __popc(idle) >= 4) {
-      // refill idle lanes in lane order from the warp's current chunk(s)
+    if (more && __popc(idle) >= 8) {
+      // refill idle lanes in lane order from the warp's chunks
       while (idle && more) {
-        if (pos >= end) {
-          chunk += W;
-          pos = chunk * kChunk;
-          end = min(pos + (uint64_t)kChunk, Q);
-          if (pos >= Q) { more = false; break; }
+        if (!have || pos >= end) {
+          if (have) chunk += W;
+          if (chunk >= n_chunks) { more = false; break; }
+          // bucket of this chunk: last b with cpre[b] <= chunk (uniform over the warp)
+          uint32_t lo = 0, hi = (uint32_t)a.nb;
+          while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(a.cpre + mid) <= chunk) lo = mid;
+            else hi = mid;
+          }
+          const uint64_t k0 = (chunk - __ldg(a.cpre + lo)) * kChunk;
+          pos = a.boff[lo] + k0;
+          end = pos + min((uint64_t)kChunk, (uint64_t)(a.bfill[lo] - k0));
+          have = true;
         }
         const uint32_t take = (uint32_t)min((uint64_t)__popc(idle), end - pos);
         const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
-        if (!active && ((idle >> lane) & 1u) && rank < take) {
-          const uint64_t L = pos + rank;  // position in bucket order
-          uint32_t lo = 0, hi = (uint32_t)a.nb;   // bucket: last b with bpre[b] <= L
-          while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(a.bpre + mid) <= L) lo = mid;
-            else hi = mid;
-          }
-          const uint64_t slot = a.boff[lo] + (L - __ldg(a.bpre + lo));
-          V q0v = a.queue[2 * slot], q1v = a.queue[2 * slot + 1];
+        if (((idle >> lane) & 1u) && rank < take) {
+          const uint64_t slot = pos + rank;
+          V q0v = a.queue[3 * slot], q1v = a.queue[3 * slot + 1], q2v = a.queue[3 * slot + 2];
           cell = to_bits<R>(q0v.x);
-          r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+          if (P2) {
+            r.ix = cell & (n - 1u); r.iy = (cell >> lg) & (n - 1u); r.iz = cell >> (2u * lg);
+          } else {
+            r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+          }
           r.tMx = q0v.y; r.tMy = q0v.z; r.tMz = q0v.w;
+          r.sx = q1v.x < (R)0 ? -1 : 1; r.tDx = fabs(q1v.x);
+          r.sy = q1v.y < (R)0 ? -1 : 1; r.tDy = fabs(q1v.y);
+          r.sz = q1v.z < (R)0 ? -1 : 1; r.tDz = fabs(q1v.z);
           r.u0 = q1v.w;
-          axis_setup<R>(q1v.x, &r.tDx, &r.sx);
-          axis_setup<R>(q1v.y, &r.tDy, &r.sy);
-          axis_setup<R>(q1v.z, &r.tDz, &r.sz);
-          r.knx = A::mul(a.kappa, q1v.x); r.kny = A::mul(a.kappa, q1v.y); r.knz = A::mul(a.kappa, q1v.z);
+          r.knx = q2v.x; r.kny = q2v.y; r.knz = q2v.z;
           r.kc = 1;  // the step out of the home cell
           Uc = a.vel[cell];
           active = true;
         }
         // lanes taken this round leave the idle set (the lowest `take` idle lanes)
         unsigned taken = 0, m = idle;
-        for (uint32_t t = 0; t < take; ++t) { unsigned b = m & (0u - m); taken |= b; m ^= b; }
+        for (uint32_t t = 0; t < take; ++t) { unsigned bb = m & (0u - m); taken |= bb; m ^= bb; }
         idle &= ~taken;
         pos += take;
       }
     }
-    if (!__any_sync(0xffffffffu, active)) break;
+    if (!__any_sync(0xffffffffu, active)) break;  // no packet left in the warp
     if (active) {
-      int res = march_cell<R>(r, Uc, n);
+      int res = march_cell<R, P2>(r, Uc, n);
       if (res == 0) {
-        cell = (r.iz * n + r.iy) * n + r.ix;
+        cell = P2 ? (((r.iz << lg) | r.iy) << lg) | r.ix : (r.iz * n + r.iy) * n + r.ix;
         Uc = a.vel[cell];
       } else {
         active = false;
@@ -691,20 +771,16 @@ template <class R>
 cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   const rec_box& b = c->box;
   Stream s{(uint32_t)c->params.seed, (uint32_t)(c->params.seed >> 32) ^ (uint32_t)step, 0u};
-  {
-    GroupTimer t(c, kTAlloc, 3);
-    k_alloc_max<R><<<c->grid, kPassThreads, 0, c->stream>>>((const R*)b.emis, c->n3, c->sc, c->part);
-    k_alloc_sum<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, s, c->sc,
-                                                          c->partQ, c->P);
-    k_alloc_prefix<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, c->sc,
-                                                             c->partQ, c->P);
-  }
   Tiles tl{(uint32_t)b.n, (uint32_t)((b.n + kTile - 1) / kTile)};
   const int nb = (int)(tl.nt * tl.nt * tl.nt);
   {
-    GroupTimer t(c, kTAlloc, 2);
+    GroupTimer t(c, kTAlloc, 4);
+    k_alloc_max<R><<<c->grid, kPassThreads, 0, c->stream>>>((const R*)b.emis, c->n3, c->sc, c->part);
+    k_alloc_sum<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, s, c->sc,
+                                                          c->partQ, c->P);
     cudaMemsetAsync(c->bcap, 0, sizeof(unsigned long long) * nb, c->stream);
-    k_alloc_index<<<c->grid, kPassThreads, 0, c->stream>>>(c->P, c->n3, tl, c->first, c->bcap);
+    k_alloc_prefix<R><<<c->alloc_blocks, AT, 0, c->stream>>>((const R*)b.emis, c->n3, b.n_packets, c->sc,
+                                                             c->partQ, c->P, c->first, tl, c->bcap);
     k_bucket_offsets<<<1, 1024, 0, c->stream>>>(c->bcap, c->bfill, nb);
   }
   double kappa, cth;
@@ -728,15 +804,17 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.nb = nb;
   a.boff = c->bcap;
   a.bfill = c->bfill;
-  a.bpre = c->bpre;
+  a.cpre = c->cpre;
   {
     GroupTimer t(c, kTEmit, 2);
     k_emit<R><<<c->transport_blocks, TT, 0, c->stream>>>(a);
-    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->bpre, nb, c->sc);
+    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->sc);
   }
   {
     GroupTimer t(c, kTMarch, 1);
-    k_march<R><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
+    const bool p2 = (b.n & (b.n - 1)) == 0;
+    if (p2) k_march<R, true><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
+    else k_march<R, false><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
   }
   {
     GroupTimer t(c, kTEnd, 1);
