@@ -141,6 +141,33 @@ rec_status lya_transport(rec_ctx* ctx, int32_t step, double z, rec_stats* dev_st
  * Errors: REC_EINVAL (z order), REC_ESTATE, REC_ECUDA. */
 rec_status rec_step(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
 
+/* Allocation-free step.  The paper has no counterpart: this is a library entry
+ * point for callers that cannot allocate device memory while they step, such as
+ * a host code whose own pool allocator has taken all device memory at start-up
+ * (a cudaMalloc would fail) or one whose loop cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  It needs no rec_ctx and performs the
+ * same passes as rec_refresh(z_from) followed by rec_step(z_from, z_to) on a
+ * context created for *box: the sums and emission weights of the incoming
+ * state, then n_sub backward-Euler substeps of Eq. (dotne-mix) and the T_b /
+ * drag update, in TALLY or FULL mixing.
+ *   params: as for rec_init; precision must be REC_PREC_FP64 (the mixed form
+ *     keeps a per-cell cache that a static array of modest size cannot hold).
+ *   box: field buffers as for rec_init (n in [1, 1024]; n_packets unused);
+ *     x_e, T, vel4, emis are updated in place, tallies zeroed at the end.
+ *   cuda_stream: a stream of the current device (NULL: legacy default stream).
+ *   dev_stats: device-visible rec_stats (may be NULL), written at the end.
+ * Scratch: a static device array of 130 KiB per device (one scalar record and
+ * per-block partial sums for at most 2048 blocks).  The step uses
+ * min(ceil(n^3/256), 8 x SM count) blocks and is rejected with REC_EINVAL when
+ * that exceeds 2048.  The first call on a device does the set-up (it looks up
+ * the array's device address, which may load the module), so make it before
+ * any stream capture.  Each call clears the scalar record on the stream first.
+ * Calls that overlap in time on one device (several streams or host threads)
+ * share the array and race: serialise them.
+ * Errors: REC_EINVAL, REC_ECUDA; rec_last_error(NULL) gives the cause. */
+rec_status rec_step_noalloc(const rec_params* params, const rec_box* box, double z_from, double z_to,
+                            void* cuda_stream, rec_stats* dev_stats);
+
 /* Reverse of rec_step (FP64 form only), tallies held fixed.
  *   x_in, T_in, vel4_in: the state BEFORE the step (device, FP64 layouts);
  *   tally_in: this step's tallies (device u32 [n^3], may be NULL in FULL mode).

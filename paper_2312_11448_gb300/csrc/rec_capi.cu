@@ -182,6 +182,24 @@ rec_status rec_step(rec_ctx* c, int32_t step, double z_from, double z_to, rec_st
   return REC_OK;
 }
 
+rec_status rec_step_noalloc(const rec_params* params, const rec_box* box, double z_from, double z_to,
+                            void* cuda_stream, rec_stats* dev_stats) {
+  g_init_error.clear();
+  std::string why;
+  rec_status s = check_params(params, &why);
+  if (s != REC_OK) return fail(nullptr, s, why);
+  if (params->precision != REC_PREC_FP64)
+    return fail(nullptr, REC_EINVAL, "rec_step_noalloc needs the FP64 form (the mixed form keeps a per-cell cache)");
+  if (!box) return fail(nullptr, REC_EINVAL, "box is NULL");
+  if (box->n < 1 || box->n > 1024) return fail(nullptr, REC_EINVAL, "box side n must be in [1, 1024]");
+  if (!box->delta || !box->vel4 || !box->x_e || !box->T || !box->tally || !box->emis)
+    return fail(nullptr, REC_EINVAL, "a field buffer is NULL");
+  if (!(z_from > z_to) || !(z_to > 0) || !is_finite(z_from)) return fail(nullptr, REC_EINVAL, "need z_from > z_to > 0");
+  s = rec::launch_rec_step_noalloc(*params, *box, z_from, z_to, (cudaStream_t)cuda_stream, dev_stats, &why);
+  if (s != REC_OK) return fail(nullptr, s, "rec_step_noalloc: " + why);
+  return REC_OK;
+}
+
 rec_status rec_step_adjoint(rec_ctx* c, int32_t step, double z_from, double z_to, const double* x_in,
                             const double* T_in, const double* vel4_in, const uint32_t* tally_in, double* xbar,
                             double* Tbar, double* Ubar, double* g_delta, double* g_a, double Xe_bar_out) {

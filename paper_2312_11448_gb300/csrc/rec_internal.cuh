@@ -160,6 +160,9 @@ double thomson_sigma_c(); // sigma_T c, m^3/s
 cudaError_t launch_state_init(rec_ctx* c, double z);
 cudaError_t launch_refresh(rec_ctx* c, double z);
 cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* st);
+// Context-free FP64 step on static device scratch; no device allocation.
+rec_status launch_rec_step_noalloc(const rec_params& p, const rec_box& b, double z_from, double z_to,
+                                   cudaStream_t stream, rec_stats* st, std::string* why);
 // Newton passes for lambda of a substep on an arbitrary FP64 state (used by the adjoint).
 void enqueue_newton_passes(rec_ctx* c, DevScalars* sc, const StepCoef& k, const double* x, const double* T,
                            const uint32_t* tally);

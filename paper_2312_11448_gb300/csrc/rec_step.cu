@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include <cooperative_groups.h>
 
@@ -617,6 +618,109 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
     else k_final<false><<<c->grid, NT, 0, c->stream>>>(a, st);
   }
   return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------- allocation-free step
+// The same refresh + Newton + final passes as rec_refresh followed by rec_step
+// (FP64 form), for callers that cannot allocate device memory at step time: a
+// host code that hands all device memory to its own pool allocator at start-up
+// (a cudaMalloc would then fail), or one stepping from a loop where the
+// implicit device synchronisation of cudaMalloc/cudaFree would stall work on
+// its other streams.  Its scratch, one DevScalars record and the per-block
+// partial sums, lives in the file-scope array below instead of a context.
+// Every call clears the record first (the last-block-done counter, the Newton
+// state and the flags must start at zero); the partials are written before
+// they are read.  All calls on a device share the array: calls that overlap in
+// time on that device (other streams, other host threads) race on it.
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 2048;
+constexpr size_t kNoAllocScBytes = (sizeof(DevScalars) + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kNoAllocScBytes + sizeof(double) * kMaxSums * kNoAllocMaxBlocks;  // 130 KiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+  unsigned char* scratch;  // device address of g_noalloc_scratch
+  int sm_count;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+// Once per device, with that device current: the address of the scratch array
+// and the SM count.  The first call on a device may load the module.
+cudaError_t noalloc_device(int dev, NoAllocDevice* out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.scratch) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    int sm = 0;
+    e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    d.sm_count = sm;
+    d.scratch = (unsigned char*)ptr;
+  }
+  *out = d;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+rec_status launch_rec_step_noalloc(const rec_params& p, const rec_box& b, double z_from, double z_to,
+                                   cudaStream_t stream, rec_stats* st, std::string* why) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { *why = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return REC_ECUDA; }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) { *why = "device ordinal beyond the static set-up table"; return REC_EINVAL; }
+  NoAllocDevice d;
+  e = noalloc_device(dev, &d);
+  if (e != cudaSuccess) { *why = std::string("scratch set-up: ") + cudaGetErrorString(e); return REC_ECUDA; }
+  const int64_t n3 = (int64_t)b.n * b.n * b.n;
+  // the grid of the context path, so that the sums are taken in the same order
+  const int64_t want = (n3 + NT - 1) / NT;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)d.sm_count * 8));
+  if (grid > kNoAllocMaxBlocks) {
+    *why = "the step needs " + std::to_string(grid) + " blocks of partial sums; the static scratch holds " +
+           std::to_string(kNoAllocMaxBlocks);
+    return REC_EINVAL;
+  }
+  DevScalars* sc = (DevScalars*)d.scratch;
+  double* part = (double*)(d.scratch + kNoAllocScBytes);
+  const Cosmo cosmo = make_cosmo(p);
+  PassArgs a;
+  a.n3 = n3;
+  a.delta = b.delta;
+  a.vel4 = b.vel4;
+  a.x = b.x_e;
+  a.xy = nullptr;
+  a.T = b.T;
+  a.tally = b.tally;
+  a.emis = b.emis;
+  a.sc = sc;
+  a.part = part;
+  a.n3_total = n3;
+  e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), stream);
+  if (e != cudaSuccess) { *why = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e); return REC_ECUDA; }
+  // sums and emission weights of the incoming state at z_from (as rec_refresh)
+  a.k = step_coef(cosmo, p, z_from + 1e-6 * (1.0 + z_from), z_from, 0);
+  k_refresh<false><<<grid, NT, 0, stream>>>(a);
+  const int ns = p.n_sub;
+  const double ya = std::log1p(z_from), yb = std::log1p(z_to);
+  for (int s = 0; s < ns; ++s) {
+    double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
+    double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
+    a.k = step_coef(cosmo, p, za, zb, s == ns - 1);
+    k_substep_begin<<<1, 32, 0, stream>>>(sc, a.k, (double)n3);
+    for (int it = 0; it < kNewtonMaxPasses; ++it) k_newton<false><<<grid, NT, 0, stream>>>(a);
+    k_final<false><<<grid, NT, 0, stream>>>(a, st);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { *why = std::string("launch: ") + cudaGetErrorString(e); return REC_ECUDA; }
+  return REC_OK;
 }
 
 }  // namespace rec

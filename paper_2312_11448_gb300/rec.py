@@ -61,6 +61,7 @@ def lib():
         L.rec_refresh.argtypes = [vp, d]
         L.lya_transport.argtypes = [vp, i32, d, vp]
         L.rec_step.argtypes = [vp, i32, d, d, vp]
+        L.rec_step_noalloc.argtypes = [P(Params), P(BoxDesc), d, d, vp, vp]
         L.rec_step_adjoint.argtypes = [vp, i32, d, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, d]
         L.rec_xe_adjoint.argtypes = [vp, vp, d, vp, vp]
         L.rec_transport_params.argtypes = [P(Params), i32, d, P(d)]
@@ -71,8 +72,8 @@ def lib():
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
         L.rec_last_error.restype = C.c_char_p
-        for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_adjoint",
-                  "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times"):
+        for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc",
+                  "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -185,6 +186,15 @@ class Box:
 
     def step(self, step, z_from, z_to, slot=0):
         self._check(lib().rec_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_step")
+
+    def step_noalloc(self, z_from, z_to, slot=0):
+        """rec_step_noalloc on this machine's fields and parameters (the context is not used)."""
+        desc = BoxDesc(self.n, self.delta.data_ptr(), self.vel4.data_ptr(), self.x.data_ptr(), self.T.data_ptr(),
+                       self.tally.data_ptr(), self.emis.data_ptr(), self.n_packets)
+        rc = lib().rec_step_noalloc(C.byref(self._params), C.byref(desc), z_from, z_to,
+                                    C.c_void_p(self.stream.cuda_stream), self._slot(slot))
+        if rc != REC_OK:
+            raise RecError(f"rec_step_noalloc: {lib().rec_last_error(None).decode()} (status {rc})")
 
     def step_adjoint(self, step, z_from, z_to, x_in, T_in, vel4_in, tally_in, xbar, Tbar, Ubar, g_delta, g_a,
                      Xe_bar_out=0.0):
