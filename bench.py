@@ -148,9 +148,9 @@ def algorithmic_bytes(precision, n3, emitted, queued, crossings, newton_passes):
            T, tally; final pass reads delta, x_e (+ cache), T, tally, velocity and
            writes x_e (+ cache), T, velocity, emission, tally."""
     if precision == "mixed":
-        v, t, d, e, qe = 16, 4, 4, 4, 32
+        v, t, d, e, qe = 16, 4, 4, 4, 48
     else:
-        v, t, d, e, qe = 32, 8, 8, 8, 64
+        v, t, d, e, qe = 32, 8, 8, 8, 96
     home = emitted - queued
     emit = emitted * (4 + t + v) + home * 4 + queued * qe
     march = queued * (qe + 4) + crossings * v
