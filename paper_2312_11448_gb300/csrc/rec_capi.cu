@@ -107,7 +107,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   if (e == cudaSuccess) e = cudaMalloc(&c->first, sizeof(uint32_t) * (size_t)(b.n_packets / 32 + 2));
   if (e == cudaSuccess && params->precision == REC_PREC_MIXED) e = cudaMalloc(&c->xy, sizeof(float) * 2 * (size_t)c->n3);
   {
-    size_t nt = (size_t)((b.n + 31) / 32), nb = nt * nt * nt;  // 32^3 super-tiles of the march queue
+    size_t nt = (size_t)((b.n + rec::kTile - 1) / rec::kTile), nb = nt * nt * nt;  // super-tiles of the march queue
     if (e == cudaSuccess) e = cudaMalloc(&c->bcap, sizeof(unsigned long long) * nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->bfill, sizeof(unsigned long long) * nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->cpre, sizeof(unsigned long long) * (nb + 1));

@@ -22,6 +22,8 @@ constexpr int kNewtonMaxPasses = 10;   // Newton evaluations launched per subste
 constexpr uint32_t kMaxCrossings = 1u << 20;  // per-packet cap on face crossings
 constexpr int kAllocThreads = 256;
 constexpr int kAllocItems = 16;        // consecutive cells per thread in the allocation scan
+// Side of the super-tiles whose buckets order the march queue.
+constexpr uint32_t kTile = 32;
 constexpr int kAllocChunk = kAllocThreads * kAllocItems;
 
 // Device-resident scalars of one box.  Everything data-dependent stays on the
@@ -50,6 +52,7 @@ struct DevScalars {
   unsigned long long sumQ;         // sum of quantised emission weights
   unsigned long long alloc_u;      // systematic-sampling offset in [0, sumQ)
   unsigned long long qtail;        // packets queued for the march
+  unsigned long long march_next;   // next queue chunk handed to a march warp
   uint32_t alloc_counter;
   int32_t emis_valid;
 };

@@ -195,12 +195,18 @@ __device__ __forceinline__ uint64_t block_scan_incl(uint64_t v, uint64_t* incl) 
 // Super-tiles of kTile^3 cells group the march queue: packets are queued in
 // the bucket of their home super-tile, and the march takes the buckets in
 // order, so the rays in flight at any time start in a compact region.
-constexpr uint32_t kTile = 32;
 
 struct Tiles {
-  uint32_t n, nt;  // box side, super-tiles per axis
+  uint32_t n, nt, lg;  // box side, super-tiles per axis, log2 n (power-of-two sides)
   __device__ __forceinline__ uint32_t of(uint32_t cell) const {
     uint32_t ix = cell % n, iy = (cell / n) % n, iz = cell / (n * n);
+    return ((iz / kTile) * nt + iy / kTile) * nt + ix / kTile;
+  }
+  template <bool P2>
+  __device__ __forceinline__ uint32_t at(uint32_t cell) const {
+    if (!P2) return of(cell);
+    const uint32_t m = n - 1u;
+    uint32_t ix = cell & m, iy = (cell >> lg) & m, iz = cell >> (2u * lg);
     return ((iz / kTile) * nt + iy / kTile) * nt + ix / kTile;
   }
 };
@@ -409,6 +415,7 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* 
     for (int t = 0; t < 1024; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; qt += qpart[t]; }
     cpre[nb] = run;
     sc->qtail = qt;
+    sc->march_next = 0;
   }
   __syncthreads();
   unsigned long long run = part[threadIdx.x];
@@ -543,7 +550,7 @@ __device__ __forceinline__ void add_counters(DevScalars* sc, uint64_t ab, uint64
 
 // Emission: one packet per thread.  Packets resonant in their home cell are
 // tallied here; the others take their first step and are queued.
-template <class R>
+template <class R, bool P2>
 __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
   using A = Ar<R>;
   using V = typename Vec4<R>::T;
@@ -617,7 +624,11 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
       V Uh = a.vel[cell];
       R dh = A::add(A::add(A::mul(r.knx, Uh.x), A::mul(r.kny, Uh.y)), A::mul(r.knz, Uh.z));
       r.u0 = A::add(A::mul(xi, vt), dh);
-      r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+      if (P2) {
+        r.ix = cell & (n - 1u); r.iy = (cell >> a.tl.lg) & (n - 1u); r.iz = cell >> (2u * a.tl.lg);
+      } else {
+        r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+      }
       axis_setup<R>(nx, &r.tDx, &r.sx);
       axis_setup<R>(ny, &r.tDy, &r.sy);
       axis_setup<R>(nz, &r.tDz, &r.sz);
@@ -625,7 +636,7 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
       r.tMy = r.sy > 0 ? A::mul(A::sub(one, f[1]), r.tDy) : (r.sy < 0 ? A::mul(f[1], r.tDy) : A::inf());
       r.tMz = r.sz > 0 ? A::mul(A::sub(one, f[2]), r.tDz) : (r.sz < 0 ? A::mul(f[2], r.tDz) : A::inf());
       r.kc = 0;
-      int res = march_cell<R>(r, Uh, n);  // home cell (res == 2 impossible with kc = 0)
+      int res = march_cell<R, P2>(r, Uh, n);  // home cell (res == 2 impossible with kc = 0)
       home = res == 1;
       queued = res == 0;
       my_cross += r.kc;
@@ -638,7 +649,7 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
     // queue the others after their first step, in their home super-tile's bucket
     const unsigned qm = __ballot_sync(0xffffffffu, queued);
     if (qm) {
-      const uint32_t bk = queued ? a.tl.of(cell) : 0xffffffffu;
+      const uint32_t bk = queued ? a.tl.template at<P2>(cell) : 0xffffffffu;
       const unsigned gm = __match_any_sync(0xffffffffu, bk) & qm;
       unsigned long long qb = 0;
       const int leader = __ffs(gm) - 1;
@@ -646,7 +657,7 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
       qb = __shfl_sync(0xffffffffu, qb, leader < 0 ? 0 : leader);
       if (queued) {
         uint64_t slot = a.boff[bk] + qb + __popc(gm & ((1u << lane) - 1u));
-        uint32_t c1 = (r.iz * n + r.iy) * n + r.ix;
+        uint32_t c1 = P2 ? (((r.iz << a.tl.lg) | r.iy) << a.tl.lg) | r.ix : (r.iz * n + r.iy) * n + r.ix;
         V q0v, q1v, q2v;
         q0v.x = bits_to<R>(c1); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
         q1v.x = r.sx < 0 ? -r.tDx : r.tDx; q1v.y = r.sy < 0 ? -r.tDy : r.tDy; q1v.z = r.sz < 0 ? -r.tDz : r.tDz;
@@ -661,11 +672,11 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
   add_counters(a.sc, my_abs, 0, my_cross);
 }
 
-// March of the queued packets.  Persistent warps; each warp owns the queue
-// chunks w, w + W, w + 2W, ... (chunks of kChunk packets within one bucket, so
-// the warps advance through the buckets together and the cells they touch
-// stay close in memory) and refills idle lanes from them, so that lanes stay
-// busy whatever the spread of path lengths.
+// March of the queued packets.  Persistent warps take chunks of kChunk queued
+// packets (never straddling a bucket) from a shared counter in queue order, so
+// the warps advance through the super-tile buckets together and the cells
+// they touch stay close in memory; each warp refills its idle lanes from its
+// current chunk, so that lanes stay busy whatever the spread of path lengths.
 // Resident blocks per SM of the march (register budget per thread).
 template <class R> constexpr int march_occupancy() { return sizeof(R) == 4 ? 5 : 4; }
 
@@ -677,11 +688,10 @@ __global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArg
   const uint32_t n = (uint32_t)a.n;
   const uint32_t lg = P2 ? (uint32_t)(__ffs((int)n) - 1) : 0u;
   const uint64_t n_chunks = a.cpre[a.nb];
-  const uint64_t W = (uint64_t)gridDim.x * (TT / 32);
-  uint64_t chunk = (uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5);
+  uint64_t chunk = 0;
   uint64_t pos = 0, end = 0;  // queue slots [pos, end) left in the current chunk
   bool have = false;          // a chunk is open
-  bool more = chunk < n_chunks;
+  bool more = n_chunks > 0;
   bool active = false;
   uint32_t cell = 0;
   Ray<R> r;
@@ -694,7 +704,11 @@ __global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArg
       // refill idle lanes in lane order from the warp's chunks
       while (idle && more) {
         if (!have || pos >= end) {
-          if (have) chunk += W;
+          // next chunk in queue order, shared by all warps: the warps in flight
+          // stay on neighbouring chunks, so their rays start close together
+          unsigned long long nc = 0;
+          if (lane == 0) nc = atomicAdd(&a.sc->march_next, 1ull);
+          chunk = __shfl_sync(0xffffffffu, nc, 0);
           if (chunk >= n_chunks) { more = false; break; }
           // bucket of this chunk: last b with cpre[b] <= chunk (uniform over the warp)
           uint32_t lo = 0, hi = (uint32_t)a.nb;
@@ -771,7 +785,10 @@ template <class R>
 cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   const rec_box& b = c->box;
   Stream s{(uint32_t)c->params.seed, (uint32_t)(c->params.seed >> 32) ^ (uint32_t)step, 0u};
-  Tiles tl{(uint32_t)b.n, (uint32_t)((b.n + kTile - 1) / kTile)};
+  const bool p2 = (b.n & (b.n - 1)) == 0;
+  uint32_t lg = 0;
+  while (p2 && (1 << lg) < b.n) ++lg;
+  Tiles tl{(uint32_t)b.n, (uint32_t)((b.n + kTile - 1) / kTile), lg};
   const int nb = (int)(tl.nt * tl.nt * tl.nt);
   {
     GroupTimer t(c, kTAlloc, 4);
@@ -807,12 +824,12 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.cpre = c->cpre;
   {
     GroupTimer t(c, kTEmit, 2);
-    k_emit<R><<<c->transport_blocks, TT, 0, c->stream>>>(a);
+    if (p2) k_emit<R, true><<<c->transport_blocks, TT, 0, c->stream>>>(a);
+    else k_emit<R, false><<<c->transport_blocks, TT, 0, c->stream>>>(a);
     k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->sc);
   }
   {
     GroupTimer t(c, kTMarch, 1);
-    const bool p2 = (b.n & (b.n - 1)) == 0;
     if (p2) k_march<R, true><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
     else k_march<R, false><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
   }
