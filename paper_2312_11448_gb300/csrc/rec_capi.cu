@@ -4,6 +4,7 @@
 // stream and returns a rec_status; no exception crosses the boundary.  The
 // context owns its scratch; field buffers belong to the caller.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -51,6 +52,140 @@ rec_status check_params(const rec_params* p, std::string* why) {
   return REC_OK;
 }
 
+rec_status check_box(const rec_box& b, std::string* why) {
+  if (b.n < 1 || b.n > 1024) { *why = "box side n must be in [1, 1024]"; return REC_EINVAL; }
+  if (!b.delta || !b.vel4 || !b.x_e || !b.T || !b.tally || !b.emis) { *why = "a field buffer is NULL"; return REC_EINVAL; }
+  if (b.n_packets >= (1ull << 32)) { *why = "n_packets must be below 2^32"; return REC_EINVAL; }
+  return REC_OK;
+}
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+// Context of several boxes: per-box records and concatenated scratch.
+rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_boxes, void* cuda_stream,
+                      rec_ctx** out) {
+  if (n_boxes > rec::kMaxBoxes) return fail(nullptr, REC_EINVAL, "at most 128 boxes per context");
+  std::string why;
+  for (int i = 0; i < n_boxes; ++i)
+    if (check_box(boxes[i], &why) != REC_OK) return fail(nullptr, REC_EINVAL, "box " + std::to_string(i) + ": " + why);
+  rec_ctx* c = new (std::nothrow) rec_ctx();
+  if (!c) return fail(nullptr, REC_ENOMEM, "host allocation failed");
+  c->params = *params;
+  c->params.emission_quantiles = nullptr;
+  c->box = boxes[0];
+  c->boxes.assign(boxes, boxes + n_boxes);
+  c->n_boxes = n_boxes;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->cosmo = rec::make_cosmo(*params);
+  c->sc = nullptr; c->sc_adj = nullptr; c->part = nullptr; c->P = nullptr; c->partQ = nullptr; c->quant = nullptr;
+  c->queue = nullptr; c->first = nullptr; c->xy = nullptr; c->bcap = nullptr; c->bfill = nullptr; c->cpre = nullptr;
+  c->emis_ready = false;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) { rec_status r = cuda_fail(nullptr, e, "device query"); delete c; return r; }
+  // offsets of every box in the concatenated scratch
+  const bool mixed = params->precision == REC_PREC_MIXED;
+  size_t nP = 0, nfirst = 0, nxy = 0, npk_all = 0;
+  c->hbx.resize(n_boxes);
+  int64_t n3_all = 0;
+  for (int i = 0; i < n_boxes; ++i) {
+    const rec_box& b = boxes[i];
+    rec::BoxDev& d = c->hbx[i];
+    std::memset(&d, 0, sizeof(d));
+    d.n3 = (int64_t)b.n * b.n * b.n;
+    d.n = (uint32_t)b.n;
+    d.p2 = (b.n & (b.n - 1)) == 0 ? 1u : 0u;
+    d.lg = 0;
+    while (d.p2 && (1 << d.lg) < b.n) ++d.lg;
+    d.nt = (uint32_t)((b.n + rec::kTile - 1) / rec::kTile);
+    d.npk = b.n_packets;
+    d.pk0 = c->tot_pk;
+    c->tot_pk += round_up(b.n_packets, 32);
+    d.ablk0 = (uint32_t)c->tot_ablk;
+    c->tot_ablk += (int)((d.n3 + rec::kAllocChunk - 1) / rec::kAllocChunk);
+    d.pblk = (uint32_t)std::max<int64_t>(1, (d.n3 + rec::kPassThreads * rec::kPassCellsPerThread - 1) /
+                                                (rec::kPassThreads * rec::kPassCellsPerThread));
+    d.pblk0 = (uint32_t)c->tot_pblk;
+    c->tot_pblk += (int)d.pblk;
+    d.bk0 = (uint32_t)c->tot_buckets;
+    c->tot_buckets += (int)(d.nt * d.nt * d.nt);
+    // scratch offsets (element counts), kept in the pointer fields until the buffers exist
+    d.P = (uint32_t*)(uintptr_t)nP;
+    nP += round_up((size_t)d.n3 + 1, 4);
+    d.first = (uint32_t*)(uintptr_t)nfirst;
+    nfirst += (size_t)(b.n_packets / 32 + 2);
+    d.xy = (void*)(uintptr_t)nxy;
+    nxy += (size_t)d.n3;
+    npk_all += b.n_packets;
+    n3_all += d.n3;
+  }
+  c->n3 = n3_all;
+  c->grid = c->tot_pblk;
+  c->alloc_blocks = c->tot_ablk;
+  const size_t qbytes = (size_t)params->n_quantiles * (mixed ? 4 : 8);
+  const size_t part_n = std::max<size_t>(2 * (size_t)rec::kMaxSums * c->tot_pblk, (size_t)rec::kMaxSums * c->tot_ablk);
+  const size_t qentry = mixed ? 48 : 96;
+  e = cudaMalloc(&c->sc, sizeof(rec::DevScalars) * n_boxes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->gsc, sizeof(rec::DevScalars));
+  if (e == cudaSuccess) e = cudaMalloc(&c->sc_adj, sizeof(rec::DevScalars));
+  if (e == cudaSuccess) e = cudaMalloc(&c->part, sizeof(double) * part_n);
+  if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(uint32_t) * nP);
+  if (e == cudaSuccess) e = cudaMalloc(&c->partQ, sizeof(unsigned long long) * (size_t)c->tot_ablk);
+  if (e == cudaSuccess) e = cudaMalloc(&c->first, sizeof(uint32_t) * nfirst);
+  if (e == cudaSuccess && mixed) e = cudaMalloc(&c->xy, sizeof(float) * 2 * nxy);
+  if (e == cudaSuccess) e = cudaMalloc(&c->bcap, sizeof(unsigned long long) * (size_t)c->tot_buckets);
+  if (e == cudaSuccess) e = cudaMalloc(&c->bfill, sizeof(unsigned long long) * (size_t)c->tot_buckets);
+  if (e == cudaSuccess) e = cudaMalloc(&c->cpre, sizeof(unsigned long long) * ((size_t)c->tot_buckets + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->quant, qbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->queue, qentry * std::max<size_t>(npk_all, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->bx, sizeof(rec::BoxDev) * n_boxes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->bstep, sizeof(rec::BoxStep) * n_boxes);
+  if (e != cudaSuccess) {
+    rec_status r = (e == cudaErrorMemoryAllocation) ? fail(nullptr, REC_ENOMEM, "device allocation failed")
+                                                    : cuda_fail(nullptr, e, "cudaMalloc");
+    rec_free(c);
+    return r;
+  }
+  for (int i = 0; i < n_boxes; ++i) {
+    const rec_box& b = boxes[i];
+    rec::BoxDev& d = c->hbx[i];
+    d.delta = b.delta;
+    d.vel4 = b.vel4;
+    d.x = b.x_e;
+    d.T = b.T;
+    d.tally = b.tally;
+    d.emis = b.emis;
+    d.P = c->P + (size_t)(uintptr_t)d.P;
+    d.first = c->first + (size_t)(uintptr_t)d.first;
+    d.xy = mixed ? (void*)((float2*)c->xy + (size_t)(uintptr_t)d.xy) : nullptr;
+    d.sc = c->sc + i;
+  }
+  std::vector<char> hq(qbytes);
+  for (int i = 0; i < params->n_quantiles; ++i) {
+    if (mixed) ((float*)hq.data())[i] = (float)params->emission_quantiles[i];
+    else ((double*)hq.data())[i] = params->emission_quantiles[i];
+  }
+  std::vector<rec::DevScalars> zero(n_boxes);
+  std::memset(zero.data(), 0, sizeof(rec::DevScalars) * n_boxes);
+  for (auto& z : zero) z.lam_prev = -1.0;
+  e = cudaMemcpyAsync(c->quant, hq.data(), qbytes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->sc, zero.data(), sizeof(rec::DevScalars) * n_boxes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->gsc, zero.data(), sizeof(rec::DevScalars), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->sc_adj, zero.data(), sizeof(rec::DevScalars), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->bx, c->hbx.data(), sizeof(rec::BoxDev) * n_boxes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    rec_status r = cuda_fail(nullptr, e, "rec_init upload");
+    rec_free(c);
+    return r;
+  }
+  *out = c;
+  return REC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -63,7 +198,8 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   std::string why;
   rec_status s = check_params(params, &why);
   if (s != REC_OK) return fail(nullptr, s, why);
-  if (!boxes || n_boxes != 1) return fail(nullptr, REC_EINVAL, "exactly one box is supported");
+  if (!boxes || n_boxes < 1) return fail(nullptr, REC_EINVAL, "need at least one box");
+  if (n_boxes > 1) return init_batch(params, boxes, n_boxes, cuda_stream, out);
   const rec_box& b = boxes[0];
   if (b.n < 1 || b.n > 1024) return fail(nullptr, REC_EINVAL, "box side n must be in [1, 1024]");
   if (!b.delta || !b.vel4 || !b.x_e || !b.T || !b.tally || !b.emis)
@@ -94,8 +230,6 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   c->grid = (int)std::min<int64_t>(want, (int64_t)c->sm_count * 8);
   if (c->grid < 1) c->grid = 1;
   c->alloc_blocks = (int)((c->n3 + rec::kAllocChunk - 1) / rec::kAllocChunk);
-  c->transport_blocks = c->sm_count * 8;
-  c->march_blocks = c->sm_count * 4;
 
   size_t qbytes = (size_t)params->n_quantiles * (params->precision == REC_PREC_MIXED ? 4 : 8);
   e = cudaMalloc(&c->sc, sizeof(rec::DevScalars));
@@ -148,7 +282,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
 rec_status rec_state_init(rec_ctx* c, double z) {
   if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
   if (!(z > 0) || !is_finite(z)) return fail(c, REC_EINVAL, "z must be positive");
-  cudaError_t e = rec::launch_state_init(c, z);
+  cudaError_t e = c->n_boxes > 1 ? rec::launch_state_init_batch(c, z) : rec::launch_state_init(c, z);
   if (e != cudaSuccess) return cuda_fail(c, e, "rec_state_init");
   c->emis_ready = true;
   return REC_OK;
@@ -157,7 +291,7 @@ rec_status rec_state_init(rec_ctx* c, double z) {
 rec_status rec_refresh(rec_ctx* c, double z) {
   if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
   if (!(z > 0) || !is_finite(z)) return fail(c, REC_EINVAL, "z must be positive");
-  cudaError_t e = rec::launch_refresh(c, z);
+  cudaError_t e = c->n_boxes > 1 ? rec::launch_refresh_batch(c, z) : rec::launch_refresh(c, z);
   if (e != cudaSuccess) return cuda_fail(c, e, "rec_refresh");
   c->emis_ready = true;
   return REC_OK;
@@ -167,7 +301,7 @@ rec_status lya_transport(rec_ctx* c, int32_t step, double z, rec_stats* st) {
   if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
   if (!(z > 0) || !is_finite(z)) return fail(c, REC_EINVAL, "z must be positive");
   if (step < 0) return fail(c, REC_EINVAL, "step must be non-negative");
-  cudaError_t e = rec::launch_transport(c, step, z, st);
+  cudaError_t e = c->n_boxes > 1 ? rec::launch_transport_batch(c, step, z, st) : rec::launch_transport(c, step, z, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "lya_transport");
   return REC_OK;
 }
@@ -177,7 +311,8 @@ rec_status rec_step(rec_ctx* c, int32_t step, double z_from, double z_to, rec_st
   (void)step;
   if (!(z_from > z_to) || !(z_to > 0) || !is_finite(z_from)) return fail(c, REC_EINVAL, "need z_from > z_to > 0");
   if (!c->emis_ready) return fail(c, REC_ESTATE, "state sums unknown: call rec_state_init or rec_refresh first");
-  cudaError_t e = rec::launch_rec_step(c, z_from, z_to, st);
+  cudaError_t e = c->n_boxes > 1 ? rec::launch_rec_step_batch(c, z_from, z_to, st)
+                                  : rec::launch_rec_step(c, z_from, z_to, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "rec_step");
   return REC_OK;
 }
@@ -205,6 +340,7 @@ rec_status rec_step_adjoint(rec_ctx* c, int32_t step, double z_from, double z_to
                             double* Tbar, double* Ubar, double* g_delta, double* g_a, double Xe_bar_out) {
   if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
   (void)step;
+  if (c->n_boxes > 1) return fail(c, REC_EINVAL, "the adjoint works on single-box contexts");
   if (c->params.precision != REC_PREC_FP64) return fail(c, REC_EINVAL, "the adjoint needs the FP64 form");
   if (c->params.n_sub != 1) return fail(c, REC_EINVAL, "the adjoint supports n_sub == 1");
   if (!(z_from > z_to) || !(z_to > 0)) return fail(c, REC_EINVAL, "need z_from > z_to > 0");
@@ -219,6 +355,7 @@ rec_status rec_step_adjoint(rec_ctx* c, int32_t step, double z_from, double z_to
 
 rec_status rec_xe_adjoint(rec_ctx* c, const double* x, double Xe_bar, double* xbar, double* g_delta) {
   if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  if (c->n_boxes > 1) return fail(c, REC_EINVAL, "the adjoint works on single-box contexts");
   if (c->params.precision != REC_PREC_FP64) return fail(c, REC_EINVAL, "the adjoint needs the FP64 form");
   if (!x || !xbar || !g_delta) return fail(c, REC_EINVAL, "a required buffer is NULL");
   cudaError_t e = rec::launch_xe_adjoint(c, x, Xe_bar, xbar, g_delta);
@@ -322,6 +459,9 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->bcap);
   cudaFree(c->bfill);
   cudaFree(c->cpre);
+  cudaFree(c->bx);
+  cudaFree(c->bstep);
+  cudaFree(c->gsc);
   delete c;
 }
 

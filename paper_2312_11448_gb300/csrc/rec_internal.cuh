@@ -57,6 +57,41 @@ struct DevScalars {
   int32_t emis_valid;
 };
 
+// Batched contexts (several boxes in one context, one launch per phase for
+// all of them).  Each box has its own fields, scalars, packet count and random
+// streams (box index in the Philox counter); the library scratch of all boxes
+// is concatenated and every box is described by one record.
+constexpr int kMaxBoxes = 128;
+constexpr int kPassCellsPerThread = 32;  // streaming-pass blocks per box: ceil(n^3 / (256 * 32))
+
+struct BoxDev {
+  // caller fields
+  const void* delta;
+  void* vel4;
+  double* x;
+  void* T;
+  uint32_t* tally;
+  void* emis;
+  // library scratch of this box
+  void* xy;            // mixed form: (x, 1 - x) cache [n3]
+  uint32_t* P;         // packet prefix [n3 + 1]
+  uint32_t* first;     // cell of packet 32 w [npk / 32 + 2]
+  DevScalars* sc;      // scalars of this box
+  int64_t n3;
+  uint32_t n, lg, nt, p2;  // side, log2 side (power of two), super-tiles per axis, side is a power of two
+  uint64_t npk;        // packets requested per transport
+  uint64_t pk0;        // first packet of the box in the batch packet space (multiple of 32)
+  uint32_t ablk0;      // first allocation block
+  uint32_t bk0;        // first march-queue bucket
+  uint32_t pblk0;      // first block of the streaming passes
+  uint32_t pblk;       // blocks of the streaming passes
+};
+
+// Transport scalars of one box at the redshift of a transport call.
+struct BoxStep {
+  double kappa, cth;
+};
+
 // Per-substep coefficients, computed on the host from the redshifts (no
 // data dependence), passed by value.
 struct StepCoef {
@@ -105,8 +140,6 @@ struct rec_ctx {
   void* quant;               // emission-profile table (float or double) [n_quantiles]
   int grid;                  // blocks of the streaming passes
   int alloc_blocks;
-  int transport_blocks;
-  int march_blocks;
   int coop_grid = 0;         // blocks of the cooperative substep kernel (0: not yet queried, -1: unavailable)
   void* queue;               // queued packets of the march (3 x 16|32 B each) [n_packets]
   int sm_count;
@@ -117,6 +150,17 @@ struct rec_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[REC_T_COUNT];
   std::vector<cudaEvent_t> pool;
   int64_t launches[REC_T_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  // batched context (n_boxes > 1); unused for one box
+  int n_boxes = 1;
+  std::vector<rec_box> boxes;
+  std::vector<rec::BoxDev> hbx;  // host copy of the box records
+  rec::BoxDev* bx = nullptr;     // device box records [n_boxes]
+  rec::BoxStep* bstep = nullptr; // device transport scalars [n_boxes]
+  rec::DevScalars* gsc = nullptr;// batch-wide counters (last-block-done, march chunks)
+  int tot_ablk = 0;              // allocation blocks of all boxes
+  int tot_pblk = 0;              // streaming-pass blocks of all boxes
+  int tot_buckets = 0;           // march-queue buckets of all boxes
+  uint64_t tot_pk = 0;           // batch packet space (each box padded to 32)
 };
 
 namespace rec {
@@ -172,6 +216,12 @@ void enqueue_newton_passes(rec_ctx* c, DevScalars* sc, const StepCoef& k, const 
 
 // rec_transport.cu
 cudaError_t launch_transport(rec_ctx* c, int step, double z, rec_stats* st);
+cudaError_t launch_transport_batch(rec_ctx* c, int step, double z, rec_stats* st);
+
+// rec_step.cu, batched contexts
+cudaError_t launch_state_init_batch(rec_ctx* c, double z);
+cudaError_t launch_refresh_batch(rec_ctx* c, double z);
+cudaError_t launch_rec_step_batch(rec_ctx* c, double z_from, double z_to, rec_stats* st);
 
 // rec_adjoint.cu
 cudaError_t launch_rec_step_adjoint(rec_ctx* c, double z_from, double z_to, const double* x_in, const double* T_in,

@@ -52,16 +52,18 @@ __device__ __forceinline__ double block_max(double v) {
   return v;
 }
 
-// True in every thread of the last block of the grid to arrive.  The caller
+// True in every thread of the last block of the grid (or of nblk blocks
+// sharing the counter) to arrive.  The caller
 // has written its partials before calling; the fence makes them visible.
-__device__ __forceinline__ bool last_block_done(uint32_t* counter) {
+__device__ __forceinline__ bool last_block_done(uint32_t* counter, uint32_t nblk) {
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == nblk - 1);
   __syncthreads();
   return am_last;
 }
+__device__ __forceinline__ bool last_block_done(uint32_t* counter) { return last_block_done(counter, gridDim.x); }
 
 // In the last block: combine K partial sums of nblk blocks (layout
 // part[b*stride + k]) in a fixed order.  Result valid in thread 0.

@@ -161,8 +161,7 @@ __device__ __forceinline__ void root_f32(float A, float s, float G, float x, flo
 
 // -------------------------------------------------------------- kernels
 // Substep prologue: C from the device sum S1s, Newton start.
-__global__ void k_substep_begin(DevScalars* sc, StepCoef k, double n3) {
-  if (threadIdx.x != 0) return;
+__device__ void substep_begin(DevScalars* sc, const StepCoef& k, double n3) {
   double n1s_mean = k.nH * sc->S1s / n3;
   double R = k.KR / n1s_mean;
   double C = (k.L2g + R) / (k.beta + k.L2g + R);
@@ -178,6 +177,12 @@ __global__ void k_substep_begin(DevScalars* sc, StepCoef k, double n3) {
   sc->passes = 0;
   sc->counter = 0;
   sc->last_step = 0.0;
+}
+__global__ void k_substep_begin(DevScalars* sc, StepCoef k, double n3) {
+  if (threadIdx.x == 0) substep_begin(sc, k, n3);
+}
+__global__ void k_substep_begin_batch(const BoxDev* bxs, int B, StepCoef k) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) substep_begin(bxs[b].sc, k, (double)bxs[b].n3);
 }
 
 // Newton step on the device scalars (last block, thread 0).
@@ -203,13 +208,13 @@ __device__ void newton_update(DevScalars* sc, double S0, double S1, double S2, d
 // v0 = sum alpha n^2 x'^2, v1 = sum n (1 - x'), v2 = sum (2 alpha n^2 x' + lambda n) dx'/dG.
 template <bool MIXED>
 __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam, double G, double tot, double S1s,
-                                                  double (&v)[3]) {
-  const int64_t stride = (int64_t)gridDim.x * NT;
+                                                  int blk, int nblk, double (&v)[3]) {
+  const int64_t stride = (int64_t)nblk * NT;
   if (!MIXED) {
     v[0] = v[1] = v[2] = 0.0;
     const double* delta = (const double*)a.delta;
     const double* T = (const double*)a.T;
-    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+    for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
       double d = delta[i], x = a.x[i];
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF64 c = cell_f64(a.k, d, x, T[i], tal, tot, S1s);
@@ -227,7 +232,7 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
     const float wscale = tot > 0.0 ? (float)(S1s / tot) : 0.0f;
     const float* delta = (const float*)a.delta;
     const float* T = (const float*)a.T;
-    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+    for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF32 c = cell_f32(f, a.k.mixing, delta[i], a.xy[i], T[i], tal, wscale);
       float xr, yr, dxdG;
@@ -246,8 +251,9 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
 // weights (zeroes the tallies on the last substep); partial sums (thread 0):
 // v0 = sum delta (1 - x'), v1 = sum delta x', v2 = sum delta.
 template <bool MIXED>
-__device__ __forceinline__ void final_block(const PassArgs& a, double G, double tot, double S1s, double (&v)[3]) {
-  const int64_t stride = (int64_t)gridDim.x * NT;
+__device__ __forceinline__ void final_block(const PassArgs& a, double G, double tot, double S1s, int blk, int nblk,
+                                            double (&v)[3]) {
+  const int64_t stride = (int64_t)nblk * NT;
   const bool zero_tally = a.k.last != 0;
   if (!MIXED) {
     v[0] = v[1] = v[2] = 0.0;
@@ -255,7 +261,7 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
     double* T = (double*)a.T;
     double4_32a* U = (double4_32a*)a.vel4;
     double* emis = (double*)a.emis;
-    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+    for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
       double d = delta[i], x = a.x[i];
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF64 c = cell_f64(a.k, d, x, T[i], tal, tot, S1s);
@@ -283,7 +289,7 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
     float4* U = (float4*)a.vel4;
     float* emis = (float*)a.emis;
     const float kdf = (float)a.k.kd, Hf = (float)a.k.H, dtf = (float)a.k.dt;
-    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+    for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
       float d = delta[i];
       double x = a.x[i];
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
@@ -346,20 +352,48 @@ __device__ __forceinline__ void finish_substep(DevScalars* sc, const StepCoef& k
   }
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(NT) k_newton(PassArgs a) {
+// Batched contexts (MB): the grid is the concatenation of every box's pass
+// blocks; a block works on its box's cells with the box's own block count, and
+// the last block of a box reduces that box's partials.  Single box: the whole grid.
+__device__ __forceinline__ void pass_view(PassArgs& a, const BoxDev* bxs, int B, int* blk, int* nblk, int* box) {
+  int lo = 0, hi = B;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (bxs[mid].pblk0 <= blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const BoxDev& d = bxs[lo];
+  a.n3 = d.n3;
+  a.delta = d.delta;
+  a.vel4 = d.vel4;
+  a.x = d.x;
+  a.xy = (float2*)d.xy;
+  a.T = d.T;
+  a.tally = d.tally;
+  a.emis = d.emis;
+  a.sc = d.sc;
+  a.part += (size_t)d.pblk0 * kMaxSums;
+  *blk = (int)(blockIdx.x - d.pblk0);
+  *nblk = (int)d.pblk;
+  *box = lo;
+}
+
+template <bool MIXED, bool MB>
+__global__ void __launch_bounds__(NT) k_newton(PassArgs a, const BoxDev* bxs, int B) {
+  int blk = blockIdx.x, nblk = gridDim.x, box = 0;
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
   DevScalars* sc = a.sc;
   if (ld_flag(&sc->conv)) return;
   const double lam = sc->lam;
   double v[3];
-  newton_block_sums<MIXED>(a, lam, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, v);
+  newton_block_sums<MIXED>(a, lam, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, blk, nblk, v);
   if (threadIdx.x == 0) {
-    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    double* p = a.part + (size_t)blk * kMaxSums;
     p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
   }
-  if (!last_block_done(&sc->counter)) return;
+  if (!last_block_done(&sc->counter, nblk)) return;
   double S[3];
-  combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
+  combine_partials<3, NT>(a.part, nblk, kMaxSums, S);
   if (threadIdx.x == 0) {
     newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
     sc->counter = 0;
@@ -367,20 +401,23 @@ __global__ void __launch_bounds__(NT) k_newton(PassArgs a) {
 }
 
 // Final pass: new state at the converged lambda, emission weights, sums.
-template <bool MIXED>
-__global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st) {
+// st: statistics record (one per box in a batch) or NULL.
+template <bool MIXED, bool MB>
+__global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st, const BoxDev* bxs, int B) {
+  int blk = blockIdx.x, nblk = gridDim.x, box = 0;
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
   DevScalars* sc = a.sc;
   const double lam = sc->lam;
   double v[3];
-  final_block<MIXED>(a, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, v);
+  final_block<MIXED>(a, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, blk, nblk, v);
   if (threadIdx.x == 0) {
-    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    double* p = a.part + (size_t)blk * kMaxSums;
     p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
   }
-  if (!last_block_done(&sc->counter)) return;
+  if (!last_block_done(&sc->counter, nblk)) return;
   double S[3];
-  combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
-  if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st);
+  combine_partials<3, NT>(a.part, nblk, kMaxSums, S);
+  if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st ? st + box : nullptr);
 }
 
 // A whole substep in one cooperative launch: Newton evaluations separated by
@@ -411,7 +448,7 @@ __global__ void __launch_bounds__(NT) k_substep_coop(PassArgs a, rec_stats* st, 
   double prev_rel = HUGE_VAL;
   while (passes < kNewtonMaxPasses && !conv) {
     double v[3];
-    newton_block_sums<MIXED>(a, lam, omC * lam + G0, tot, S1s, v);
+    newton_block_sums<MIXED>(a, lam, omC * lam + G0, tot, S1s, blockIdx.x, gridDim.x, v);
     double* part = a.part + (size_t)(passes & 1) * gridDim.x * kMaxSums;
     if (threadIdx.x == 0) {
       double* p = part + (size_t)blockIdx.x * kMaxSums;
@@ -438,7 +475,7 @@ __global__ void __launch_bounds__(NT) k_substep_coop(PassArgs a, rec_stats* st, 
     ++passes;
   }
   double v[3];
-  final_block<MIXED>(a, omC * lam + G0, tot, S1s, v);
+  final_block<MIXED>(a, omC * lam + G0, tot, S1s, blockIdx.x, gridDim.x, v);
   double* part = a.part + (size_t)(passes & 1) * gridDim.x * kMaxSums;
   if (threadIdx.x == 0) {
     double* p = part + (size_t)blockIdx.x * kMaxSums;
@@ -462,13 +499,15 @@ __global__ void __launch_bounds__(NT) k_substep_coop(PassArgs a, rec_stats* st, 
 
 // Emission weights and sums of the current state at redshift z (no update);
 // also recounts the tallies.
-template <bool MIXED>
-__global__ void __launch_bounds__(NT) k_refresh(PassArgs a) {
+template <bool MIXED, bool MB>
+__global__ void __launch_bounds__(NT) k_refresh(PassArgs a, const BoxDev* bxs, int B) {
+  int blk = blockIdx.x, nblk = gridDim.x, box = 0;
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
   DevScalars* sc = a.sc;
-  const int64_t stride = (int64_t)gridDim.x * NT;
+  const int64_t stride = (int64_t)nblk * NT;
   double v[6];  // S1s, Sdx, Sd, sum alpha n^2 x^2, sum n(1-x), tally count
   for (int k = 0; k < 6; ++k) v[k] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+  for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
     double d, T;
     if (MIXED) { d = ((const float*)a.delta)[i]; T = ((const float*)a.T)[i]; }
     else { d = ((const double*)a.delta)[i]; T = ((const double*)a.T)[i]; }
@@ -492,12 +531,12 @@ __global__ void __launch_bounds__(NT) k_refresh(PassArgs a) {
   }
   block_sum<6, NT>(v);
   if (threadIdx.x == 0) {
-    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    double* p = a.part + (size_t)blk * kMaxSums;
     for (int k = 0; k < 6; ++k) p[k] = v[k];
   }
-  if (!last_block_done(&sc->counter)) return;
+  if (!last_block_done(&sc->counter, nblk)) return;
   double S[6];
-  combine_partials<6, NT>(a.part, gridDim.x, kMaxSums, S);
+  combine_partials<6, NT>(a.part, nblk, kMaxSums, S);
   if (threadIdx.x == 0) {
     sc->S1s = S[0];
     sc->Sdx = S[1];
@@ -512,10 +551,12 @@ __global__ void __launch_bounds__(NT) k_refresh(PassArgs a) {
 }
 
 // x_e from the hydrogen Saha equation and T = T_gamma (initial state).
-template <bool MIXED>
-__global__ void k_state_init(PassArgs a, double nH_over_S, double Tg) {
-  const int64_t stride = (int64_t)gridDim.x * NT;
-  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+template <bool MIXED, bool MB>
+__global__ void k_state_init(PassArgs a, double nH_over_S, double Tg, const BoxDev* bxs, int B) {
+  int blk = blockIdx.x, nblk = gridDim.x, box = 0;
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
+  const int64_t stride = (int64_t)nblk * NT;
+  for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
     double d = MIXED ? (double)((const float*)a.delta)[i] : ((const double*)a.delta)[i];
     // x^2/(1-x) = S/n_H  =>  x = 2/(1 + sqrt(1 + 4 n_H/S))
     a.x[i] = 2.0 / (1.0 + sqrt(1.0 + 4.0 * nH_over_S * d));
@@ -551,15 +592,15 @@ void enqueue_newton_passes(rec_ctx* c, DevScalars* sc, const StepCoef& k, const 
   a.T = const_cast<double*>(T);
   a.tally = const_cast<uint32_t*>(tally);
   k_substep_begin<<<1, 32, 0, c->stream>>>(sc, k, (double)c->n3);
-  for (int it = 0; it < kNewtonMaxPasses; ++it) k_newton<false><<<c->grid, NT, 0, c->stream>>>(a);
+  for (int it = 0; it < kNewtonMaxPasses; ++it) k_newton<false, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
 }
 
 cudaError_t launch_refresh(rec_ctx* c, double z) {
   StepCoef k = step_coef(c->cosmo, c->params, z + 1e-6 * (1.0 + z), z, 0);
   PassArgs a = pass_args(c, k);
   GroupTimer t(c, kTOther, 1);
-  if (c->params.precision == REC_PREC_MIXED) k_refresh<true><<<c->grid, NT, 0, c->stream>>>(a);
-  else k_refresh<false><<<c->grid, NT, 0, c->stream>>>(a);
+  if (c->params.precision == REC_PREC_MIXED) k_refresh<true, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
+  else k_refresh<false, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
   return cudaGetLastError();
 }
 
@@ -568,8 +609,9 @@ cudaError_t launch_state_init(rec_ctx* c, double z) {
   PassArgs a = pass_args(c, k);
   double S = saha_S(k.Tg);
   GroupTimer t(c, kTOther, 1);
-  if (c->params.precision == REC_PREC_MIXED) k_state_init<true><<<c->grid, NT, 0, c->stream>>>(a, k.nH / S, k.Tg);
-  else k_state_init<false><<<c->grid, NT, 0, c->stream>>>(a, k.nH / S, k.Tg);
+  if (c->params.precision == REC_PREC_MIXED)
+    k_state_init<true, false><<<c->grid, NT, 0, c->stream>>>(a, k.nH / S, k.Tg, nullptr, 1);
+  else k_state_init<false, false><<<c->grid, NT, 0, c->stream>>>(a, k.nH / S, k.Tg, nullptr, 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_refresh(c, z);
@@ -611,15 +653,73 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
     }
     k_substep_begin<<<1, 32, 0, c->stream>>>(c->sc, k, (double)c->n3);
     for (int it = 0; it < kNewtonMaxPasses; ++it) {
-      if (mixed) k_newton<true><<<c->grid, NT, 0, c->stream>>>(a);
-      else k_newton<false><<<c->grid, NT, 0, c->stream>>>(a);
+      if (mixed) k_newton<true, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
+      else k_newton<false, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
     }
-    if (mixed) k_final<true><<<c->grid, NT, 0, c->stream>>>(a, st);
-    else k_final<false><<<c->grid, NT, 0, c->stream>>>(a, st);
+    if (mixed) k_final<true, false><<<c->grid, NT, 0, c->stream>>>(a, st, nullptr, 1);
+    else k_final<false, false><<<c->grid, NT, 0, c->stream>>>(a, st, nullptr, 1);
   }
   return cudaGetLastError();
 }
 
+
+// ------------------------------------------------------- batched contexts
+// One launch per pass over all boxes of the context (grid = the boxes' pass
+// blocks); each box keeps its own sums, lambda, Newton state and statistics.
+namespace {
+PassArgs batch_args(rec_ctx* c, const StepCoef& k) {
+  PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.part = c->part;
+  a.k = k;
+  return a;
+}
+}  // namespace
+
+cudaError_t launch_refresh_batch(rec_ctx* c, double z) {
+  StepCoef k = step_coef(c->cosmo, c->params, z + 1e-6 * (1.0 + z), z, 0);
+  PassArgs a = batch_args(c, k);
+  GroupTimer t(c, kTOther, 1);
+  if (c->params.precision == REC_PREC_MIXED) k_refresh<true, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, c->bx, c->n_boxes);
+  else k_refresh<false, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, c->bx, c->n_boxes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_init_batch(rec_ctx* c, double z) {
+  StepCoef k = step_coef(c->cosmo, c->params, z + 1e-6 * (1.0 + z), z, 0);
+  PassArgs a = batch_args(c, k);
+  double S = saha_S(k.Tg);
+  {
+    GroupTimer t(c, kTOther, 1);
+    if (c->params.precision == REC_PREC_MIXED)
+      k_state_init<true, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, k.nH / S, k.Tg, c->bx, c->n_boxes);
+    else k_state_init<false, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, k.nH / S, k.Tg, c->bx, c->n_boxes);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_refresh_batch(c, z);
+}
+
+cudaError_t launch_rec_step_batch(rec_ctx* c, double z_from, double z_to, rec_stats* st) {
+  const int ns = c->params.n_sub;
+  const bool mixed = c->params.precision == REC_PREC_MIXED;
+  const double ya = std::log1p(z_from), yb = std::log1p(z_to);
+  GroupTimer t(c, kTStep, ns * (kNewtonMaxPasses + 2));
+  for (int s = 0; s < ns; ++s) {
+    double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
+    double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
+    StepCoef k = step_coef(c->cosmo, c->params, za, zb, s == ns - 1);
+    PassArgs a = batch_args(c, k);
+    k_substep_begin_batch<<<1, kMaxBoxes, 0, c->stream>>>(c->bx, c->n_boxes, k);
+    for (int it = 0; it < kNewtonMaxPasses; ++it) {
+      if (mixed) k_newton<true, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, c->bx, c->n_boxes);
+      else k_newton<false, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, c->bx, c->n_boxes);
+    }
+    if (mixed) k_final<true, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, st, c->bx, c->n_boxes);
+    else k_final<false, true><<<c->tot_pblk, NT, 0, c->stream>>>(a, st, c->bx, c->n_boxes);
+  }
+  return cudaGetLastError();
+}
 
 // ------------------------------------------------------- allocation-free step
 // The same refresh + Newton + final passes as rec_refresh followed by rec_step
@@ -707,7 +807,7 @@ rec_status launch_rec_step_noalloc(const rec_params& p, const rec_box& b, double
   if (e != cudaSuccess) { *why = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e); return REC_ECUDA; }
   // sums and emission weights of the incoming state at z_from (as rec_refresh)
   a.k = step_coef(cosmo, p, z_from + 1e-6 * (1.0 + z_from), z_from, 0);
-  k_refresh<false><<<grid, NT, 0, stream>>>(a);
+  k_refresh<false, false><<<grid, NT, 0, stream>>>(a, nullptr, 1);
   const int ns = p.n_sub;
   const double ya = std::log1p(z_from), yb = std::log1p(z_to);
   for (int s = 0; s < ns; ++s) {
@@ -715,8 +815,8 @@ rec_status launch_rec_step_noalloc(const rec_params& p, const rec_box& b, double
     double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
     a.k = step_coef(cosmo, p, za, zb, s == ns - 1);
     k_substep_begin<<<1, 32, 0, stream>>>(sc, a.k, (double)n3);
-    for (int it = 0; it < kNewtonMaxPasses; ++it) k_newton<false><<<grid, NT, 0, stream>>>(a);
-    k_final<false><<<grid, NT, 0, stream>>>(a, st);
+    for (int it = 0; it < kNewtonMaxPasses; ++it) k_newton<false, false><<<grid, NT, 0, stream>>>(a, nullptr, 1);
+    k_final<false, false><<<grid, NT, 0, stream>>>(a, st, nullptr, 1);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) { *why = std::string("launch: ") + cudaGetErrorString(e); return REC_ECUDA; }

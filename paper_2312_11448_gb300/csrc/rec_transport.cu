@@ -30,6 +30,7 @@
 // binary64 for the FP64 form, so its integer results are reproducible.
 
 #include <cmath>
+#include <cstring>
 
 #include "rec_internal.cuh"
 #include "rec_reduce.cuh"
@@ -310,12 +311,10 @@ __device__ __forceinline__ uint32_t sys_floor(uint64_t N, uint64_t pre, uint64_t
 // range, so a warp of 32 consecutive packets finds its first cell with one
 // load) and the packets per super-tile (the capacity of its march-queue bucket).
 template <class R>
-__global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, uint64_t n_packets, DevScalars* sc,
-                                                     const unsigned long long* partQ, uint32_t* P, uint32_t* first,
-                                                     Tiles tl, unsigned long long* bcap) {
-  const R rmax = (R)sc->rmax;
-  const uint64_t S = sc->sumQ, u = sc->alloc_u;
-  const int64_t c0 = (int64_t)blockIdx.x * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+__device__ __forceinline__ void alloc_prefix_block(const R* emis, int64_t n3, uint64_t n_packets, uint64_t S,
+                                                   uint64_t u, R rmax, uint64_t pre_block, int64_t c0, uint32_t* P,
+                                                   uint32_t* first, const Tiles& tl, uint32_t bk0,
+                                                   unsigned long long* bcap) {
   uint64_t Q[kAllocItems];
   uint64_t acc = 0;
   {
@@ -336,7 +335,7 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
     for (int k = 0; k < kAllocItems; ++k) out[k] = 0u;
   } else {
     uint64_t rem;
-    uint32_t pk = sys_floor(n_packets, partQ[blockIdx.x] + incl - acc, u, S, &rem);
+    uint32_t pk = sys_floor(n_packets, pre_block + incl - acc, u, S, &rem);
     uint32_t bk = 0xffffffffu, bcount = 0;
 #pragma unroll
     for (int k = 0; k < kAllocItems; ++k) {
@@ -347,7 +346,7 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
       const uint32_t p1 = pk + (uint32_t)dq;
       if (p1 > pk && c0 + k < n3) {
         for (uint32_t w = (pk + 31u) >> 5; 32ull * w < p1; ++w) first[w] = (uint32_t)(c0 + k);
-        const uint32_t b = tl.of((uint32_t)(c0 + k));
+        const uint32_t b = bk0 + tl.of((uint32_t)(c0 + k));
         if (b != bk) {
           if (bcount) atomicAdd(&bcap[bk], (unsigned long long)bcount);
           bk = b;
@@ -359,7 +358,7 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
     }
     if (bcount) atomicAdd(&bcap[bk], (unsigned long long)bcount);
   }
-  if (c0 + kAllocItems <= n3) {  // P is a 256-byte aligned allocation
+  if (c0 + kAllocItems <= n3 && (reinterpret_cast<uintptr_t>(P + c0) & 15u) == 0) {
     uint4* q = reinterpret_cast<uint4*>(P + c0);
 #pragma unroll
     for (int k = 0; k < kAllocItems / 4; ++k) q[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
@@ -370,6 +369,14 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
   }
 }
 
+template <class R>
+__global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, uint64_t n_packets, DevScalars* sc,
+                                                     const unsigned long long* partQ, uint32_t* P, uint32_t* first,
+                                                     Tiles tl, unsigned long long* bcap) {
+  const int64_t c0 = (int64_t)blockIdx.x * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+  alloc_prefix_block<R>(emis, n3, n_packets, sc->sumQ, sc->alloc_u, (R)sc->rmax, partQ[blockIdx.x], c0, P, first, tl,
+                        0u, bcap);
+}
 
 // One block: bucket capacities -> offsets (in place); fill counters cleared.
 __global__ void __launch_bounds__(1024) k_bucket_offsets(unsigned long long* bcap, unsigned long long* bfill, int nb) {
@@ -548,127 +555,188 @@ __device__ __forceinline__ void add_counters(DevScalars* sc, uint64_t ab, uint64
   }
 }
 
+// Batched contexts: per-box event counters of one block in shared memory
+// (absorbed, capped, crossings), added to the boxes' scalars at the block's end.
+struct BoxCounters {
+  unsigned long long v[3][kMaxBoxes];
+};
+__device__ __forceinline__ void box_counters_clear(BoxCounters& c, int B) {
+  for (int i = threadIdx.x; i < 3 * kMaxBoxes; i += blockDim.x) c.v[i / kMaxBoxes][i % kMaxBoxes] = 0ull;
+  __syncthreads();
+}
+__device__ __forceinline__ void box_counters_add(BoxCounters& c, int b, uint64_t ab, uint64_t cap, uint64_t cross) {
+  if (ab) atomicAdd(&c.v[0][b], (unsigned long long)ab);
+  if (cap) atomicAdd(&c.v[1][b], (unsigned long long)cap);
+  if (cross) atomicAdd(&c.v[2][b], (unsigned long long)cross);
+}
+__device__ __forceinline__ void box_counters_flush(BoxCounters& c, const BoxDev* bxs, int B) {
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    DevScalars* sc = bxs[b].sc;
+    if (c.v[0][b]) atomicAdd(&sc->absorbed, c.v[0][b]);
+    if (c.v[1][b]) atomicAdd(&sc->capped, c.v[1][b]);
+    if (c.v[2][b]) atomicAdd(&sc->crossings, c.v[2][b]);
+  }
+}
+
+// Last index i in [0, B) with key(i) <= v (key non-decreasing, key(0) <= v).
+template <class F>
+__device__ __forceinline__ int last_le(int B, uint64_t v, F key) {
+  int lo = 0, hi = B;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if ((uint64_t)key(mid) <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One box as the emission sees it: its fields, packet prefix and coarse index,
+// transport scalars, random stream, super-tiles and first queue bucket.
+template <class R>
+struct EmitBox {
+  const uint32_t* P;
+  const uint32_t* first;
+  uint32_t n3, n;
+  const typename Vec4<R>::T* vel;
+  const R* T;
+  uint32_t* tally;
+  R kappa, cth;
+  Stream strm;
+  Tiles tl;
+  uint32_t bk0;
+};
+
 // Emission: one packet per thread.  Packets resonant in their home cell are
-// tallied here; the others take their first step and are queued.
+// tallied here; the others take their first step and are queued.  One warp
+// emits the packets base .. base + 31 of one box (N packets).
 template <class R, bool P2>
-__global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
+__device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitBox<R>& e, uint32_t base, uint32_t N,
+                                          uint64_t& my_abs, uint64_t& my_cross) {
   using A = Ar<R>;
   using V = typename Vec4<R>::T;
   const int lane = threadIdx.x & 31;
-  const uint32_t N = __ldg(a.P + a.n3);  // packets actually allocated
-  const uint32_t n = (uint32_t)a.n;
-  const uint32_t n3 = (uint32_t)a.n3;
+  const uint32_t n = e.n, n3 = e.n3;
   const R one = (R)1, two = (R)2, zero = (R)0;
+  const uint32_t p = (uint32_t)base + lane;
+  const bool act = p < N;
+  // ---- cell of each packet: the coarse index gives the cell of the warp's
+  // first packet, then a 32-cell window of P resolves the rest with ballots
+  const uint32_t c0 = __ldg(e.first + (base >> 5));
+  const uint32_t Pc0 = __ldg(e.P + c0);
+  const uint32_t widx = c0 + 1u + lane;
+  const uint32_t wv = (widx <= n3) ? __ldg(e.P + widx) : 0xffffffffu;
+  // off = number of window entries <= p (the window is sorted): binary search
+  // over the 32 lane values with shuffles
+  uint32_t off = 0;
+#pragma unroll
+  for (uint32_t step = 16; step > 0; step >>= 1) {
+    const uint32_t probe = __shfl_sync(0xffffffffu, wv, (off + step - 1u) & 31u);
+    if (probe <= p) off += step;
+  }
+  const uint32_t w31 = __shfl_sync(0xffffffffu, wv, 31);  // every lane takes part
+  if (off == 31u && w31 <= p) off = 32u;
+  const uint32_t prev = __shfl_sync(0xffffffffu, wv, (off > 0 ? off - 1u : 0u) & 31u);
+  uint32_t cell = c0 + off, Pc = (off == 0) ? Pc0 : prev;
+  if (act && off >= 32) {
+    cell = upper_bound(e.P, c0 + 32u, n3, p) - 1u;
+    Pc = __ldg(e.P + cell);
+  }
+  bool home = false, queued = false;
+  Ray<R> r;
+  R nx = zero, ny = zero, nz = one;
+  if (act) {
+    const uint32_t j = p - Pc;
+    // (1) injection point uniform in the cell, frequency quantile
+    R f[3], uq;
+    Draws<R>::position(e.strm, cell, j, f, &uq);
+    // isotropic direction (Marsaglia 1972): candidate pairs t = 0, 1, ...
+    // (each Philox block is computed once for the pairs it holds)
+    {
+      typename Draws<R>::Block blk;
+      for (int t = 0; t < 32; ++t) {
+        R ua, ub;
+        if (Draws<R>::first_of_block(t)) blk = Draws<R>::block(e.strm, cell, j, t);
+        Draws<R>::pair_from(blk, t, &ua, &ub);
+        R v1 = A::sub(A::mul(two, ua), one), v2 = A::sub(A::mul(two, ub), one);
+        R s = A::add(A::mul(v1, v1), A::mul(v2, v2));
+        if (s < one && s > zero) {
+          R fac = A::mul(two, A::sqr(A::sub(one, s)));
+          nx = A::mul(v1, fac); ny = A::mul(v2, fac); nz = A::sub(one, A::mul(two, s));
+          break;
+        }
+      }
+    }
+    // emission frequency from the tabulated inverse CDF
+    R tq = A::mul(uq, (R)(a.M - 1));
+    int k = A::trunc(tq);
+    if (k > a.M - 2) k = a.M - 2;
+    R fr = A::sub(tq, (R)k);
+    R q0 = __ldg(a.quant + k), q1 = __ldg(a.quant + k + 1);
+    R xi = A::add(q0, A::mul(fr, A::sub(q1, q0)));
+    R vt = A::sqr(A::mul(__ldg(e.T + cell), e.cth));
+    r.knx = A::mul(e.kappa, nx); r.kny = A::mul(e.kappa, ny); r.knz = A::mul(e.kappa, nz);
+    V Uh = e.vel[cell];
+    R dh = A::add(A::add(A::mul(r.knx, Uh.x), A::mul(r.kny, Uh.y)), A::mul(r.knz, Uh.z));
+    r.u0 = A::add(A::mul(xi, vt), dh);
+    if (P2) {
+      r.ix = cell & (n - 1u); r.iy = (cell >> e.tl.lg) & (n - 1u); r.iz = cell >> (2u * e.tl.lg);
+    } else {
+      r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+    }
+    axis_setup<R>(nx, &r.tDx, &r.sx);
+    axis_setup<R>(ny, &r.tDy, &r.sy);
+    axis_setup<R>(nz, &r.tDz, &r.sz);
+    r.tMx = r.sx > 0 ? A::mul(A::sub(one, f[0]), r.tDx) : (r.sx < 0 ? A::mul(f[0], r.tDx) : A::inf());
+    r.tMy = r.sy > 0 ? A::mul(A::sub(one, f[1]), r.tDy) : (r.sy < 0 ? A::mul(f[1], r.tDy) : A::inf());
+    r.tMz = r.sz > 0 ? A::mul(A::sub(one, f[2]), r.tDz) : (r.sz < 0 ? A::mul(f[2], r.tDz) : A::inf());
+    r.kc = 0;
+    int res = march_cell<R, P2>(r, Uh, n);  // home cell (res == 2 impossible with kc = 0)
+    home = res == 1;
+    queued = res == 0;
+    my_cross += r.kc;
+    if (home) ++my_abs;
+  }
+  // warp-aggregated tally of the packets resonant at home (mostly one cell per warp)
+  const uint32_t key = home ? cell : 0xffffffffu;
+  const unsigned m = __match_any_sync(0xffffffffu, key);
+  if (home && lane == __ffs(m) - 1) atomicAdd(e.tally + cell, (uint32_t)__popc(m));
+  // queue the others after their first step, in their home super-tile's bucket
+  const unsigned qm = __ballot_sync(0xffffffffu, queued);
+  if (qm) {
+    const uint32_t bk = queued ? e.bk0 + e.tl.template at<P2>(cell) : 0xffffffffu;
+    const unsigned gm = __match_any_sync(0xffffffffu, bk) & qm;
+    unsigned long long qb = 0;
+    const int leader = __ffs(gm) - 1;
+    if (queued && lane == leader) qb = atomicAdd(&a.bfill[bk], (unsigned long long)__popc(gm));
+    qb = __shfl_sync(0xffffffffu, qb, leader < 0 ? 0 : leader);
+    if (queued) {
+      uint64_t slot = a.boff[bk] + qb + __popc(gm & ((1u << lane) - 1u));
+      uint32_t c1 = P2 ? (((r.iz << e.tl.lg) | r.iy) << e.tl.lg) | r.ix : (r.iz * n + r.iy) * n + r.ix;
+      V q0v, q1v, q2v;
+      q0v.x = bits_to<R>(c1); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
+      q1v.x = r.sx < 0 ? -r.tDx : r.tDx; q1v.y = r.sy < 0 ? -r.tDy : r.tDy; q1v.z = r.sz < 0 ? -r.tDz : r.tDz;
+      q1v.w = r.u0;
+      q2v.x = r.knx; q2v.y = r.kny; q2v.z = r.knz; q2v.w = zero;
+      a.queue[3 * slot] = q0v;
+      a.queue[3 * slot + 1] = q1v;
+      a.queue[3 * slot + 2] = q2v;
+    }
+  }
+}
+
+// Resident blocks per SM of the emission (register budget per thread).
+template <class R> constexpr int emit_occupancy() { return sizeof(R) == 4 ? 5 : 3; }
+
+template <class R, bool P2>
+__global__ void __launch_bounds__(TT, emit_occupancy<R>()) k_emit(TransportArgs<R> a) {
+  const EmitBox<R> e{a.P, a.first, (uint32_t)a.n3, (uint32_t)a.n, a.vel, a.T, a.tally, a.kappa, a.cth, a.strm, a.tl, 0u};
+  const uint32_t N = __ldg(a.P + a.n3);  // packets actually allocated
   uint64_t my_abs = 0, my_cross = 0;
   const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
   for (uint64_t base = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 32; base < N;
-       base += warps_total * 32) {
-    const uint32_t p = (uint32_t)base + lane;
-    const bool act = p < N;
-    // ---- cell of each packet: the coarse index gives the cell of the warp's
-    // first packet, then a 32-cell window of P resolves the rest with ballots
-    const uint32_t c0 = __ldg(a.first + (base >> 5));
-    const uint32_t Pc0 = __ldg(a.P + c0);
-    const uint32_t widx = c0 + 1u + lane;
-    const uint32_t wv = (widx <= n3) ? __ldg(a.P + widx) : 0xffffffffu;
-    // off = number of window entries <= p (the window is sorted): binary search
-    // over the 32 lane values with shuffles
-    uint32_t off = 0;
-#pragma unroll
-    for (uint32_t step = 16; step > 0; step >>= 1) {
-      const uint32_t probe = __shfl_sync(0xffffffffu, wv, (off + step - 1u) & 31u);
-      if (probe <= p) off += step;
-    }
-    const uint32_t w31 = __shfl_sync(0xffffffffu, wv, 31);  // every lane takes part
-    if (off == 31u && w31 <= p) off = 32u;
-    const uint32_t prev = __shfl_sync(0xffffffffu, wv, (off > 0 ? off - 1u : 0u) & 31u);
-    uint32_t cell = c0 + off, Pc = (off == 0) ? Pc0 : prev;
-    if (act && off >= 32) {
-      cell = upper_bound(a.P, c0 + 32u, n3, p) - 1u;
-      Pc = __ldg(a.P + cell);
-    }
-    bool home = false, queued = false;
-    Ray<R> r;
-    R nx = zero, ny = zero, nz = one;
-    if (act) {
-      const uint32_t j = p - Pc;
-      // (1) injection point uniform in the cell, frequency quantile
-      R f[3], uq;
-      Draws<R>::position(a.strm, cell, j, f, &uq);
-      // isotropic direction (Marsaglia 1972): candidate pairs t = 0, 1, ...
-      // (each Philox block is computed once for the pairs it holds)
-      {
-        typename Draws<R>::Block blk;
-        for (int t = 0; t < 32; ++t) {
-          R ua, ub;
-          if (Draws<R>::first_of_block(t)) blk = Draws<R>::block(a.strm, cell, j, t);
-          Draws<R>::pair_from(blk, t, &ua, &ub);
-          R v1 = A::sub(A::mul(two, ua), one), v2 = A::sub(A::mul(two, ub), one);
-          R s = A::add(A::mul(v1, v1), A::mul(v2, v2));
-          if (s < one && s > zero) {
-            R fac = A::mul(two, A::sqr(A::sub(one, s)));
-            nx = A::mul(v1, fac); ny = A::mul(v2, fac); nz = A::sub(one, A::mul(two, s));
-            break;
-          }
-        }
-      }
-      // emission frequency from the tabulated inverse CDF
-      R tq = A::mul(uq, (R)(a.M - 1));
-      int k = A::trunc(tq);
-      if (k > a.M - 2) k = a.M - 2;
-      R fr = A::sub(tq, (R)k);
-      R q0 = __ldg(a.quant + k), q1 = __ldg(a.quant + k + 1);
-      R xi = A::add(q0, A::mul(fr, A::sub(q1, q0)));
-      R vt = A::sqr(A::mul(__ldg(a.T + cell), a.cth));
-      r.knx = A::mul(a.kappa, nx); r.kny = A::mul(a.kappa, ny); r.knz = A::mul(a.kappa, nz);
-      V Uh = a.vel[cell];
-      R dh = A::add(A::add(A::mul(r.knx, Uh.x), A::mul(r.kny, Uh.y)), A::mul(r.knz, Uh.z));
-      r.u0 = A::add(A::mul(xi, vt), dh);
-      if (P2) {
-        r.ix = cell & (n - 1u); r.iy = (cell >> a.tl.lg) & (n - 1u); r.iz = cell >> (2u * a.tl.lg);
-      } else {
-        r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
-      }
-      axis_setup<R>(nx, &r.tDx, &r.sx);
-      axis_setup<R>(ny, &r.tDy, &r.sy);
-      axis_setup<R>(nz, &r.tDz, &r.sz);
-      r.tMx = r.sx > 0 ? A::mul(A::sub(one, f[0]), r.tDx) : (r.sx < 0 ? A::mul(f[0], r.tDx) : A::inf());
-      r.tMy = r.sy > 0 ? A::mul(A::sub(one, f[1]), r.tDy) : (r.sy < 0 ? A::mul(f[1], r.tDy) : A::inf());
-      r.tMz = r.sz > 0 ? A::mul(A::sub(one, f[2]), r.tDz) : (r.sz < 0 ? A::mul(f[2], r.tDz) : A::inf());
-      r.kc = 0;
-      int res = march_cell<R, P2>(r, Uh, n);  // home cell (res == 2 impossible with kc = 0)
-      home = res == 1;
-      queued = res == 0;
-      my_cross += r.kc;
-      if (home) ++my_abs;
-    }
-    // warp-aggregated tally of the packets resonant at home (mostly one cell per warp)
-    const uint32_t key = home ? cell : 0xffffffffu;
-    const unsigned m = __match_any_sync(0xffffffffu, key);
-    if (home && lane == __ffs(m) - 1) atomicAdd(a.tally + cell, (uint32_t)__popc(m));
-    // queue the others after their first step, in their home super-tile's bucket
-    const unsigned qm = __ballot_sync(0xffffffffu, queued);
-    if (qm) {
-      const uint32_t bk = queued ? a.tl.template at<P2>(cell) : 0xffffffffu;
-      const unsigned gm = __match_any_sync(0xffffffffu, bk) & qm;
-      unsigned long long qb = 0;
-      const int leader = __ffs(gm) - 1;
-      if (queued && lane == leader) qb = atomicAdd(&a.bfill[bk], (unsigned long long)__popc(gm));
-      qb = __shfl_sync(0xffffffffu, qb, leader < 0 ? 0 : leader);
-      if (queued) {
-        uint64_t slot = a.boff[bk] + qb + __popc(gm & ((1u << lane) - 1u));
-        uint32_t c1 = P2 ? (((r.iz << a.tl.lg) | r.iy) << a.tl.lg) | r.ix : (r.iz * n + r.iy) * n + r.ix;
-        V q0v, q1v, q2v;
-        q0v.x = bits_to<R>(c1); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
-        q1v.x = r.sx < 0 ? -r.tDx : r.tDx; q1v.y = r.sy < 0 ? -r.tDy : r.tDy; q1v.z = r.sz < 0 ? -r.tDz : r.tDz;
-        q1v.w = r.u0;
-        q2v.x = r.knx; q2v.y = r.kny; q2v.z = r.knz; q2v.w = zero;
-        a.queue[3 * slot] = q0v;
-        a.queue[3 * slot + 1] = q1v;
-        a.queue[3 * slot + 2] = q2v;
-      }
-    }
-  }
+       base += warps_total * 32)
+    emit_warp<R, P2>(a, e, (uint32_t)base, N, my_abs, my_cross);
   add_counters(a.sc, my_abs, 0, my_cross);
 }
 
@@ -677,16 +745,28 @@ __global__ void __launch_bounds__(TT) k_emit(TransportArgs<R> a) {
 // the warps advance through the super-tile buckets together and the cells
 // they touch stay close in memory; each warp refills its idle lanes from its
 // current chunk, so that lanes stay busy whatever the spread of path lengths.
-// Resident blocks per SM of the march (register budget per thread).
-template <class R> constexpr int march_occupancy() { return sizeof(R) == 4 ? 5 : 4; }
+// Resident blocks per SM of the march (register budget per thread; a batch
+// keeps the box of each lane's packet in registers).
+template <class R, bool MB> constexpr int march_occupancy() { return MB ? 4 : (sizeof(R) == 4 ? 5 : 4); }
 
 // P2: the box side is a power of two (cell index by shifts and masks).
-template <class R, bool P2>
-__global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArgs<R> a) {
+// MB: batched context; the lanes of a warp may hold packets of different boxes.
+template <class R, bool P2, bool MB>
+__global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(TransportArgs<R> a, const BoxDev* bxs, int B) {
   using V = typename Vec4<R>::T;
   const int lane = threadIdx.x & 31;
   const uint32_t n = (uint32_t)a.n;
   const uint32_t lg = P2 ? (uint32_t)(__ffs((int)n) - 1) : 0u;
+  __shared__ BoxCounters cnt;
+  if (MB) box_counters_clear(cnt, B);
+  // box of the lane's packet (batch) and of the open chunk
+  const V* lvel = a.vel;
+  uint32_t* ltally = a.tally;
+  uint32_t ln = n;
+  int lbox = -1, cbox = 0;
+  const V* cvel = a.vel;
+  uint32_t* ctally = a.tally;
+  uint32_t cn = n;
   const uint64_t n_chunks = a.cpre[a.nb];
   uint64_t chunk = 0;
   uint64_t pos = 0, end = 0;  // queue slots [pos, end) left in the current chunk
@@ -721,17 +801,33 @@ __global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArg
           pos = a.boff[lo] + k0;
           end = pos + min((uint64_t)kChunk, (uint64_t)(a.bfill[lo] - k0));
           have = true;
+          if (MB) {  // box of this bucket: last b with bk0 <= lo
+            cbox = last_le(B, lo, [&](int i) { return bxs[i].bk0; });
+            cvel = (const V*)bxs[cbox].vel4;
+            ctally = bxs[cbox].tally;
+            cn = bxs[cbox].n;
+          }
         }
         const uint32_t take = (uint32_t)min((uint64_t)__popc(idle), end - pos);
         const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
         if (((idle >> lane) & 1u) && rank < take) {
           const uint64_t slot = pos + rank;
           V q0v = a.queue[3 * slot], q1v = a.queue[3 * slot + 1], q2v = a.queue[3 * slot + 2];
+          if (MB) {
+            if (lbox != cbox) {  // counters of the previous box to shared memory
+              if (lbox >= 0) box_counters_add(cnt, lbox, my_abs, my_cap, my_cross);
+              my_abs = my_cap = my_cross = 0;
+              lbox = cbox;
+            }
+            lvel = cvel;
+            ltally = ctally;
+            ln = cn;
+          }
           cell = to_bits<R>(q0v.x);
           if (P2) {
             r.ix = cell & (n - 1u); r.iy = (cell >> lg) & (n - 1u); r.iz = cell >> (2u * lg);
           } else {
-            r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
+            r.ix = cell % ln; r.iy = (cell / ln) % ln; r.iz = cell / (ln * ln);
           }
           r.tMx = q0v.y; r.tMy = q0v.z; r.tMz = q0v.w;
           r.sx = q1v.x < (R)0 ? -1 : 1; r.tDx = fabs(q1v.x);
@@ -740,7 +836,7 @@ __global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArg
           r.u0 = q1v.w;
           r.knx = q2v.x; r.kny = q2v.y; r.knz = q2v.z;
           r.kc = 1;  // the step out of the home cell
-          Uc = a.vel[cell];
+          Uc = lvel[cell];
           active = true;
         }
         // lanes taken this round leave the idle set (the lowest `take` idle lanes)
@@ -752,19 +848,24 @@ __global__ void __launch_bounds__(TT, march_occupancy<R>()) k_march(TransportArg
     }
     if (!__any_sync(0xffffffffu, active)) break;  // no packet left in the warp
     if (active) {
-      int res = march_cell<R, P2>(r, Uc, n);
+      int res = march_cell<R, P2>(r, Uc, ln);
       if (res == 0) {
-        cell = P2 ? (((r.iz << lg) | r.iy) << lg) | r.ix : (r.iz * n + r.iy) * n + r.ix;
-        Uc = a.vel[cell];
+        cell = P2 ? (((r.iz << lg) | r.iy) << lg) | r.ix : (r.iz * ln + r.iy) * ln + r.ix;
+        Uc = lvel[cell];
       } else {
         active = false;
         my_cross += r.kc - 1;  // the first crossing was counted at emission
-        if (res == 1) { atomicAdd(a.tally + cell, 1u); ++my_abs; }
+        if (res == 1) { atomicAdd(ltally + cell, 1u); ++my_abs; }
         else ++my_cap;
       }
     }
   }
-  add_counters(a.sc, my_abs, my_cap, my_cross);
+  if (MB) {
+    if (lbox >= 0) box_counters_add(cnt, lbox, my_abs, my_cap, my_cross);
+    box_counters_flush(cnt, bxs, B);
+  } else {
+    add_counters(a.sc, my_abs, my_cap, my_cross);
+  }
 }
 
 __global__ void k_transport_end(DevScalars* sc, rec_stats* st) {
@@ -824,18 +925,248 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.cpre = c->cpre;
   {
     GroupTimer t(c, kTEmit, 2);
-    if (p2) k_emit<R, true><<<c->transport_blocks, TT, 0, c->stream>>>(a);
-    else k_emit<R, false><<<c->transport_blocks, TT, 0, c->stream>>>(a);
+    const int eb = c->sm_count * emit_occupancy<R>();
+    if (p2) k_emit<R, true><<<eb, TT, 0, c->stream>>>(a);
+    else k_emit<R, false><<<eb, TT, 0, c->stream>>>(a);
     k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->sc);
   }
   {
     GroupTimer t(c, kTMarch, 1);
-    if (p2) k_march<R, true><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
-    else k_march<R, false><<<c->sm_count * march_occupancy<R>(), TT, 0, c->stream>>>(a);
+    const int mb = c->sm_count * march_occupancy<R, false>();
+    if (p2) k_march<R, true, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1);
+    else k_march<R, false, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1);
   }
   {
     GroupTimer t(c, kTEnd, 1);
     k_transport_end<<<1, 32, 0, c->stream>>>(c->sc, st);
+  }
+  return cudaGetLastError();
+}
+
+// ---- batched contexts: every phase is one launch over all boxes ------------------
+
+// Allocation blocks: kAllocChunk cells of one box each; box of block g = last b
+// with ablk0 <= g.
+__device__ __forceinline__ int alloc_box(const BoxDev* bxs, int B, uint32_t g) {
+  return last_le(B, g, [&](int i) { return bxs[i].ablk0; });
+}
+
+template <class R>
+__global__ void __launch_bounds__(AT) k_alloc_max_batch(const BoxDev* bxs, int B, DevScalars* gsc, double* part) {
+  const int b = alloc_box(bxs, B, blockIdx.x);
+  const BoxDev& d = bxs[b];
+  const int64_t c0 = (int64_t)(blockIdx.x - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+  R v[kAllocItems];
+  load_items<R>((const R*)d.emis, c0, d.n3, v);
+  double m = 0.0;
+  int bad = 0;
+#pragma unroll
+  for (int k = 0; k < kAllocItems; ++k) {
+    if (c0 + k >= d.n3) continue;
+    double r = (double)v[k];
+    if (!(r >= 0.0) || isinf(r)) bad = 1;
+    else m = fmax(m, r);
+  }
+  bad = __syncthreads_or(bad);
+  double bm = block_max<AT>(m);
+  if (threadIdx.x == 0) {
+    part[(size_t)blockIdx.x * kMaxSums + 0] = bm;
+    part[(size_t)blockIdx.x * kMaxSums + 1] = bad ? 1.0 : 0.0;
+  }
+  if (!last_block_done(&gsc->counter)) return;
+  // one warp per box: maximum over the box's blocks
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < B; i += AT / 32) {
+    const uint32_t g0 = bxs[i].ablk0;
+    const uint32_t g1 = (i + 1 < B) ? bxs[i + 1].ablk0 : gridDim.x;
+    double mx = 0.0, anybad = 0.0;
+    for (uint32_t g = g0 + lane; g < g1; g += 32) {
+      mx = fmax(mx, __ldcg(part + (size_t)g * kMaxSums));
+      anybad = fmax(anybad, __ldcg(part + (size_t)g * kMaxSums + 1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      anybad = fmax(anybad, __shfl_xor_sync(0xffffffffu, anybad, o));
+    }
+    if (lane == 0) {
+      DevScalars* sc = bxs[i].sc;
+      sc->rmax = anybad > 0.0 ? 0.0 : mx;
+      sc->flags &= ~(2 | 4);
+      if (anybad > 0.0) sc->flags |= 4;
+    }
+  }
+  if (threadIdx.x == 0) gsc->counter = 0;
+}
+
+template <class R>
+__global__ void __launch_bounds__(AT) k_alloc_sum_batch(const BoxDev* bxs, int B, uint32_t k0, uint32_t k1,
+                                                        DevScalars* gsc, unsigned long long* partQ) {
+  const int b = alloc_box(bxs, B, blockIdx.x);
+  const BoxDev& d = bxs[b];
+  const R rmax = (R)d.sc->rmax;
+  uint64_t acc = 0;
+  if (rmax > (R)0) {
+    const int64_t c0 = (int64_t)(blockIdx.x - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+    R v[kAllocItems];
+    load_items<R>((const R*)d.emis, c0, d.n3, v);
+#pragma unroll
+    for (int k = 0; k < kAllocItems; ++k) acc += quantised<R>(v[k], rmax);
+  }
+  uint64_t incl;
+  uint64_t tot = block_scan_incl(acc, &incl);
+  if (threadIdx.x == 0) partQ[blockIdx.x] = tot;
+  if (!last_block_done(&gsc->alloc_counter)) return;
+  // one warp per box: exclusive scan of its block sums (in place), the
+  // systematic-sampling offset and the box's packet total
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < B; i += AT / 32) {
+    const BoxDev& e = bxs[i];
+    const uint32_t g0 = e.ablk0;
+    const uint32_t g1 = (i + 1 < B) ? bxs[i + 1].ablk0 : gridDim.x;
+    uint64_t run = 0;
+    for (uint32_t gb = g0; gb < g1; gb += 32) {
+      const uint32_t g = gb + lane;
+      uint64_t q = g < g1 ? __ldcg(&partQ[g]) : 0ull, v = q;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (g < g1) partQ[g] = run + v - q;
+      run += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) {
+      DevScalars* sc = e.sc;
+      const uint64_t sumQ = run;
+      U4 r = draw(Stream{k0, k1, (uint32_t)i}, 0u, 0u, kAllocBlock);
+      uint64_t w = ((uint64_t)r.b << 32) | r.a;
+      uint64_t npk = (sumQ > 0) ? e.npk : 0;
+      sc->sumQ = sumQ;
+      sc->alloc_u = sumQ > 0 ? w % sumQ : 0;
+      e.P[e.n3] = (uint32_t)npk;
+      sc->emitted = npk;
+      sc->absorbed = 0;
+      sc->capped = 0;
+      sc->crossings = 0;
+      sc->qtail = 0;
+      if (sumQ == 0 && e.npk > 0) sc->flags |= 4;
+    }
+  }
+  if (threadIdx.x == 0) gsc->alloc_counter = 0;
+}
+
+template <class R>
+__global__ void __launch_bounds__(AT) k_alloc_prefix_batch(const BoxDev* bxs, int B, const unsigned long long* partQ,
+                                                           unsigned long long* bcap) {
+  const int b = alloc_box(bxs, B, blockIdx.x);
+  const BoxDev& d = bxs[b];
+  const DevScalars* sc = d.sc;
+  const int64_t c0 = (int64_t)(blockIdx.x - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+  alloc_prefix_block<R>((const R*)d.emis, d.n3, d.npk, sc->sumQ, sc->alloc_u, (R)sc->rmax, partQ[blockIdx.x], c0,
+                        d.P, d.first, Tiles{d.n, d.nt, d.lg}, d.bk0, bcap);
+}
+
+// Emission over the batch packet space (each box padded to a multiple of 32,
+// so a warp's 32 packets belong to one box).
+template <class R>
+__global__ void __launch_bounds__(TT, emit_occupancy<R>()) k_emit_batch(TransportArgs<R> a, const BoxDev* bxs,
+                                                                        const BoxStep* bst, int B, uint64_t tot_pk) {
+  using V = typename Vec4<R>::T;
+  __shared__ BoxCounters cnt;
+  box_counters_clear(cnt, B);
+  uint64_t my_abs = 0, my_cross = 0;
+  int cur = -1;
+  const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
+  for (uint64_t gbase = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 32; gbase < tot_pk;
+       gbase += warps_total * 32) {
+    const int b = last_le(B, gbase, [&](int i) { return bxs[i].pk0; });
+    if (b != cur) {
+      if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
+      my_abs = my_cross = 0;
+      cur = b;
+    }
+    const BoxDev& d = bxs[b];
+    const uint32_t N = __ldg(d.P + d.n3);  // packets actually allocated to this box
+    const uint64_t base = gbase - d.pk0;
+    if (base >= N) continue;  // padding of the packet space (uniform over the warp)
+    const EmitBox<R> e{d.P, d.first, (uint32_t)d.n3, d.n, (const V*)d.vel4, (const R*)d.T, d.tally,
+                       (R)bst[b].kappa, (R)bst[b].cth, Stream{a.strm.k0, a.strm.k1, (uint32_t)b},
+                       Tiles{d.n, d.nt, d.lg}, d.bk0};
+    if (d.p2) emit_warp<R, true>(a, e, (uint32_t)base, N, my_abs, my_cross);
+    else emit_warp<R, false>(a, e, (uint32_t)base, N, my_abs, my_cross);
+  }
+  if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
+  box_counters_flush(cnt, bxs, B);
+}
+
+struct BoxStepArgs {
+  BoxStep s[kMaxBoxes];
+};
+__global__ void k_set_box_step(BoxStepArgs p, BoxStep* out, int B) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) out[b] = p.s[b];
+}
+
+__global__ void k_transport_end_batch(const BoxDev* bxs, int B, const unsigned long long* bfill, rec_stats* st) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const BoxDev& d = bxs[b];
+    DevScalars* sc = d.sc;
+    unsigned long long q = 0;
+    const uint32_t nb = d.nt * d.nt * d.nt;
+    for (uint32_t k = 0; k < nb; ++k) q += bfill[d.bk0 + k];
+    sc->qtail = q;
+    sc->tally_total += sc->absorbed;
+    if (sc->capped) sc->flags |= 2;
+    if (st) {
+      st[b].emitted = sc->emitted;
+      st[b].absorbed = sc->absorbed;
+      st[b].capped = sc->capped;
+      st[b].crossings = sc->crossings;
+      st[b].queued = q;
+      st[b].flags = sc->flags;
+    }
+  }
+}
+
+template <class R>
+cudaError_t run_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
+  const int B = c->n_boxes;
+  const uint32_t k0 = (uint32_t)c->params.seed, k1 = (uint32_t)(c->params.seed >> 32) ^ (uint32_t)step;
+  const int nb = c->tot_buckets;
+  {
+    GroupTimer t(c, kTAlloc, 5);
+    BoxStepArgs bs;
+    for (int b = 0; b < B; ++b) transport_scalars(c->cosmo, (int)c->hbx[b].n, z, &bs.s[b].kappa, &bs.s[b].cth);
+    k_set_box_step<<<1, kMaxBoxes, 0, c->stream>>>(bs, c->bstep, B);
+    k_alloc_max_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, c->gsc, c->part);
+    k_alloc_sum_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, k0, k1, c->gsc, c->partQ);
+    cudaMemsetAsync(c->bcap, 0, sizeof(unsigned long long) * nb, c->stream);
+    k_alloc_prefix_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, c->partQ, c->bcap);
+    k_bucket_offsets<<<1, 1024, 0, c->stream>>>(c->bcap, c->bfill, nb);
+  }
+  TransportArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.quant = (const R*)c->quant;
+  a.M = c->params.n_quantiles;
+  a.strm = Stream{k0, k1, 0u};
+  a.sc = c->gsc;
+  a.queue = (typename Vec4<R>::T*)c->queue;
+  a.nb = nb;
+  a.boff = c->bcap;
+  a.bfill = c->bfill;
+  a.cpre = c->cpre;
+  {
+    GroupTimer t(c, kTEmit, 2);
+    k_emit_batch<R><<<c->sm_count * emit_occupancy<R>(), TT, 0, c->stream>>>(a, c->bx, c->bstep, B, c->tot_pk);
+    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->gsc);
+  }
+  {
+    GroupTimer t(c, kTMarch, 1);
+    k_march<R, false, true><<<c->sm_count * march_occupancy<R, true>(), TT, 0, c->stream>>>(a, c->bx, B);
+  }
+  {
+    GroupTimer t(c, kTEnd, 1);
+    k_transport_end_batch<<<1, kMaxBoxes, 0, c->stream>>>(c->bx, B, c->bfill, st);
   }
   return cudaGetLastError();
 }
@@ -845,6 +1176,11 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
 cudaError_t launch_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   if (c->params.precision == REC_PREC_MIXED) return run_transport<float>(c, step, z, st);
   return run_transport<double>(c, step, z, st);
+}
+
+cudaError_t launch_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
+  if (c->params.precision == REC_PREC_MIXED) return run_transport_batch<float>(c, step, z, st);
+  return run_transport_batch<double>(c, step, z, st);
 }
 
 }  // namespace rec

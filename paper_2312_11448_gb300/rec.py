@@ -117,6 +117,112 @@ def objective(zs, Xe, objective=1, z_star=1100.0, **kw):
     return J.value, dJ
 
 
+class Batch:
+    """Several boxes in one context (n_boxes > 1): every phase of a call is one
+    launch over all boxes.  boxes: list of (n, delta, U, n_packets).  Fields live
+    in per-box torch CUDA tensors; statistics have one record per box."""
+
+    def __init__(self, boxes, precision="mixed", mixing="tally", seed=1, n_sub=1, quantiles=None, stream=None,
+                 **cosmo):
+        import torch
+        if not torch.cuda.is_available():
+            raise RecError("a CUDA device is required (there is no CPU fallback)")
+        if len(boxes) < 2:
+            raise RecError("a batch needs at least two boxes (use Box for one)")
+        self.torch = torch
+        self.precision = precision
+        self.mixing = mixing
+        fdt = torch.float32 if precision == "mixed" else torch.float64
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream or torch.cuda.current_stream(dev)
+        self.n = [int(b[0]) for b in boxes]
+        self.n_packets = [int(b[3]) for b in boxes]
+        self.delta, self.vel4, self.x, self.T, self.tally, self.emis = [], [], [], [], [], []
+        with torch.cuda.stream(self.stream):
+            for (n, delta, U, _npk) in boxes:
+                n3 = int(n) ** 3
+                d = torch.as_tensor(np.asarray(delta).ravel(), dtype=torch.float64)
+                if d.numel() != n3:
+                    raise RecError("delta must have n^3 cells")
+                u = torch.as_tensor(np.asarray(U).reshape(-1, 3), dtype=torch.float64)
+                v4 = torch.zeros(n3, 4, dtype=torch.float64)
+                v4[:, :3] = u
+                self.delta.append(d.to(dev, fdt))
+                self.vel4.append(v4.to(dev, fdt).contiguous())
+                self.x.append(torch.zeros(n3, dtype=torch.float64, device=dev))
+                self.T.append(torch.zeros(n3, dtype=fdt, device=dev))
+                self.tally.append(torch.zeros(n3, dtype=torch.int32, device=dev))
+                self.emis.append(torch.zeros(n3, dtype=fdt, device=dev))
+            self._stats = torch.zeros(len(boxes), C.sizeof(Stats), dtype=torch.uint8, device=dev)
+        self._params, self._q = make_params(precision, mixing, seed, n_sub, quantiles, **cosmo)
+        descs = (BoxDesc * len(boxes))()
+        for i in range(len(boxes)):
+            descs[i] = BoxDesc(self.n[i], self.delta[i].data_ptr(), self.vel4[i].data_ptr(), self.x[i].data_ptr(),
+                               self.T[i].data_ptr(), self.tally[i].data_ptr(), self.emis[i].data_ptr(),
+                               self.n_packets[i])
+        ctx = C.c_void_p()
+        self.stream.synchronize()
+        rc = lib().rec_init(C.byref(self._params), descs, len(boxes), C.c_void_p(self.stream.cuda_stream),
+                            C.byref(ctx))
+        if rc != REC_OK:
+            raise RecError(f"rec_init: {lib().rec_last_error(None).decode()} (status {rc})")
+        self.ctx = ctx
+
+    def _check(self, rc, what):
+        if rc != REC_OK:
+            raise RecError(f"{what}: {lib().rec_last_error(self.ctx).decode()} (status {rc})")
+
+    def state_init(self, z):
+        self._check(lib().rec_state_init(self.ctx, z), "rec_state_init")
+
+    def refresh(self, z):
+        self._check(lib().rec_refresh(self.ctx, z), "rec_refresh")
+
+    def transport(self, step, z):
+        self._check(lib().lya_transport(self.ctx, int(step), z, C.c_void_p(self._stats.data_ptr())), "lya_transport")
+
+    def step(self, step, z_from, z_to):
+        self._check(lib().rec_step(self.ctx, int(step), z_from, z_to, C.c_void_p(self._stats.data_ptr())), "rec_step")
+
+    def timing(self, enable=True):
+        self._check(lib().rec_timing(self.ctx, 1 if enable else 0), "rec_timing")
+
+    def kernel_times(self) -> dict:
+        ms = (C.c_double * 7)()
+        ln = (C.c_int64 * 7)()
+        self._check(lib().rec_kernel_times(self.ctx, ms, ln), "rec_kernel_times")
+        return {g: (ms[i], ln[i]) for i, g in enumerate(Box.TIMER_GROUPS)}
+
+    def stats(self) -> list:
+        """One statistics record per box."""
+        self.stream.synchronize()
+        return [_stats_dict(Stats.from_buffer_copy(row.tobytes())) for row in self._stats.cpu().numpy()]
+
+    def tally_np(self, b) -> np.ndarray:
+        self.stream.synchronize()
+        return self.tally[b].cpu().numpy().view(np.uint32)
+
+    def host(self, name, b) -> np.ndarray:
+        self.stream.synchronize()
+        return getattr(self, name)[b].cpu().numpy()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().rec_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stats_dict(s) -> dict:
+    return dict(emitted=s.emitted, absorbed=s.absorbed, capped=s.capped, crossings=s.crossings, queued=s.queued,
+                X_e=s.X_e, lam=s.lambda_, C=s.C_mix, S1s=s.S1s, newton_passes=s.newton_passes, flags=s.flags)
+
+
 class Box:
     """One periodic box and its context.  Fields live in torch CUDA tensors."""
 
@@ -229,11 +335,7 @@ class Box:
         raw = self._stats.cpu().numpy()
         out = []
         for row in raw:
-            s = Stats.from_buffer_copy(row.tobytes())
-            out.append(dict(emitted=s.emitted, absorbed=s.absorbed, capped=s.capped, crossings=s.crossings,
-                            queued=s.queued,
-                            X_e=s.X_e, lam=s.lambda_, C=s.C_mix, S1s=s.S1s, newton_passes=s.newton_passes,
-                            flags=s.flags))
+            out.append(_stats_dict(Stats.from_buffer_copy(row.tobytes())))
         return out
 
     def tally_np(self) -> np.ndarray:
