@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prep", type=int, default=S0, help="untimed steps before the warm-up (profiling: 0)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-box measurement")
     return ap.parse_args()
 
 
@@ -127,9 +128,12 @@ def fields_of(cfg, seed):
 
 
 def make_box(cfg, precision, seed):
+    import torch
     from paper_2312_11448_gb300 import rec
     delta, U = fields_of(cfg, seed)
-    return rec.Box(cfg.n, delta, U, cfg.n_packets, precision=precision, mixing="tally", seed=seed), delta, U
+    # a non-default stream, so that steps can also be captured as CUDA graphs
+    return rec.Box(cfg.n, delta, U, cfg.n_packets, precision=precision, mixing="tally", seed=seed,
+                   stream=torch.cuda.Stream()), delta, U
 
 
 def advance(box, zs, s_from, s_to):
@@ -165,9 +169,12 @@ def algorithmic_bytes(precision, n3, emitted, queued, crossings, newton_passes):
     return dict(emit=emit, march=march, rec_step=step, alloc=alloc)
 
 
-def time_form(cfg, zs, precision, W, K, seed, dist, clocks, prep=S0):
+def time_form(cfg, zs, precision, W, K, seed, dist, clocks, prep=S0, graph=False):
     import torch
+    from paper_2312_11448_gb300 import tune
     box, delta, U = make_box(cfg, precision, seed)
+    # transport tuning from the committed autotuner table, when it has this workload
+    tuned = tune.apply_table(box, tune.workload_key(cfg.n, cfg.n_packets, precision))
     box.state_init(zs[0])
     advance(box, zs, 0, prep)
     s_timed = prep + W
@@ -203,7 +210,24 @@ def time_form(cfg, zs, precision, W, K, seed, dist, clocks, prep=S0):
         raise RuntimeError(f"{precision} form: invalid state (flags={flags}, X_e={st[-1]['X_e']}, emitted={emitted})")
     ab = algorithmic_bytes(precision, box.n3, emitted, queued, crossings, passes)
     out = dict(ms=ms, kt=kt, emitted=emitted, queued=queued, crossings=crossings, passes=passes, flags=flags, ab=ab,
-               Xe=st[-1]["X_e"], box=box, delta=delta, U=U)
+               Xe=st[-1]["X_e"], box=box, delta=delta, U=U,
+               tuning=dict(box.tuning(), source="autotuner table" if tuned else "defaults"))
+    if graph:
+        # the next K steps as one CUDA graph launch per step (rec_graph_step)
+        s0 = s_timed + K
+        box.graph_step(s0, zs[s0], zs[s0 + 1])  # instantiates the executable graph
+        s0 += 1
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(K):
+            s = s0 + k
+            box.graph_step(s, zs[s], zs[s + 1], slot=k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["graph_ms"] = e0.elapsed_time(e1)
+        gst = box.stats_all()[:K]
+        if any(r["flags"] & 4 for r in gst) or not math.isfinite(gst[-1]["X_e"]):
+            raise RuntimeError("graph steps: invalid state")
     return out
 
 
@@ -236,6 +260,65 @@ def time_e2e(cfg, zs, res, K):
     h2d = h_delta.numel() * h_delta.element_size() + h_vel.numel() * h_vel.element_size()
     d2h = h_x.numel() * h_x.element_size() + h_T.numel() * h_T.element_size()
     return ms, h2d, d2h
+
+
+def time_batched(W, K, prep=60, n_boxes=64):
+    """The batched workload: 64 boxes with sides uniform in {32,48,64,96,128},
+    sigma_lnrho uniform in [0.1, 1.5], 1e6 packets per 32^3 scaled by volume,
+    mixed form, tally mixing, z 1600 -> 700 in 200 steps; one context, one
+    launch per phase for all boxes.  Timed after `prep` + W untimed steps."""
+    import torch
+    from paper_2312_11448_gb300 import rec
+    from paper_2312_11448_gb300.inputs import batched_configs, make_box as fields, z_schedule
+    cfgs = batched_configs(7, n_boxes)
+    boxes = []
+    for i, c in enumerate(cfgs):
+        d, U = fields(c, seed=100 + i)
+        boxes.append((c.n, d, U, c.n_packets))
+    zs = z_schedule(cfgs[0].z_start, cfgs[0].z_end, cfgs[0].n_steps)
+    batch = rec.Batch(boxes, precision="mixed", mixing="tally", seed=7)
+    del boxes
+    from paper_2312_11448_gb300 import tune
+    tuned = tune.apply_table(batch, tune.batch_key(n_boxes, "mixed"))
+    batch.state_init(zs[0])
+    for s in range(prep + W):
+        batch.transport(s, zs[s])
+        batch.step(s, zs[s], zs[s + 1])
+    batch.timing(True)
+    stream = batch.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    emitted = 0
+    for k in range(K):
+        s = prep + W + k
+        batch.transport(s, zs[s])
+        batch.step(s, zs[s], zs[s + 1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = batch.kernel_times()
+    st = batch.stats()
+    emitted = sum(r["emitted"] for r in st)
+    flags = 0
+    for r in st:
+        flags |= r["flags"]
+    cells = sum(c.n ** 3 for c in cfgs)
+    tuning = batch.tuning()
+    batch.close()
+    torch.cuda.empty_cache()
+    if flags & 4 or emitted < sum(c.n_packets for c in cfgs):
+        raise RuntimeError(f"batched: invalid state (flags={flags}, emitted={emitted})")
+    sides = sorted({c.n for c in cfgs})
+    return {"workload": (f"{n_boxes} boxes, sides in {sides} (uniform draw), sigma_lnrho U[0.1,1.5], 1e6 packets "
+                         f"per 32^3 scaled by volume, mixed form, tally mixing, steps {prep + W}+ of 200 "
+                         f"(z 1600->700), one context"),
+            "value": cells * K / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / K, "steps": K,
+            "warmup": W, "cells": cells, "packets_per_step": emitted,
+            "packets_per_s": emitted * K / (ms * 1e-3),
+            "kernel_ms_per_step": {g: v[0] / K for g, v in kt.items() if v[1]},
+            "launches_per_step": sum(v[1] for v in kt.values()) / K, "flags": flags,
+            "tuning": dict(tuning, source="autotuner table" if tuned else "defaults")}
 
 
 # ------------------------------------------------------------------------ oracle (CPU)
@@ -334,12 +417,21 @@ def run_ours(args):
     cfg, zs = workload(args.n, args.packets)
     K, W = args.steps, max(3, args.warmup)
     clocks = Clocks(local)
-    mixed = time_form(cfg, zs, "mixed", W, K, seed=1 + rank, dist=dist, clocks=clocks, prep=args.prep)
+    mixed = time_form(cfg, zs, "mixed", W, K, seed=1 + rank, dist=dist, clocks=clocks, prep=args.prep, graph=True)
     fp64 = None
     if not args.no_fp64:
         fp64 = time_form(cfg, zs, "fp64", W, max(5, K // 3), seed=1 + rank, dist=dist, clocks=clocks,
                          prep=args.prep)
     e2e = None if args.no_e2e else time_e2e(cfg, zs, mixed, K)
+    batched = None
+    if not args.no_batched:
+        for r in (mixed, fp64):
+            if r:
+                r["box"].close()
+        torch.cuda.empty_cache()
+        t0 = clocks.mark()
+        batched = time_batched(W=2, K=max(3, K // 6))
+        clocks.window(t0, clocks.mark())
     clk = clocks.summary()
 
     def max_over_ranks(v):
@@ -352,6 +444,7 @@ def run_ours(args):
     ms_mixed = max_over_ranks(mixed["ms"])
     ms_fp64 = max_over_ranks(fp64["ms"]) if fp64 else None
     ms_e2e = max_over_ranks(e2e[0]) if e2e else None
+    ms_graph = max_over_ranks(mixed["graph_ms"]) if "graph_ms" in mixed else None
     n3 = cfg.n ** 3
     K64 = max(5, K // 3)
     if rank != 0:
@@ -387,6 +480,7 @@ def run_ours(args):
         "roofline": dict(roof(dominant), traffic=profiled_traffic(dominant)),
         "roofline_other": {g: roof(g) for g in ("emit", "march", "rec_step", "alloc") if g in groups and g != dominant},
         "queued_fraction": mixed["queued"] / max(mixed["emitted"], 1),
+        "tuning": mixed["tuning"],
         "gpu_launches": launches,
     }
     if fp64:
@@ -399,6 +493,13 @@ def run_ours(args):
         out["e2e"] = {"value": world * n3 * K / (ms_e2e * 1e-3), "unit": "cell-steps/s", "h2d_bytes_per_step": e2e[1],
                       "d2h_bytes_per_step": e2e[2],
                       "api": "rec.Box: H2D of delta and velocity, lya_transport, rec_step, D2H of x_e and T per step"}
+    if ms_graph:
+        gms = ms_graph
+        out["graph"] = {"ms_per_step": gms / K, "value": world * n3 * K / (gms * 1e-3), "unit": "cell-steps/s",
+                        "api": "rec_graph_step: transport + rec_step captured as one CUDA graph per step, "
+                               "executable graph updated in place", "steps": K}
+    if batched:
+        out["batched"] = batched
     out["clocks"] = clk
     if world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(cfg, zs)

@@ -98,7 +98,8 @@ typedef struct {
   uint64_t n_packets; /* packets emitted per lya_transport call, < 2^32 */
 } rec_box;
 
-/* Device-side statistics record (caller-owned device memory). */
+/* Device-side statistics record (caller-owned device memory; one per box of a
+ * batched context). */
 typedef struct {
   uint64_t emitted, absorbed, capped, crossings; /* transport counters of the last call */
   uint64_t queued;  /* packets that left their home cell (marched by the second kernel) */
@@ -111,10 +112,29 @@ typedef struct {
                             bit 2: non-finite or negative emission weight */
 } rec_stats;
 
-/* Create a context for n_boxes boxes (only n_boxes == 1 is supported here).
+/* Launch and scheduling parameters of the transport: a library setting with
+ * no counterpart in the paper.  They change only the speed: tallies, counters
+ * and every other result are identical for any valid setting. */
+typedef struct {
+  int32_t emit_blocks_per_sm;  /* emission grid, blocks of 256 threads per SM: 1..5 (FP64 form 1..3, batch 1..4) */
+  int32_t march_blocks_per_sm; /* march grid: 1..5 (FP64 form and batch 1..4) */
+  int32_t march_refill;        /* idle lanes of a warp that trigger a refill from the queue: 1..32 */
+  int32_t march_chunk;         /* queued packets per unit of march work handed to a warp: 8..4096 */
+  int32_t tile;                /* side of the super-tiles that order the march queue: 8, 16, 32 or 64 */
+} rec_tuning;
+
+/* Create a context for n_boxes independent boxes (1 <= n_boxes <= 128), each
+ * with its own side, fields and packet count; all share params (cosmology,
+ * precision form, mixing mode, seed).  With n_boxes > 1 every phase of a call
+ * (allocation, emission, march, each rec_step pass) is one launch over all
+ * boxes; box b draws its random numbers with box index b in the Philox counter
+ * (box 0 therefore reproduces a single-box context bit for bit), keeps its own
+ * sums, lambda and Newton state, and the dev_stats arguments of lya_transport
+ * and rec_step point to n_boxes records, one per box.  The adjoint entry points
+ * need a single-box context.
  * Validates params and buffers, copies the emission-profile table, allocates
  * scratch.  Does not touch the field buffers.
- * Errors: REC_EINVAL, REC_ENOMEM, REC_ECUDA. */
+ * Errors: REC_EINVAL (message names the offending box), REC_ENOMEM, REC_ECUDA. */
 rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_boxes, void* cuda_stream,
                     rec_ctx** out);
 
@@ -140,6 +160,25 @@ rec_status lya_transport(rec_ctx* ctx, int32_t step, double z, rec_stats* dev_st
  * dev_stats (device pointer, may be NULL).
  * Errors: REC_EINVAL (z order), REC_ESTATE, REC_ECUDA. */
 rec_status rec_step(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
+
+/* lya_transport(step, z_from) followed by rec_step(step, z_from, z_to), enqueued
+ * as one CUDA graph: the call captures both on the context stream, updates the
+ * executable graph it keeps from the previous call in place (the launch
+ * sequence of a step never changes, only kernel parameters do) and launches
+ * it.  Results are those of the two calls.  dev_stats receives the transport
+ * counters and the rec_step statistics (n_boxes records for a batch).
+ * Requires a context created on a non-default stream, kernel timing off, and
+ * a stream that is not already being captured.
+ * Errors: REC_EINVAL, REC_ESTATE, REC_ECUDA. */
+rec_status rec_graph_step(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
+
+/* Current transport tuning of a context (defaults after rec_init). */
+rec_status rec_get_tuning(const rec_ctx* ctx, rec_tuning* out);
+
+/* Set the transport tuning; takes effect from the next lya_transport.
+ * Synchronises the context stream (a set-up call, not for inside a step).
+ * Errors: REC_EINVAL (a field out of range; nothing changed), REC_ECUDA. */
+rec_status rec_set_tuning(rec_ctx* ctx, const rec_tuning* tuning);
 
 /* Allocation-free step.  The paper has no counterpart: this is a library entry
  * point for callers that cannot allocate device memory while they step, such as

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -61,6 +62,32 @@ rec_status check_box(const rec_box& b, std::string* why) {
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
+rec_tuning default_tuning(bool mixed, bool batch) {
+  rec_tuning t;
+  rec::transport_limits(mixed, batch, &t.emit_blocks_per_sm, &t.march_blocks_per_sm);
+  t.march_refill = 8;
+  t.march_chunk = 64;
+  t.tile = 32;
+  return t;
+}
+
+uint32_t log2u(uint32_t v) {
+  uint32_t l = 0;
+  while ((1u << l) < v) ++l;
+  return l;
+}
+
+// Super-tile layout of every box of a batch for the tile side in use.
+void layout_buckets(rec_ctx* c) {
+  c->tot_buckets = 0;
+  for (auto& d : c->hbx) {
+    d.nt = (d.n + (uint32_t)c->tune.tile - 1) / (uint32_t)c->tune.tile;
+    d.tlg = log2u((uint32_t)c->tune.tile);
+    d.bk0 = (uint32_t)c->tot_buckets;
+    c->tot_buckets += (int)(d.nt * d.nt * d.nt);
+  }
+}
+
 // Context of several boxes: per-box records and concatenated scratch.
 rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_boxes, void* cuda_stream,
                       rec_ctx** out) {
@@ -86,8 +113,9 @@ rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_
   if (e != cudaSuccess) { rec_status r = cuda_fail(nullptr, e, "device query"); delete c; return r; }
   // offsets of every box in the concatenated scratch
   const bool mixed = params->precision == REC_PREC_MIXED;
-  size_t nP = 0, nfirst = 0, nxy = 0, npk_all = 0;
+  size_t nP = 0, nfirst = 0, nxy = 0, npk_all = 0, nb_alloc = 0;
   c->hbx.resize(n_boxes);
+  c->tune = default_tuning(mixed, true);
   int64_t n3_all = 0;
   for (int i = 0; i < n_boxes; ++i) {
     const rec_box& b = boxes[i];
@@ -98,7 +126,8 @@ rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_
     d.p2 = (b.n & (b.n - 1)) == 0 ? 1u : 0u;
     d.lg = 0;
     while (d.p2 && (1 << d.lg) < b.n) ++d.lg;
-    d.nt = (uint32_t)((b.n + rec::kTile - 1) / rec::kTile);
+    d.mn = b.n >= 2 ? UINT64_MAX / (uint64_t)b.n + 1 : 0;
+    d.mn2 = b.n >= 2 ? UINT64_MAX / ((uint64_t)b.n * b.n) + 1 : 0;
     d.npk = b.n_packets;
     d.pk0 = c->tot_pk;
     c->tot_pk += round_up(b.n_packets, 32);
@@ -108,8 +137,8 @@ rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_
                                                 (rec::kPassThreads * rec::kPassCellsPerThread));
     d.pblk0 = (uint32_t)c->tot_pblk;
     c->tot_pblk += (int)d.pblk;
-    d.bk0 = (uint32_t)c->tot_buckets;
-    c->tot_buckets += (int)(d.nt * d.nt * d.nt);
+    const size_t nt_min = (size_t)((b.n + rec::kMinTile - 1) / rec::kMinTile);
+    nb_alloc += nt_min * nt_min * nt_min;
     // scratch offsets (element counts), kept in the pointer fields until the buffers exist
     d.P = (uint32_t*)(uintptr_t)nP;
     nP += round_up((size_t)d.n3 + 1, 4);
@@ -121,6 +150,7 @@ rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_
     n3_all += d.n3;
   }
   c->n3 = n3_all;
+  layout_buckets(c);
   c->grid = c->tot_pblk;
   c->alloc_blocks = c->tot_ablk;
   const size_t qbytes = (size_t)params->n_quantiles * (mixed ? 4 : 8);
@@ -134,9 +164,9 @@ rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_
   if (e == cudaSuccess) e = cudaMalloc(&c->partQ, sizeof(unsigned long long) * (size_t)c->tot_ablk);
   if (e == cudaSuccess) e = cudaMalloc(&c->first, sizeof(uint32_t) * nfirst);
   if (e == cudaSuccess && mixed) e = cudaMalloc(&c->xy, sizeof(float) * 2 * nxy);
-  if (e == cudaSuccess) e = cudaMalloc(&c->bcap, sizeof(unsigned long long) * (size_t)c->tot_buckets);
-  if (e == cudaSuccess) e = cudaMalloc(&c->bfill, sizeof(unsigned long long) * (size_t)c->tot_buckets);
-  if (e == cudaSuccess) e = cudaMalloc(&c->cpre, sizeof(unsigned long long) * ((size_t)c->tot_buckets + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->bcap, sizeof(unsigned long long) * nb_alloc);
+  if (e == cudaSuccess) e = cudaMalloc(&c->bfill, sizeof(unsigned long long) * nb_alloc);
+  if (e == cudaSuccess) e = cudaMalloc(&c->cpre, sizeof(unsigned long long) * (nb_alloc + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->quant, qbytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->queue, qentry * std::max<size_t>(npk_all, 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->bx, sizeof(rec::BoxDev) * n_boxes);
@@ -230,6 +260,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   c->grid = (int)std::min<int64_t>(want, (int64_t)c->sm_count * 8);
   if (c->grid < 1) c->grid = 1;
   c->alloc_blocks = (int)((c->n3 + rec::kAllocChunk - 1) / rec::kAllocChunk);
+  c->tune = default_tuning(params->precision == REC_PREC_MIXED, false);
 
   size_t qbytes = (size_t)params->n_quantiles * (params->precision == REC_PREC_MIXED ? 4 : 8);
   e = cudaMalloc(&c->sc, sizeof(rec::DevScalars));
@@ -241,7 +272,8 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   if (e == cudaSuccess) e = cudaMalloc(&c->first, sizeof(uint32_t) * (size_t)(b.n_packets / 32 + 2));
   if (e == cudaSuccess && params->precision == REC_PREC_MIXED) e = cudaMalloc(&c->xy, sizeof(float) * 2 * (size_t)c->n3);
   {
-    size_t nt = (size_t)((b.n + rec::kTile - 1) / rec::kTile), nb = nt * nt * nt;  // super-tiles of the march queue
+    // super-tiles of the march queue, sized for the smallest tile side
+    size_t nt = (size_t)((b.n + rec::kMinTile - 1) / rec::kMinTile), nb = nt * nt * nt;
     if (e == cudaSuccess) e = cudaMalloc(&c->bcap, sizeof(unsigned long long) * nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->bfill, sizeof(unsigned long long) * nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->cpre, sizeof(unsigned long long) * (nb + 1));
@@ -314,6 +346,82 @@ rec_status rec_step(rec_ctx* c, int32_t step, double z_from, double z_to, rec_st
   cudaError_t e = c->n_boxes > 1 ? rec::launch_rec_step_batch(c, z_from, z_to, st)
                                   : rec::launch_rec_step(c, z_from, z_to, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "rec_step");
+  return REC_OK;
+}
+
+rec_status rec_get_tuning(const rec_ctx* c, rec_tuning* out) {
+  if (!c || !out) return fail(nullptr, REC_EINVAL, "ctx or out is NULL");
+  *out = c->tune;
+  return REC_OK;
+}
+
+rec_status rec_set_tuning(rec_ctx* c, const rec_tuning* t) {
+  if (!c || !t) return fail(nullptr, REC_EINVAL, "ctx or tuning is NULL");
+  int emax = 0, mmax = 0;
+  rec::transport_limits(c->params.precision == REC_PREC_MIXED, c->n_boxes > 1, &emax, &mmax);
+  if (t->emit_blocks_per_sm < 1 || t->emit_blocks_per_sm > emax)
+    return fail(c, REC_EINVAL, "emit_blocks_per_sm must be in [1, " + std::to_string(emax) + "]");
+  if (t->march_blocks_per_sm < 1 || t->march_blocks_per_sm > mmax)
+    return fail(c, REC_EINVAL, "march_blocks_per_sm must be in [1, " + std::to_string(mmax) + "]");
+  if (t->march_refill < 1 || t->march_refill > 32) return fail(c, REC_EINVAL, "march_refill must be in [1, 32]");
+  if (t->march_chunk < 8 || t->march_chunk > 4096) return fail(c, REC_EINVAL, "march_chunk must be in [8, 4096]");
+  if (t->tile != 8 && t->tile != 16 && t->tile != 32 && t->tile != 64)
+    return fail(c, REC_EINVAL, "tile must be 8, 16, 32 or 64");
+  cudaError_t e = cudaStreamSynchronize(c->stream);  // no transport of this context in flight
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_set_tuning");
+  c->tune = *t;
+  if (c->n_boxes > 1) {
+    layout_buckets(c);
+    e = cudaMemcpy(c->bx, c->hbx.data(), sizeof(rec::BoxDev) * c->n_boxes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rec_set_tuning upload");
+  }
+  return REC_OK;
+}
+
+rec_status rec_graph_step(rec_ctx* c, int32_t step, double z_from, double z_to, rec_stats* st) {
+  if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
+  if (step < 0) return fail(c, REC_EINVAL, "step must be non-negative");
+  if (!(z_from > z_to) || !(z_to > 0) || !is_finite(z_from)) return fail(c, REC_EINVAL, "need z_from > z_to > 0");
+  if (!c->emis_ready) return fail(c, REC_ESTATE, "emission weights unknown: call rec_state_init or rec_refresh first");
+  if (c->timing) return fail(c, REC_EINVAL, "kernel timing is off for graph steps (rec_timing(ctx, 0))");
+  if (c->stream == nullptr) return fail(c, REC_EINVAL, "graph steps need a non-default stream");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) return fail(c, REC_EINVAL, "the context stream is already being captured");
+  if (c->coop_grid == 0) {  // resolve the substep launch mode outside the capture
+    const char* sel = std::getenv("REC_SUBSTEP");
+    if (!(sel && std::strcmp(sel, "coop") == 0)) c->coop_grid = -1;
+  }
+  e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+  c->capturing = true;
+  cudaError_t e1 = c->n_boxes > 1 ? rec::launch_transport_batch(c, step, z_from, st)
+                                  : rec::launch_transport(c, step, z_from, st);
+  cudaError_t e2 = (e1 == cudaSuccess) ? (c->n_boxes > 1 ? rec::launch_rec_step_batch(c, z_from, z_to, st)
+                                                         : rec::launch_rec_step(c, z_from, z_to, st))
+                                       : cudaSuccess;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->stream, &g);
+  c->capturing = false;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(c, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e), "rec_graph_step capture");
+  }
+  // same topology every step: update the kernel parameters of the executable graph in place
+  if (c->gexec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(c->gexec, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  if (!c->gexec) e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { c->gexec = nullptr; return cuda_fail(c, e, "cudaGraphInstantiate"); }
+  e = cudaGraphLaunch(c->gexec, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
   return REC_OK;
 }
 
@@ -459,6 +567,7 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->bcap);
   cudaFree(c->bfill);
   cudaFree(c->cpre);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
   cudaFree(c->bx);
   cudaFree(c->bstep);
   cudaFree(c->gsc);

@@ -22,8 +22,9 @@ constexpr int kNewtonMaxPasses = 10;   // Newton evaluations launched per subste
 constexpr uint32_t kMaxCrossings = 1u << 20;  // per-packet cap on face crossings
 constexpr int kAllocThreads = 256;
 constexpr int kAllocItems = 16;        // consecutive cells per thread in the allocation scan
-// Side of the super-tiles whose buckets order the march queue.
-constexpr uint32_t kTile = 32;
+// Smallest side of the super-tiles whose buckets order the march queue (the
+// bucket arrays are sized for it; the side in use is a tuning parameter).
+constexpr uint32_t kMinTile = 8;
 constexpr int kAllocChunk = kAllocThreads * kAllocItems;
 
 // Device-resident scalars of one box.  Everything data-dependent stays on the
@@ -79,6 +80,8 @@ struct BoxDev {
   DevScalars* sc;      // scalars of this box
   int64_t n3;
   uint32_t n, lg, nt, p2;  // side, log2 side (power of two), super-tiles per axis, side is a power of two
+  uint64_t mn, mn2;        // multipliers ceil(2^64/n), ceil(2^64/n^2) of the exact divisions (n >= 2)
+  uint32_t tlg;            // log2 of the super-tile side in use
   uint64_t npk;        // packets requested per transport
   uint64_t pk0;        // first packet of the box in the batch packet space (multiple of 32)
   uint32_t ablk0;      // first allocation block
@@ -150,6 +153,10 @@ struct rec_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[REC_T_COUNT];
   std::vector<cudaEvent_t> pool;
   int64_t launches[REC_T_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  rec_tuning tune;  // transport launch and scheduling parameters
+  // graph-captured steps (rec_graph_step): the executable graph, updated in place
+  cudaGraphExec_t gexec = nullptr;
+  bool capturing = false;  // no timing events while a step is captured
   // batched context (n_boxes > 1); unused for one box
   int n_boxes = 1;
   std::vector<rec_box> boxes;
@@ -175,7 +182,7 @@ struct GroupTimer {
   cudaEvent_t e0 = nullptr;
   GroupTimer(rec_ctx* ctx, int group, int n_launches) : c(ctx), g(group) {
     c->launches[g] += n_launches;
-    if (c->timing) { e0 = take(); cudaEventRecord(e0, c->stream); }
+    if (c->timing && !c->capturing) { e0 = take(); cudaEventRecord(e0, c->stream); }
   }
   ~GroupTimer() {
     if (e0) {
@@ -217,6 +224,7 @@ void enqueue_newton_passes(rec_ctx* c, DevScalars* sc, const StepCoef& k, const 
 // rec_transport.cu
 cudaError_t launch_transport(rec_ctx* c, int step, double z, rec_stats* st);
 cudaError_t launch_transport_batch(rec_ctx* c, int step, double z, rec_stats* st);
+void transport_limits(bool mixed, bool batch, int* emit_max, int* march_max);
 
 // rec_step.cu, batched contexts
 cudaError_t launch_state_init_batch(rec_ctx* c, double z);

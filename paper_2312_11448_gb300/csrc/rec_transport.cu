@@ -84,6 +84,7 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }  // correctly rounded 1/a
   static __device__ __forceinline__ float sqr(float a) { return __fsqrt_rn(a); }
   static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
   static __device__ __forceinline__ int trunc(float a) { return __float2int_rz(a); }
@@ -93,6 +94,7 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }  // correctly rounded 1/a
   static __device__ __forceinline__ double sqr(double a) { return __dsqrt_rn(a); }
   static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
   static __device__ __forceinline__ int trunc(double a) { return __double2int_rz(a); }
@@ -193,24 +195,57 @@ __device__ __forceinline__ uint64_t block_scan_incl(uint64_t v, uint64_t* incl) 
   return total;
 }
 
-// Super-tiles of kTile^3 cells group the march queue: packets are queued in
+// Super-tiles of 2^tlg cells per side group the march queue: packets are queued in
 // the bucket of their home super-tile, and the march takes the buckets in
 // order, so the rays in flight at any time start in a compact region.
 
+// Cell coordinates: shifts and masks for power-of-two sides, otherwise the
+// quotients by n and n^2 from 64-bit multiply-high with precomputed
+// multipliers ceil(2^64 / d), exact for every 32-bit dividend (Lemire, Kaser &
+// Kurz 2019, "Faster remainder by direct computation").
 struct Tiles {
   uint32_t n, nt, lg;  // box side, super-tiles per axis, log2 n (power-of-two sides)
-  __device__ __forceinline__ uint32_t of(uint32_t cell) const {
-    uint32_t ix = cell % n, iy = (cell / n) % n, iz = cell / (n * n);
-    return ((iz / kTile) * nt + iy / kTile) * nt + ix / kTile;
+  uint64_t mn, mn2;    // multipliers for the division by n and by n^2 (unused when n = 1: cell = 0)
+  uint32_t tlg;        // log2 of the super-tile side
+  template <bool P2>
+  __device__ __forceinline__ void coords(uint32_t cell, uint32_t* ix, uint32_t* iy, uint32_t* iz) const {
+    if (P2) {
+      const uint32_t m = n - 1u;
+      *ix = cell & m; *iy = (cell >> lg) & m; *iz = cell >> (2u * lg);
+    } else {
+      const uint32_t q = (uint32_t)__umul64hi(mn, (uint64_t)cell);   // cell / n
+      const uint32_t z = (uint32_t)__umul64hi(mn2, (uint64_t)cell);  // cell / n^2
+      *ix = cell - q * n; *iy = q - z * n; *iz = z;
+    }
   }
   template <bool P2>
   __device__ __forceinline__ uint32_t at(uint32_t cell) const {
-    if (!P2) return of(cell);
-    const uint32_t m = n - 1u;
-    uint32_t ix = cell & m, iy = (cell >> lg) & m, iz = cell >> (2u * lg);
-    return ((iz / kTile) * nt + iy / kTile) * nt + ix / kTile;
+    uint32_t ix, iy, iz;
+    coords<P2>(cell, &ix, &iy, &iz);
+    return ((iz >> tlg) * nt + (iy >> tlg)) * nt + (ix >> tlg);
   }
+  __device__ __forceinline__ uint32_t of(uint32_t cell) const { return at<false>(cell); }
 };
+
+// Multiplier ceil(2^64 / d) of the exact 32-bit division by d >= 2.
+inline uint64_t fastdiv_multiplier(uint64_t d) { return d >= 2 ? UINT64_MAX / d + 1 : 0; }
+inline uint32_t log2_of(uint32_t v) {
+  uint32_t l = 0;
+  while ((1u << l) < v) ++l;
+  return l;
+}
+inline Tiles make_tiles(int n, int tile) {
+  Tiles t;
+  t.n = (uint32_t)n;
+  t.tlg = log2_of((uint32_t)tile);
+  t.nt = (uint32_t)((n + tile - 1) / tile);
+  t.lg = 0;
+  if ((n & (n - 1)) == 0)
+    while ((1 << t.lg) < n) ++t.lg;
+  t.mn = fastdiv_multiplier((uint64_t)n);
+  t.mn2 = fastdiv_multiplier((uint64_t)n * (uint64_t)n);
+  return t;
+}
 
 // The allocation kernels give each thread kAllocItems consecutive cells.
 template <class R>
@@ -400,18 +435,16 @@ __global__ void __launch_bounds__(1024) k_bucket_offsets(unsigned long long* bca
   }
 }
 
-// One block: the march works through the queue in chunks of kChunk packets that
-// never straddle a bucket; cpre[b] = first chunk of bucket b, cpre[nb] = all
-// chunks.  Also the total queued.
-constexpr int kChunk = 64;
-
+// One block: the march works through the queue in chunks of `chunk` packets
+// that never straddle a bucket; cpre[b] = first chunk of bucket b, cpre[nb] =
+// all chunks.  Also the total queued.
 __global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* bfill, unsigned long long* cpre, int nb,
-                                                      DevScalars* sc) {
+                                                      DevScalars* sc, uint32_t chunk) {
   __shared__ unsigned long long part[1024], qpart[1024];
   const int per = (nb + 1023) / 1024;
   unsigned long long s = 0, q = 0;
   for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
-    s += (bfill[b] + kChunk - 1) / kChunk;
+    s += (bfill[b] + chunk - 1) / chunk;
     q += bfill[b];
   }
   part[threadIdx.x] = s;
@@ -428,7 +461,7 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* 
   unsigned long long run = part[threadIdx.x];
   for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
     cpre[b] = run;
-    run += (bfill[b] + kChunk - 1) / kChunk;
+    run += (bfill[b] + chunk - 1) / chunk;
   }
 }
 
@@ -458,6 +491,8 @@ struct TransportArgs {
   unsigned long long* boff;        // bucket start in the queue (capacity prefix)
   unsigned long long* bfill;       // packets queued per bucket
   const unsigned long long* cpre;  // first march chunk of each bucket [nb + 1]
+  uint32_t chunk;                  // queued packets per march chunk
+  int refill;                      // idle lanes of a warp that trigger a refill
 };
 
 // First index k in [lo, hi] with P[k] > key (P[hi] > key holds).
@@ -489,8 +524,9 @@ struct Ray {
 template <class R>
 __device__ __forceinline__ void axis_setup(R nd, R* tD, int* st) {
   using A = Ar<R>;
-  if (nd > (R)0) { *st = 1; *tD = A::div((R)1, nd); }
-  else if (nd < (R)0) { *st = -1; *tD = A::div((R)1, -nd); }
+  // 1/|n_d| correctly rounded: the same value as the division 1/|n_d|
+  if (nd > (R)0) { *st = 1; *tD = A::rcp(nd); }
+  else if (nd < (R)0) { *st = -1; *tD = A::rcp(-nd); }
   else { *st = 0; *tD = A::inf(); }
 }
 
@@ -679,11 +715,7 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
     V Uh = e.vel[cell];
     R dh = A::add(A::add(A::mul(r.knx, Uh.x), A::mul(r.kny, Uh.y)), A::mul(r.knz, Uh.z));
     r.u0 = A::add(A::mul(xi, vt), dh);
-    if (P2) {
-      r.ix = cell & (n - 1u); r.iy = (cell >> e.tl.lg) & (n - 1u); r.iz = cell >> (2u * e.tl.lg);
-    } else {
-      r.ix = cell % n; r.iy = (cell / n) % n; r.iz = cell / (n * n);
-    }
+    e.tl.template coords<P2>(cell, &r.ix, &r.iy, &r.iz);
     axis_setup<R>(nx, &r.tDx, &r.sx);
     axis_setup<R>(ny, &r.tDy, &r.sy);
     axis_setup<R>(nz, &r.tDz, &r.sz);
@@ -740,7 +772,7 @@ __global__ void __launch_bounds__(TT, emit_occupancy<R>()) k_emit(TransportArgs<
   add_counters(a.sc, my_abs, 0, my_cross);
 }
 
-// March of the queued packets.  Persistent warps take chunks of kChunk queued
+// March of the queued packets.  Persistent warps take chunks of a.chunk queued
 // packets (never straddling a bucket) from a shared counter in queue order, so
 // the warps advance through the super-tile buckets together and the cells
 // they touch stay close in memory; each warp refills its idle lanes from its
@@ -780,7 +812,7 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
   uint64_t my_abs = 0, my_cap = 0, my_cross = 0;
   for (;;) {
     unsigned idle = __ballot_sync(0xffffffffu, !active);
-    if (more && __popc(idle) >= 8) {
+    if (more && __popc(idle) >= a.refill) {
       // refill idle lanes in lane order from the warp's chunks
       while (idle && more) {
         if (!have || pos >= end) {
@@ -797,9 +829,9 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
             if (__ldg(a.cpre + mid) <= chunk) lo = mid;
             else hi = mid;
           }
-          const uint64_t k0 = (chunk - __ldg(a.cpre + lo)) * kChunk;
+          const uint64_t k0 = (chunk - __ldg(a.cpre + lo)) * a.chunk;
           pos = a.boff[lo] + k0;
-          end = pos + min((uint64_t)kChunk, (uint64_t)(a.bfill[lo] - k0));
+          end = pos + min((uint64_t)a.chunk, (uint64_t)(a.bfill[lo] - k0));
           have = true;
           if (MB) {  // box of this bucket: last b with bk0 <= lo
             cbox = last_le(B, lo, [&](int i) { return bxs[i].bk0; });
@@ -826,8 +858,10 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
           cell = to_bits<R>(q0v.x);
           if (P2) {
             r.ix = cell & (n - 1u); r.iy = (cell >> lg) & (n - 1u); r.iz = cell >> (2u * lg);
-          } else {
+          } else if (MB) {
             r.ix = cell % ln; r.iy = (cell / ln) % ln; r.iz = cell / (ln * ln);
+          } else {
+            a.tl.template coords<false>(cell, &r.ix, &r.iy, &r.iz);
           }
           r.tMx = q0v.y; r.tMy = q0v.z; r.tMz = q0v.w;
           r.sx = q1v.x < (R)0 ? -1 : 1; r.tDx = fabs(q1v.x);
@@ -887,9 +921,8 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   const rec_box& b = c->box;
   Stream s{(uint32_t)c->params.seed, (uint32_t)(c->params.seed >> 32) ^ (uint32_t)step, 0u};
   const bool p2 = (b.n & (b.n - 1)) == 0;
-  uint32_t lg = 0;
-  while (p2 && (1 << lg) < b.n) ++lg;
-  Tiles tl{(uint32_t)b.n, (uint32_t)((b.n + kTile - 1) / kTile), lg};
+  const rec_tuning& tu = c->tune;
+  const Tiles tl = make_tiles(b.n, tu.tile);
   const int nb = (int)(tl.nt * tl.nt * tl.nt);
   {
     GroupTimer t(c, kTAlloc, 4);
@@ -923,16 +956,18 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.boff = c->bcap;
   a.bfill = c->bfill;
   a.cpre = c->cpre;
+  a.chunk = (uint32_t)tu.march_chunk;
+  a.refill = tu.march_refill;
   {
     GroupTimer t(c, kTEmit, 2);
-    const int eb = c->sm_count * emit_occupancy<R>();
+    const int eb = c->sm_count * tu.emit_blocks_per_sm;
     if (p2) k_emit<R, true><<<eb, TT, 0, c->stream>>>(a);
     else k_emit<R, false><<<eb, TT, 0, c->stream>>>(a);
-    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->sc);
+    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->sc, a.chunk);
   }
   {
     GroupTimer t(c, kTMarch, 1);
-    const int mb = c->sm_count * march_occupancy<R, false>();
+    const int mb = c->sm_count * tu.march_blocks_per_sm;
     if (p2) k_march<R, true, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1);
     else k_march<R, false, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1);
   }
@@ -1064,37 +1099,42 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix_batch(const BoxDev* bxs, in
   const DevScalars* sc = d.sc;
   const int64_t c0 = (int64_t)(blockIdx.x - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
   alloc_prefix_block<R>((const R*)d.emis, d.n3, d.npk, sc->sumQ, sc->alloc_u, (R)sc->rmax, partQ[blockIdx.x], c0,
-                        d.P, d.first, Tiles{d.n, d.nt, d.lg}, d.bk0, bcap);
+                        d.P, d.first, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0, bcap);
 }
 
 // Emission over the batch packet space (each box padded to a multiple of 32,
 // so a warp's 32 packets belong to one box).
 template <class R>
-__global__ void __launch_bounds__(TT, emit_occupancy<R>()) k_emit_batch(TransportArgs<R> a, const BoxDev* bxs,
-                                                                        const BoxStep* bst, int B, uint64_t tot_pk) {
+__global__ void __launch_bounds__(TT, 4) k_emit_batch(TransportArgs<R> a, const BoxDev* bxs, const BoxStep* bst,
+                                                      int B, uint64_t tot_pk) {
   using V = typename Vec4<R>::T;
   __shared__ BoxCounters cnt;
   box_counters_clear(cnt, B);
   uint64_t my_abs = 0, my_cross = 0;
   int cur = -1;
+  uint64_t lo_pk = 1, hi_pk = 0;  // packet range of box cur (empty before the first lookup)
+  uint32_t N = 0;
   const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
   for (uint64_t gbase = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 32; gbase < tot_pk;
        gbase += warps_total * 32) {
-    const int b = last_le(B, gbase, [&](int i) { return bxs[i].pk0; });
-    if (b != cur) {
+    if (gbase < lo_pk || gbase >= hi_pk) {  // next box (uniform over the warp)
+      const int b = last_le(B, gbase, [&](int i) { return bxs[i].pk0; });
       if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
       my_abs = my_cross = 0;
       cur = b;
+      lo_pk = bxs[b].pk0;
+      hi_pk = (b + 1 < B) ? bxs[b + 1].pk0 : tot_pk;
+      N = __ldg(bxs[b].P + bxs[b].n3);  // packets actually allocated to this box
     }
-    const BoxDev& d = bxs[b];
-    const uint32_t N = __ldg(d.P + d.n3);  // packets actually allocated to this box
-    const uint64_t base = gbase - d.pk0;
-    if (base >= N) continue;  // padding of the packet space (uniform over the warp)
+    const uint64_t base = gbase - lo_pk;
+    if (base >= N) continue;  // padding of the packet space
+    const BoxDev& d = bxs[cur];
     const EmitBox<R> e{d.P, d.first, (uint32_t)d.n3, d.n, (const V*)d.vel4, (const R*)d.T, d.tally,
-                       (R)bst[b].kappa, (R)bst[b].cth, Stream{a.strm.k0, a.strm.k1, (uint32_t)b},
-                       Tiles{d.n, d.nt, d.lg}, d.bk0};
-    if (d.p2) emit_warp<R, true>(a, e, (uint32_t)base, N, my_abs, my_cross);
-    else emit_warp<R, false>(a, e, (uint32_t)base, N, my_abs, my_cross);
+                       (R)bst[cur].kappa, (R)bst[cur].cth, Stream{a.strm.k0, a.strm.k1, (uint32_t)cur},
+                       Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0};
+    // one code path for all sides (the power-of-two specialisation would double
+    // the inlined body and spill registers)
+    emit_warp<R, false>(a, e, (uint32_t)base, N, my_abs, my_cross);
   }
   if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
   box_counters_flush(cnt, bxs, B);
@@ -1155,14 +1195,16 @@ cudaError_t run_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
   a.boff = c->bcap;
   a.bfill = c->bfill;
   a.cpre = c->cpre;
+  a.chunk = (uint32_t)c->tune.march_chunk;
+  a.refill = c->tune.march_refill;
   {
     GroupTimer t(c, kTEmit, 2);
-    k_emit_batch<R><<<c->sm_count * emit_occupancy<R>(), TT, 0, c->stream>>>(a, c->bx, c->bstep, B, c->tot_pk);
-    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->gsc);
+    k_emit_batch<R><<<c->sm_count * c->tune.emit_blocks_per_sm, TT, 0, c->stream>>>(a, c->bx, c->bstep, B, c->tot_pk);
+    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->gsc, a.chunk);
   }
   {
     GroupTimer t(c, kTMarch, 1);
-    k_march<R, false, true><<<c->sm_count * march_occupancy<R, true>(), TT, 0, c->stream>>>(a, c->bx, B);
+    k_march<R, false, true><<<c->sm_count * c->tune.march_blocks_per_sm, TT, 0, c->stream>>>(a, c->bx, B);
   }
   {
     GroupTimer t(c, kTEnd, 1);
@@ -1172,6 +1214,14 @@ cudaError_t run_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
 }
 
 }  // namespace
+
+// Largest resident blocks per SM of the emission and the march (their
+// launch bounds), for the checks of rec_set_tuning.
+void transport_limits(bool mixed, bool batch, int* emit_max, int* march_max) {
+  *emit_max = batch ? 4 : (mixed ? emit_occupancy<float>() : emit_occupancy<double>());
+  *march_max = batch ? march_occupancy<float, true>()
+                     : (mixed ? march_occupancy<float, false>() : march_occupancy<double, false>());
+}
 
 cudaError_t launch_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   if (c->params.precision == REC_PREC_MIXED) return run_transport<float>(c, step, z, st);

@@ -45,6 +45,15 @@ class Stats(C.Structure):
                 ("S1s", C.c_double), ("newton_passes", C.c_int32), ("flags", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    """rec_tuning: transport launch and scheduling parameters (speed only)."""
+    _fields_ = [("emit_blocks_per_sm", C.c_int32), ("march_blocks_per_sm", C.c_int32), ("march_refill", C.c_int32),
+                ("march_chunk", C.c_int32), ("tile", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class RecError(RuntimeError):
     pass
 
@@ -62,6 +71,9 @@ def lib():
         L.lya_transport.argtypes = [vp, i32, d, vp]
         L.rec_step.argtypes = [vp, i32, d, d, vp]
         L.rec_step_noalloc.argtypes = [P(Params), P(BoxDesc), d, d, vp, vp]
+        L.rec_graph_step.argtypes = [vp, i32, d, d, vp]
+        L.rec_get_tuning.argtypes = [vp, P(Tuning)]
+        L.rec_set_tuning.argtypes = [vp, P(Tuning)]
         L.rec_step_adjoint.argtypes = [vp, i32, d, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, d]
         L.rec_xe_adjoint.argtypes = [vp, vp, d, vp, vp]
         L.rec_transport_params.argtypes = [P(Params), i32, d, P(d)]
@@ -72,7 +84,7 @@ def lib():
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
         L.rec_last_error.restype = C.c_char_p
-        for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc",
+        for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc", "rec_graph_step", "rec_get_tuning", "rec_set_tuning",
                   "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times"):
             getattr(L, f).restype = C.c_int
         _lib = L
@@ -184,8 +196,18 @@ class Batch:
     def step(self, step, z_from, z_to):
         self._check(lib().rec_step(self.ctx, int(step), z_from, z_to, C.c_void_p(self._stats.data_ptr())), "rec_step")
 
+    def graph_step(self, step, z_from, z_to):
+        self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, C.c_void_p(self._stats.data_ptr())),
+                    "rec_graph_step")
+
     def timing(self, enable=True):
         self._check(lib().rec_timing(self.ctx, 1 if enable else 0), "rec_timing")
+
+    def tuning(self) -> dict:
+        return _get_tuning(self)
+
+    def set_tuning(self, **kw):
+        _set_tuning(self, **kw)
 
     def kernel_times(self) -> dict:
         ms = (C.c_double * 7)()
@@ -216,6 +238,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _get_tuning(obj) -> dict:
+    t = Tuning()
+    obj._check(lib().rec_get_tuning(obj.ctx, C.byref(t)), "rec_get_tuning")
+    return t.as_dict()
+
+
+def _set_tuning(obj, **kw):
+    t = Tuning()
+    obj._check(lib().rec_get_tuning(obj.ctx, C.byref(t)), "rec_get_tuning")
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    obj._check(lib().rec_set_tuning(obj.ctx, C.byref(t)), "rec_set_tuning")
 
 
 def _stats_dict(s) -> dict:
@@ -293,6 +329,10 @@ class Box:
     def step(self, step, z_from, z_to, slot=0):
         self._check(lib().rec_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_step")
 
+    def graph_step(self, step, z_from, z_to, slot=0):
+        """transport(step, z_from) + step(step, z_from, z_to) as one CUDA graph launch."""
+        self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_graph_step")
+
     def step_noalloc(self, z_from, z_to, slot=0):
         """rec_step_noalloc on this machine's fields and parameters (the context is not used)."""
         desc = BoxDesc(self.n, self.delta.data_ptr(), self.vel4.data_ptr(), self.x.data_ptr(), self.T.data_ptr(),
@@ -315,6 +355,12 @@ class Box:
                     "rec_xe_adjoint")
 
     TIMER_GROUPS = ("alloc", "emit", "march", "transport_end", "rec_step", "adjoint", "other")
+
+    def tuning(self) -> dict:
+        return _get_tuning(self)
+
+    def set_tuning(self, **kw):
+        _set_tuning(self, **kw)
 
     def timing(self, enable=True):
         self._check(lib().rec_timing(self.ctx, 1 if enable else 0), "rec_timing")

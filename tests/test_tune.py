@@ -1,0 +1,57 @@
+"""The autotuner's search logic on the CPU (a synthetic cost with a known
+minimum), its table keys and files."""
+import json
+
+from paper_2312_11448_gb300 import tune
+
+
+def _start():
+    return {"emit_blocks_per_sm": 5, "march_blocks_per_sm": 5, "march_refill": 8, "march_chunk": 64, "tile": 32}
+
+
+def test_coordinate_descent_finds_separable_minimum():
+    target = {"emit_blocks_per_sm": 3, "march_blocks_per_sm": 4, "march_refill": 16, "march_chunk": 128, "tile": 16}
+
+    def cost(s):
+        return sum((s[f] - target[f]) ** 2 / (1 + target[f]) for f in tune.FIELDS) + 1.0
+
+    best, c, log = tune.coordinate_descent(_start(), cost)
+    assert best == target and c == 1.0
+    # every trial is a setting on the candidate grid, none evaluated twice
+    keys = [tuple(s[f] for f in tune.FIELDS) for s, _ in log]
+    assert len(keys) == len(set(keys))
+    for s, _ in log:
+        for f in tune.FIELDS:
+            assert s[f] in tune.CANDIDATES[f] or s[f] == _start()[f]
+
+
+def test_coordinate_descent_respects_limits_and_keeps_start_when_best():
+    def cost(s):
+        return 10.0 - s["march_blocks_per_sm"]  # wants the largest grid
+
+    best, c, _ = tune.coordinate_descent(_start(), cost,
+                                         allowed=lambda f, v: not (f == "march_blocks_per_sm" and v > 4))
+    assert best["march_blocks_per_sm"] == 5  # the start value stays allowed
+    flat, c2, log = tune.coordinate_descent(_start(), lambda s: 1.0)
+    assert flat == _start() and c2 == 1.0 and len(log) > 1
+
+
+def test_workload_keys_and_table(tmp_path):
+    assert tune.workload_key(256, 100_000_000, "mixed") == "n256-ppc4-mixed-single"
+    assert tune.workload_key(32, 1_000_000, "mixed", batch=True) == "n32-ppc16-mixed-batch"
+    assert tune.workload_key(8, 0, "fp64") == "n8-ppc1-fp64-single"
+    p = tmp_path / "t.json"
+    p.write_text(json.dumps({"k": {"setting": _start()}}))
+    assert tune.load_table(str(p))["k"]["setting"]["tile"] == 32
+    assert tune.load_table(str(tmp_path / "missing.json")) == {}
+
+    class Fake:
+        def __init__(self):
+            self.set = None
+
+        def set_tuning(self, **kw):
+            self.set = kw
+
+    f = Fake()
+    assert tune.apply_table(f, "k", str(p)) == _start() and f.set == _start()
+    assert tune.apply_table(f, "absent", str(p)) is None
