@@ -402,11 +402,36 @@ def profiled_traffic(group):
         return None
 
 
+# ------------------------------------------------------------------------ multi-rank
+def rank_env():
+    """(rank, world size, local rank) from the torchrun environment."""
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def rank_seed(rank):
+    """Each rank runs its own independent box (weak scaling): seed 1 + rank."""
+    return 1 + rank
+
+
+def reduce_max(v, dist, device):
+    """Max over ranks of a timing (the slowest rank sets the whole job's time)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, K, ms_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * K / (ms_max * 1e-3)
+
+
 # ---------------------------------------------------------------------------- arms
 def run_ours(args):
     import torch
-    rank, world, local = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(
-        os.environ.get("LOCAL_RANK", 0))
+    rank, world, local = rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -417,10 +442,11 @@ def run_ours(args):
     cfg, zs = workload(args.n, args.packets)
     K, W = args.steps, max(3, args.warmup)
     clocks = Clocks(local)
-    mixed = time_form(cfg, zs, "mixed", W, K, seed=1 + rank, dist=dist, clocks=clocks, prep=args.prep, graph=True)
+    mixed = time_form(cfg, zs, "mixed", W, K, seed=rank_seed(rank), dist=dist, clocks=clocks, prep=args.prep,
+                      graph=True)
     fp64 = None
     if not args.no_fp64:
-        fp64 = time_form(cfg, zs, "fp64", W, max(5, K // 3), seed=1 + rank, dist=dist, clocks=clocks,
+        fp64 = time_form(cfg, zs, "fp64", W, max(5, K // 3), seed=rank_seed(rank), dist=dist, clocks=clocks,
                          prep=args.prep)
     e2e = None if args.no_e2e else time_e2e(cfg, zs, mixed, K)
     batched = None
@@ -435,11 +461,7 @@ def run_ours(args):
     clk = clocks.summary()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, "cuda")
 
     ms_mixed = max_over_ranks(mixed["ms"])
     ms_fp64 = max_over_ranks(fp64["ms"]) if fp64 else None
@@ -450,7 +472,7 @@ def run_ours(args):
     if rank != 0:
         dist.barrier() if dist else None
         return
-    value = world * n3 * K / (ms_mixed * 1e-3)
+    value = job_value(world, n3, K, ms_mixed)
     peak, peak_kind = measured_peaks()
     groups = {g: v for g, v in mixed["kt"].items() if v[1]}
     dominant = max(("emit", "march", "rec_step", "alloc"), key=lambda g: groups.get(g, (0, 0))[0])
