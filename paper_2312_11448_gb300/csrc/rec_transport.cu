@@ -109,6 +109,7 @@ template <class R> struct Draws;
 template <> struct Draws<float> {
   // block 0: three cell offsets and the frequency quantile; blocks 1..16: two
   // direction pairs each
+  static constexpr int kPairs = 2;
   static __device__ __forceinline__ void position(const Stream& s, uint32_t c, uint32_t j, float f[3], float* uq) {
     U4 r = draw(s, c, j, 0u);
     f[0] = u01f(r.a); f[1] = u01f(r.b); f[2] = u01f(r.c); *uq = u01f(r.d);
@@ -126,6 +127,7 @@ template <> struct Draws<float> {
 template <> struct Draws<double> {
   // blocks 0, 1: three cell offsets and the quantile (two words per deviate);
   // blocks 2..33: one direction pair each
+  static constexpr int kPairs = 1;
   static __device__ __forceinline__ void position(const Stream& s, uint32_t c, uint32_t j, double f[3], double* uq) {
     U4 r = draw(s, c, j, 0u), q = draw(s, c, j, 1u);
     f[0] = u01d(r.a, r.b); f[1] = u01d(r.c, r.d); f[2] = u01d(q.a, q.b); *uq = u01d(q.c, q.d);
@@ -522,12 +524,13 @@ struct Ray {
 
 // tDelta and step of one axis from the direction cosine (Amanatides-Woo).
 template <class R>
+// Written without branches: 1/|n_d| correctly rounded (the same value as the
+// division 1/|n_d|) is +inf for n_d = 0, which is the tDelta of an axis never
+// crossed.
 __device__ __forceinline__ void axis_setup(R nd, R* tD, int* st) {
   using A = Ar<R>;
-  // 1/|n_d| correctly rounded: the same value as the division 1/|n_d|
-  if (nd > (R)0) { *st = 1; *tD = A::rcp(nd); }
-  else if (nd < (R)0) { *st = -1; *tD = A::rcp(-nd); }
-  else { *st = 0; *tD = A::inf(); }
+  *st = (nd > (R)0) - (nd < (R)0);
+  *tD = A::rcp(fabs(nd));
 }
 
 // One cell of the march: resonance test in the current cell, then a step
@@ -686,21 +689,36 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
     // (1) injection point uniform in the cell, frequency quantile
     R f[3], uq;
     Draws<R>::position(e.strm, cell, j, f, &uq);
-    // isotropic direction (Marsaglia 1972): candidate pairs t = 0, 1, ...
-    // (each Philox block is computed once for the pairs it holds)
+    // isotropic direction (Marsaglia 1972): the first accepted of the candidate
+    // pairs t = 0, 1, ... (each Philox block is computed once for the pairs it
+    // holds).  The pairs of the first block are tested side by side; the loop
+    // over later blocks runs for the few packets that reject all of them.
     {
-      typename Draws<R>::Block blk;
-      for (int t = 0; t < 32; ++t) {
-        R ua, ub;
+      typename Draws<R>::Block blk = Draws<R>::block(e.strm, cell, j, 0);
+      R ua, ub;
+      Draws<R>::pair_from(blk, 0, &ua, &ub);
+      R v1 = A::sub(A::mul(two, ua), one), v2 = A::sub(A::mul(two, ub), one);
+      R s = A::add(A::mul(v1, v1), A::mul(v2, v2));
+      bool ok = s < one && s > zero;
+      int t = 1;
+      if (Draws<R>::kPairs == 2) {  // the block's second pair
+        Draws<R>::pair_from(blk, 1, &ua, &ub);
+        const R w1 = A::sub(A::mul(two, ua), one), w2 = A::sub(A::mul(two, ub), one);
+        const R sw = A::add(A::mul(w1, w1), A::mul(w2, w2));
+        if (!ok && sw < one && sw > zero) { v1 = w1; v2 = w2; s = sw; ok = true; }
+        t = 2;
+      }
+      for (; !ok && t < 32; ++t) {
         if (Draws<R>::first_of_block(t)) blk = Draws<R>::block(e.strm, cell, j, t);
         Draws<R>::pair_from(blk, t, &ua, &ub);
-        R v1 = A::sub(A::mul(two, ua), one), v2 = A::sub(A::mul(two, ub), one);
-        R s = A::add(A::mul(v1, v1), A::mul(v2, v2));
-        if (s < one && s > zero) {
-          R fac = A::mul(two, A::sqr(A::sub(one, s)));
-          nx = A::mul(v1, fac); ny = A::mul(v2, fac); nz = A::sub(one, A::mul(two, s));
-          break;
-        }
+        v1 = A::sub(A::mul(two, ua), one);
+        v2 = A::sub(A::mul(two, ub), one);
+        s = A::add(A::mul(v1, v1), A::mul(v2, v2));
+        ok = s < one && s > zero;
+      }
+      if (ok) {
+        R fac = A::mul(two, A::sqr(A::sub(one, s)));
+        nx = A::mul(v1, fac); ny = A::mul(v2, fac); nz = A::sub(one, A::mul(two, s));
       }
     }
     // emission frequency from the tabulated inverse CDF
@@ -719,9 +737,11 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
     axis_setup<R>(nx, &r.tDx, &r.sx);
     axis_setup<R>(ny, &r.tDy, &r.sy);
     axis_setup<R>(nz, &r.tDz, &r.sz);
-    r.tMx = r.sx > 0 ? A::mul(A::sub(one, f[0]), r.tDx) : (r.sx < 0 ? A::mul(f[0], r.tDx) : A::inf());
-    r.tMy = r.sy > 0 ? A::mul(A::sub(one, f[1]), r.tDy) : (r.sy < 0 ? A::mul(f[1], r.tDy) : A::inf());
-    r.tMz = r.sz > 0 ? A::mul(A::sub(one, f[2]), r.tDz) : (r.sz < 0 ? A::mul(f[2], r.tDz) : A::inf());
+    // distance to the first face along each axis (f in (0,1): an axis with
+    // tDelta = inf gets tMax = inf)
+    r.tMx = A::mul(r.sx < 0 ? f[0] : A::sub(one, f[0]), r.tDx);
+    r.tMy = A::mul(r.sy < 0 ? f[1] : A::sub(one, f[1]), r.tDy);
+    r.tMz = A::mul(r.sz < 0 ? f[2] : A::sub(one, f[2]), r.tDz);
     r.kc = 0;
     int res = march_cell<R, P2>(r, Uh, n);  // home cell (res == 2 impossible with kc = 0)
     home = res == 1;
