@@ -144,6 +144,7 @@ struct rec_ctx {
   int grid;                  // blocks of the streaming passes
   int alloc_blocks;
   int coop_grid = 0;         // blocks of the cooperative substep kernel (0: not yet queried, -1: unavailable)
+  int newton_tma = 0;        // TMA-staged Newton pass usable (0: not yet queried, 1 / -1)
   void* queue;               // queued packets of the march (3 x 16|32 B each) [n_packets]
   int sm_count;
   bool emis_ready;

@@ -112,7 +112,6 @@ struct CellF32 {
 // a few ulp (the form's tolerance is 1e-4), so divisions, square roots and
 // exponentials use the approximate hardware instructions.
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ float fsqrt(float a) { return a * rsqrtf(a); }  // a > 0
 __device__ __forceinline__ float fexp2(float a) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
@@ -400,6 +399,146 @@ __global__ void __launch_bounds__(NT) k_newton(PassArgs a, const BoxDev* bxs, in
   }
 }
 
+// ---- Newton evaluation of the mixed form with TMA-staged tiles ----------------
+// Persistent CTAs stream tiles of kTmaTile cells of the four per-cell inputs
+// (Delta, the (x, 1 - x) cache, T, tallies) into a ring of kTmaStages shared-memory
+// stages with bulk asynchronous copies (cp.async.bulk, completion counted in bytes
+// on one mbarrier per stage); thread 0 keeps kTmaStages - 1 tiles in flight while
+// the CTA evaluates the current one, so no warp waits on a global load.  Cells
+// past the last whole tile are read directly.  Every wait on a stage barrier
+// is bounded: past kTmaWaitLimit polls the CTA records bit 3 in the flags,
+// waits (bounded) for the copies it issued and leaves without its partial sums.
+constexpr int kTmaTile = 1024;
+constexpr int kTmaStages = 3;
+constexpr int kTmaThreads = 256;
+constexpr uint32_t kTmaWaitLimit = 1u << 22;
+constexpr int kTmaCtasPerSm = 3;  // resident CTAs per SM (shared-memory ring of each)
+
+struct TmaStage {
+  float delta[kTmaTile];
+  float2 xy[kTmaTile];
+  float T[kTmaTile];
+  uint32_t tally[kTmaTile];
+};
+constexpr uint32_t kTmaStageBytes = kTmaTile * (4 + 8 + 4 + 4);
+constexpr size_t kTmaSmem = sizeof(TmaStage) * kTmaStages + 8 * kTmaStages;
+static_assert(sizeof(TmaStage) == kTmaStageBytes, "stage layout");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(b))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a) {
+  DevScalars* sc = a.sc;
+  if (ld_flag(&sc->conv)) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TmaStage* stage = reinterpret_cast<TmaStage*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(TmaStage) * kTmaStages);
+  const double lam = sc->lam;
+  const double G = sc->omC * lam + sc->G0, tot = (double)sc->tally_total, S1s = sc->S1s;
+  const int64_t n_tiles = a.n3 / kTmaTile;  // whole tiles, copied in bulk
+  const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const float* delta = (const float*)a.delta;
+  const float* Tg = (const float*)a.T;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTmaStages; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t it) {  // thread 0: tile `it` of this CTA into its stage
+    const int s = (int)(it % kTmaStages);
+    const int64_t c0 = ((int64_t)blockIdx.x + it * gridDim.x) * kTmaTile;
+    mbar_expect_tx(&full[s], kTmaStageBytes);
+    bulk_load(stage[s].delta, delta + c0, kTmaTile * 4, &full[s]);
+    bulk_load(stage[s].xy, a.xy + c0, kTmaTile * 8, &full[s]);
+    bulk_load(stage[s].T, Tg + c0, kTmaTile * 4, &full[s]);
+    bulk_load(stage[s].tally, a.tally + c0, kTmaTile * 4, &full[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int64_t it = 0; it < my_tiles && it < kTmaStages - 1; ++it) issue(it);
+  Kahan32 s0, s1, s2;
+  const CoefF32 f = coef_f32(a.k);
+  const float Gf = (float)G, lamf = (float)lam;
+  const float wscale = tot > 0.0 ? (float)(S1s / tot) : 0.0f;
+  auto cell = [&](float d, float2 xy, float T, uint32_t tal) {
+    CellF32 c = cell_f32(f, a.k.mixing, d, xy, T, (a.k.mixing == REC_MIX_TALLY) ? tal : 0u, wscale);
+    float xr, yr, dxdG;
+    root_f32(c.A, c.s, Gf, c.xf, c.yf, &xr, &yr, &dxdG);
+    float an2 = c.al * c.n * c.n;
+    s0.add(an2 * xr * xr);
+    s1.add(c.n * yr);
+    s2.add((2.0f * an2 * xr + lamf * c.n) * dxdG);
+  };
+  bool timed_out = false;
+  int64_t it = 0;
+  for (; it < my_tiles; ++it) {
+    if (threadIdx.x == 0 && it + kTmaStages - 1 < my_tiles) {
+      // the stage refilled here was read by every thread before the barrier that ended the last iteration
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(it + kTmaStages - 1);
+    }
+    const int s = (int)(it % kTmaStages);
+    const uint32_t parity = (uint32_t)((it / kTmaStages) & 1);
+    uint32_t polls = 0;
+    while (!mbar_try_wait(&full[s], parity))
+      if (++polls > kTmaWaitLimit) { timed_out = true; break; }
+    if (!timed_out) {
+      const TmaStage& t = stage[s];
+      for (int k = threadIdx.x; k < kTmaTile; k += kTmaThreads) cell(t.delta[k], t.xy[k], t.T[k], t.tally[k]);
+    }
+    if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+  }
+  if (timed_out) {
+    if (threadIdx.x == 0) {
+      atomicOr(&sc->flags, 8);
+      // the copies issued for the tiles it .. it + kTmaStages - 2 may still be in flight
+      for (int64_t j = it; j < my_tiles && j < it + kTmaStages - 1; ++j) {
+        uint32_t polls = 0;
+        while (!mbar_try_wait(&full[j % kTmaStages], (uint32_t)((j / kTmaStages) & 1)) && ++polls < kTmaWaitLimit) {
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  // cells after the last whole tile
+  for (int64_t i = n_tiles * kTmaTile + (int64_t)blockIdx.x * kTmaThreads + threadIdx.x; i < a.n3;
+       i += (int64_t)gridDim.x * kTmaThreads)
+    cell(delta[i], a.xy[i], Tg[i], a.tally[i]);
+  double v[3] = {s0.value(), s1.value(), s2.value()};
+  block_sum<3, kTmaThreads>(v);
+  if (threadIdx.x == 0) {
+    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+  }
+  if (!last_block_done(&sc->counter)) return;
+  double S[3];
+  combine_partials<3, kTmaThreads>(a.part, gridDim.x, kMaxSums, S);
+  if (threadIdx.x == 0) {
+    newton_update(sc, S[0], S[1], S[2], 1e-5);
+    sc->counter = 0;
+  }
+}
+
 // Final pass: new state at the converged lambda, emission weights, sums.
 // st: statistics record (one per box in a batch) or NULL.
 template <bool MIXED, bool MB>
@@ -617,6 +756,22 @@ cudaError_t launch_state_init(rec_ctx* c, double z) {
   return launch_refresh(c, z);
 }
 
+// The TMA-staged Newton pass needs 16-byte aligned streams (bulk copies) and
+// its shared-memory ring; REC_NEWTON=plain selects the grid-stride kernel.
+bool newton_tma_ok(rec_ctx* c, const PassArgs& a) {
+  if (c->newton_tma == 0) {
+    const char* sel = std::getenv("REC_NEWTON");
+    bool ok = !(sel && std::strcmp(sel, "plain") == 0);
+    ok = ok && cudaFuncSetAttribute(k_newton_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) ==
+                   cudaSuccess;
+    ok = ok && kTmaCtasPerSm * c->sm_count <= 2 * c->grid;  // its blocks fit the partials (2 x grid entries)
+    c->newton_tma = ok ? 1 : -1;
+    cudaGetLastError();
+  }
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  return c->newton_tma > 0 && al(a.delta) && al(a.xy) && al(a.T) && al(a.tally);
+}
+
 cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* st) {
   const int ns = c->params.n_sub;
   const bool mixed = c->params.precision == REC_PREC_MIXED;
@@ -652,8 +807,10 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
       continue;
     }
     k_substep_begin<<<1, 32, 0, c->stream>>>(c->sc, k, (double)c->n3);
+    const bool tma = mixed && newton_tma_ok(c, a);
     for (int it = 0; it < kNewtonMaxPasses; ++it) {
-      if (mixed) k_newton<true, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
+      if (tma) k_newton_tma<<<c->sm_count * kTmaCtasPerSm, kTmaThreads, kTmaSmem, c->stream>>>(a);
+      else if (mixed) k_newton<true, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
       else k_newton<false, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
     }
     if (mixed) k_final<true, false><<<c->grid, NT, 0, c->stream>>>(a, st, nullptr, 1);

@@ -60,6 +60,40 @@ def test_single_step_matches_oracle(cosmo, precision, mixing, n, z_from, z_to):
     box.close()
 
 
+@pytest.mark.parametrize("mixing", ["full", "tally"])
+@pytest.mark.parametrize("n", [64, 77])
+def test_mixed_step_tma_newton_matches_oracle(cosmo, mixing, n):
+    """Boxes large enough for the TMA-staged Newton pass of the mixed form
+    (64^3: whole tiles only; 77^3: 445 tiles and a 853-cell tail read directly)."""
+    box = new_box(n, "mixed", mixing, n_packets=1000)
+    rng = np.random.default_rng(n + 1)
+    d, _, _ = oracle_fields(box)
+    x0, T0 = _state(cosmo, d, 1250.0, rng)
+    tally = rng.poisson(20 * d ** 1.5).astype(np.uint32)
+    _check_step(cosmo, box, x0, T0, tally, 1250.0, 1240.0)
+    box.close()
+
+
+def test_tma_and_plain_newton_agree(cosmo, monkeypatch):
+    """The TMA-staged and the grid-stride Newton passes sum the same cells in a
+    different order: the mixed-form state agrees far inside the tolerance."""
+    out = []
+    for sel in ("", "plain"):
+        monkeypatch.setenv("REC_NEWTON", sel)
+        box = new_box(77, "mixed", "tally", n_packets=1000)
+        rng = np.random.default_rng(5)
+        d, _, _ = oracle_fields(box)
+        x0, T0 = _state(cosmo, d, 1150.0, rng)
+        set_state(box, x0, T0, tally=rng.poisson(20 * d ** 1.5).astype(np.uint32))
+        box.refresh(1150.0)
+        box.step(0, 1150.0, 1140.0)
+        out.append((box.host("x"), box.stats()))
+        box.close()
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-6, atol=0)
+    assert out[0][1]["lam"] == pytest.approx(out[1][1]["lam"], rel=1e-6)
+    assert out[0][1]["flags"] == 0 and out[1][1]["flags"] == 0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_full_mixing_trajectory_matches_oracle(cosmo, precision):
     """30 chained steps 1600 -> 900 starting from the GPU's own Saha state;
