@@ -476,9 +476,9 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     groups = {g: v for g, v in mixed["kt"].items() if v[1]}
     dominant = max(("emit", "march", "rec_step", "alloc"), key=lambda g: groups.get(g, (0, 0))[0])
-    names = {"emit": "k_emit<float> (packet emission + home-cell test)",
-             "march": "k_march<float> (march of queued packets)",
-             "rec_step": "rec_step passes (k_newton<1> + k_final<1>)", "alloc": "allocation (3 kernels)"}
+    names = {"emit": "k_emit<float, pow2> (packet emission + home-cell test)",
+             "march": "k_march<float, pow2> (march of queued packets)",
+             "rec_step": "rec_step passes (k_newton_tma + k_final<mixed>)", "alloc": "allocation (3 kernels)"}
 
     def roof(g):
         ms_g = groups[g][0] / K

@@ -109,7 +109,8 @@ typedef struct {
   double S1s;     /* sum over cells of delta (1 - x_e) at the end state */
   int32_t newton_passes; /* Newton evaluations of the last substep */
   int32_t flags;         /* bit 0: Newton did not converge; bit 1: packets hit the crossing cap;
-                            bit 2: non-finite or negative emission weight */
+                            bit 2: non-finite or negative emission weight; bit 3: a bounded
+                            device-side wait expired (copy pipeline of a Newton pass) */
 } rec_stats;
 
 /* Launch and scheduling parameters of the transport: a library setting with
