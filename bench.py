@@ -322,9 +322,11 @@ def time_batched(W, K, prep=60, n_boxes=64):
 
 
 # ------------------------------------------------------------------------ oracle (CPU)
-def oracle_sample(cfg, zs, sample_packets):
+def oracle_sample(cfg, zs, sample_packets, threads=0):
     """The oracle as it stands on one host core: one rec_step over every cell and
-    the transport of `sample_packets` packets of the step; returns seconds."""
+    the transport of `sample_packets` packets of the step; returns seconds.
+    threads > 0: the transport runs in the OpenMP build of the same source on that
+    many threads (the rec_step stays single-threaded)."""
     import oracle as O
     from paper_2312_11448_gb300.inputs import doppler_quantiles, pack_vel4
     cp = O.default_cosmo()
@@ -336,12 +338,28 @@ def oracle_sample(cfg, zs, sample_packets):
     v4 = pack_vel4(U, np.float32)
     t0 = time.perf_counter()
     tally, cnt, _ = O.transport(cp, cfg.n, z, 1, S0, sample_packets, emis.astype(np.float32), v4,
-                                T.astype(np.float32), doppler_quantiles().astype(np.float32), precision="f32")
+                                T.astype(np.float32), doppler_quantiles().astype(np.float32), precision="f32",
+                                threads=threads)
     t_tr = time.perf_counter() - t0
     t0 = time.perf_counter()
     O.rec_step(cp, cfg.n, zs[S0], zs[S0 + 1], delta, x, T, U=U, tally=tally, mixing="tally")
     t_st = time.perf_counter() - t0
     return t_tr, t_st
+
+
+def cpu_baseline_all_cores(cfg, zs, sample_packets=20_000_000):
+    """The OpenMP build of the oracle's transport on every host core (the
+    rec_step single-threaded), same workload and sample scaling."""
+    cores = os.cpu_count() or 1
+    sample_packets = min(sample_packets, cfg.n_packets)
+    t_tr, t_st = oracle_sample(cfg, zs, sample_packets, threads=cores)
+    t_step = t_st + t_tr * (cfg.n_packets / sample_packets)
+    return {"value": cfg.n ** 3 / t_step, "unit": "cell-steps/s", "cores": cores, "kind": "oracle (OpenMP build)",
+            "packets_per_s": sample_packets / t_tr,
+            "sample": (f"OpenMP build of the oracle source: transport of {sample_packets:.0e} of the "
+                       f"{cfg.n_packets:.0e} packets over {cores} threads ({t_tr:.2f} s, scaled linearly) + the "
+                       f"single-threaded oracle rec_step over all {cfg.n}^3 cells ({t_st:.2f} s); "
+                       f"{platform_name()}")}
 
 
 def cpu_baseline(cfg, zs, sample_packets=4_000_000):
@@ -525,6 +543,7 @@ def run_ours(args):
     out["clocks"] = clk
     if world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(cfg, zs)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cfg, zs)
     print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

@@ -40,33 +40,44 @@ def default_cosmo(**kw) -> Cosmo:
     return Cosmo(**p)
 
 
-def lib():
-    global _lib
+_lib_omp = None
+
+
+def lib(openmp=False):
+    """liboracle.so; openmp=True: the OpenMP build of the same source (timing only)."""
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            _lib_omp = _bind(C.CDLL(_build.build(openmp=True)))
+        return _lib_omp
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        d, i64, u32, u64, i = C.c_double, C.c_int64, C.c_uint32, C.c_uint64, C.c_int
-        P = C.POINTER
-        L.orc_background.argtypes = [P(Cosmo), d, P(d)]
-        L.orc_dt.argtypes = [P(Cosmo), d, d]
-        L.orc_dt.restype = d
-        L.orc_rates.argtypes = [P(Cosmo), d, d, P(d)]
-        L.orc_saha_xe.argtypes = [P(Cosmo), d, i64, P(d), P(d)]
-        L.orc_rec_step.argtypes = [P(Cosmo), i, i, i, d, d, P(d), P(d), P(d), P(d), P(u32), P(d), P(d)]
-        L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
-        L.orc_philox4x32_10.restype = None
-        L.orc_transport_params.argtypes = [P(Cosmo), i, d, P(d)]
-        L.orc_allocate_f32.argtypes = [i, P(C.c_float), u64, u64, u32, u32, P(u32)]
-        L.orc_allocate_f64.argtypes = [i, P(d), u64, u64, u32, u32, P(u32)]
-        for name, R in (("orc_transport_f32", C.c_float), ("orc_transport_f64", d)):
-            getattr(L, name).argtypes = [P(Cosmo), i, d, u64, u32, u32, u64, P(R), P(R), P(R), P(R), i,
-                                         P(u32), P(u64), P(Packet), i64]
-        L.orc_traj_objective.argtypes = [P(Cosmo), i, i, i, i, P(d), P(u32), P(d), P(d), P(d), P(d), i, d,
-                                         P(d), P(d)]
-        L.orc_traj_tangent.argtypes = [P(Cosmo), i, i, i, i, P(d), P(u32), P(d), P(d), P(d), P(d), P(d), P(d),
-                                       i, d, P(d)]
-        _lib = L
+        _lib = _bind(C.CDLL(_build.build()))
     return _lib
+
+
+def _bind(L):
+    d, i64, u32, u64, i = C.c_double, C.c_int64, C.c_uint32, C.c_uint64, C.c_int
+    P = C.POINTER
+    L.orc_background.argtypes = [P(Cosmo), d, P(d)]
+    L.orc_dt.argtypes = [P(Cosmo), d, d]
+    L.orc_dt.restype = d
+    L.orc_rates.argtypes = [P(Cosmo), d, d, P(d)]
+    L.orc_saha_xe.argtypes = [P(Cosmo), d, i64, P(d), P(d)]
+    L.orc_rec_step.argtypes = [P(Cosmo), i, i, i, d, d, P(d), P(d), P(d), P(d), P(u32), P(d), P(d)]
+    L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+    L.orc_philox4x32_10.restype = None
+    L.orc_transport_params.argtypes = [P(Cosmo), i, d, P(d)]
+    L.orc_allocate_f32.argtypes = [i, P(C.c_float), u64, u64, u32, u32, P(u32)]
+    L.orc_allocate_f64.argtypes = [i, P(d), u64, u64, u32, u32, P(u32)]
+    for name, R in (("orc_transport_f32", C.c_float), ("orc_transport_f64", d)):
+        getattr(L, name).argtypes = [P(Cosmo), i, d, u64, u32, u32, u64, P(R), P(R), P(R), P(R), i,
+                                     P(u32), P(u64), P(Packet), i64]
+    L.orc_traj_objective.argtypes = [P(Cosmo), i, i, i, i, P(d), P(u32), P(d), P(d), P(d), P(d), i, d,
+                                     P(d), P(d)]
+    L.orc_traj_tangent.argtypes = [P(Cosmo), i, i, i, i, P(d), P(u32), P(d), P(d), P(d), P(d), P(d), P(d),
+                                   i, d, P(d)]
+    L.orc_threads.argtypes = [i]
+    return L
 
 
 def _p(a, ctype):
@@ -153,11 +164,12 @@ def allocate(n, emis, n_packets, seed, step, box=0):
 
 
 def transport(cp: Cosmo, n: int, z: float, seed: int, step: int, n_packets: int, emis, vel4, T, quant, box=0,
-              precision="f32", dump=0):
+              precision="f32", dump=0, threads=0):
     """Ballistic transport; returns (tally, counters dict, packets or None).
 
     precision "f32" runs the binary32 operation sequence, "f64" the binary64 one.
-    vel4 is [n^3, 4] (Ux, Uy, Uz, unused) in km/s.
+    vel4 is [n^3, 4] (Ux, Uy, Uz, unused) in km/s.  threads > 0 runs the OpenMP
+    build on that many threads (same results; host-cores timing only).
     """
     R, ct = (np.float32, C.c_float) if precision == "f32" else (np.float64, C.c_double)
     e = np.ascontiguousarray(emis, dtype=R).ravel()
@@ -167,7 +179,10 @@ def transport(cp: Cosmo, n: int, z: float, seed: int, step: int, n_packets: int,
     tally = np.zeros(e.size, dtype=np.uint32)
     cnt = np.zeros(4, dtype=np.uint64)
     pk = (Packet * dump)() if dump > 0 else None
-    fn = lib().orc_transport_f32 if precision == "f32" else lib().orc_transport_f64
+    L = lib(openmp=threads > 0)
+    if threads > 0:
+        L.orc_threads(int(threads))
+    fn = L.orc_transport_f32 if precision == "f32" else L.orc_transport_f64
     rc = fn(C.byref(cp), n, z, seed, step, box, n_packets, _p(e, ct), _p(v, ct), _p(TT, ct), _p(q, ct), q.size,
             _p(tally, C.c_uint32), _p(cnt, C.c_uint64), pk, dump)
     _check(rc, "transport")

@@ -13,18 +13,27 @@ SOURCES = ["oracle_physics.cpp", "oracle_transport.cpp"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
-def build(force: bool = False) -> str:
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """liboracle.so (the oracle); openmp=True builds liboracle_omp.so, the same
+    source with the transport's cell loop spread over threads, used only to
+    time the oracle on all host cores."""
+    lib = LIB_OMP if openmp else LIB
     srcs = [os.path.join(HERE, s) for s in SOURCES] + [os.path.join(HERE, "oracle.h")]
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(s) <= t for s in srcs):
-            return LIB
+            return lib
+    extra = ["-fopenmp", "-DORACLE_OPENMP"] if openmp else []
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-Wall", "-Wextra", "-o", LIB + ".tmp"] + [os.path.join(HERE, s) for s in SOURCES]
+           "-Wall", "-Wextra"] + extra + ["-o", lib + ".tmp"] + [os.path.join(HERE, s) for s in SOURCES]
     subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
+    print(build(force="--force" in sys.argv, openmp=True))

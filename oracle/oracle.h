@@ -72,6 +72,9 @@ int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_fro
 /* Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11).  Pinned by
  * statistical tests (uniformity, bit balance, avalanche). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Threads of the transport: 1 in the plain build; the OpenMP build (host-cores
+ * timing baseline) sets its thread count to n (> 0) and returns it. */
+int orc_threads(int n);
 
 /* Transport scalars at redshift z for an n^3 box: out[0] = kappa, cells of
  * Hubble drift per km/s of velocity; out[1] = cth, so that the thermal

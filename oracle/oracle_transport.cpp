@@ -15,6 +15,10 @@
 
 #include "oracle.h"
 
+#ifdef ORACLE_OPENMP
+#include <omp.h>
+#endif
+
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -167,6 +171,12 @@ int transport(const orc_cosmo* cp, int n, double z, uint64_t seed, uint32_t step
   const R one = (R)1, two = (R)2;
   uint64_t emitted = 0, absorbed = 0, capped = 0, crossings = 0;
   int64_t ndump = 0;
+  // The OpenMP build of this file (host-cores timing baseline only) spreads the
+  // emitting cells over threads; integer tallies and counters are the same in
+  // any order.  The plain build ignores the pragmas.
+#ifdef ORACLE_OPENMP
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : emitted, absorbed, capped, crossings) if (dump == nullptr)
+#endif
   for (int64_t c = 0; c < n3; ++c) {
     uint32_t np = P[c + 1] - P[c];
     const int hx = (int)(c % n), hy = (int)((c / n) % n), hz = (int)(c / ((int64_t)n * n));
@@ -235,7 +245,13 @@ int transport(const orc_cosmo* cp, int n, double z, uint64_t seed, uint32_t step
         ++kc;
       }
       crossings += kc;
-      if (done) { tally[cell] += 1u; ++absorbed; }
+      if (done) {
+#ifdef ORACLE_OPENMP
+#pragma omp atomic
+#endif
+        tally[cell] += 1u;
+        ++absorbed;
+      }
       else ++capped;
       if (dump && ndump < dump_cap) {
         orc_packet& p = dump[ndump++];
@@ -255,6 +271,16 @@ int transport(const orc_cosmo* cp, int n, double z, uint64_t seed, uint32_t step
 extern "C" {
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) { philox(ctr, key, out); }
+
+int orc_threads(int n) {
+#ifdef ORACLE_OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 int orc_transport_params(const orc_cosmo* cp, int n, double z, double* out) {
   if (!cp || n <= 0 || !out) return -1;

@@ -224,3 +224,15 @@ def test_precisions_agree_statistically(cosmo):
     a, b = out["f32"][0], out["f64"][0]
     z = (a - b) / np.sqrt(np.maximum(a + b, 1.0))
     assert abs(z.mean()) < 0.1 and z.std() < 1.2
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_openmp_build_same_integers(cosmo, precision):
+    """The OpenMP build (used only to time the oracle on all host cores) gives
+    the same tallies and counters as the plain build: integer sums in any order."""
+    n = 16
+    emis, vel4, T, q = _inputs(n, 1.0, seed=9, precision=precision)
+    t1, c1, _ = O.transport(cosmo, n, 1150.0, 5, 3, 150000, emis, vel4, T, q, precision=precision)
+    t4, c4, _ = O.transport(cosmo, n, 1150.0, 5, 3, 150000, emis, vel4, T, q, precision=precision, threads=4)
+    assert np.array_equal(t1, t4) and c1 == c4
+    assert O.lib().orc_threads(0) == 1 and O.lib(openmp=True).orc_threads(4) == 4
