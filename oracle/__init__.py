@@ -77,6 +77,7 @@ def _bind(L):
     L.orc_traj_tangent.argtypes = [P(Cosmo), i, i, i, i, P(d), P(u32), P(d), P(d), P(d), P(d), P(d), P(d),
                                    i, d, P(d)]
     L.orc_threads.argtypes = [i]
+    L.orc_divergence.argtypes = [P(Cosmo), i, d, P(d), P(d)]
     return L
 
 
@@ -128,13 +129,21 @@ def rec_step(cp: Cosmo, n: int, z_from: float, z_to: float, delta, x, T, U=None,
     t = None if tally is None else np.ascontiguousarray(tally, dtype=np.uint32).ravel()
     em = np.empty_like(d) if want_emis else None
     st = np.zeros(6)
-    mix = {"tally": 0, "full": 1}[mixing]
+    mix = {"tally": 0, "full": 1, "local": 2}[mixing]
     rc = lib().orc_rec_step(C.byref(cp), n, mix, n_sub, z_from, z_to, _p(d, C.c_double), _p(x1, C.c_double),
                             _p(T1, C.c_double), _p(U1, C.c_double), _p(t, C.c_uint32), _p(em, C.c_double),
                             _p(st, C.c_double))
     _check(rc, "rec_step")
     stats = dict(lam=st[0], C=st[1], Xe=st[2], iters=int(st[3]), S1s=st[4], dt=st[5])
     return x1, T1, U1, em, stats
+
+
+def divergence(cp: Cosmo, n: int, z: float, U) -> np.ndarray:
+    """Physical velocity divergence per cell (1/s) as the local mode uses it."""
+    u = _f64(U).reshape(-1, 3)
+    out = np.zeros(u.shape[0])
+    _check(lib().orc_divergence(C.byref(cp), n, z, _p(u, C.c_double), _p(out, C.c_double)), "divergence")
+    return out
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

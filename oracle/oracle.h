@@ -59,7 +59,9 @@ int orc_saha_xe(const orc_cosmo* cp, double z, int64_t n3, const double* delta, 
 /* One recombination step z_from -> z_to in n_sub substeps (Sec. IV, Eq.
  * dotne-mix; Eq. Tb-evolution; Eq. alpha-def).  mixing: 0 = TALLY (local 2s
  * population from the absorbed-Ly-alpha tallies), 1 = FULL (the paper's
- * full-mixing limit).  In/out: x (ionisation fraction), T (K), U ([n^3][3],
+ * full-mixing limit), 2 = LOCAL (the no-mixing limit of Sec. III.A.2: Eq. rec
+ * per cell with H -> H + div v / 3 in Eq. R-alpha; div v from U, zero if U is
+ * NULL; stats[1] = volume mean of the local C, stats[3] = 0).  In/out: x (ionisation fraction), T (K), U ([n^3][3],
  * km/s, may be NULL).  tally may be NULL in FULL mode.  emis (may be NULL)
  * receives alpha_e n_e^2 at the end state.  stats[0]=lambda, [1]=C_mix,
  * [2]=X_e, [3]=Newton iterations of the last substep, [4]=S_1s used,
@@ -68,6 +70,11 @@ int orc_saha_xe(const orc_cosmo* cp, double z, int64_t n3, const double* delta, 
 int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_from, double z_to,
                  const double* delta, double* x, double* T, double* U, const uint32_t* tally,
                  double* emis, double* stats);
+
+/* Physical divergence of the peculiar velocity U ([n^3][3], km/s) at redshift
+ * z, 1/s: periodic central differences on the comoving grid of side L_box,
+ * times 1 + z.  Pinned by the closed form for sinusoidal fields. */
+int orc_divergence(const orc_cosmo* cp, int n, double z, const double* U, double* div);
 
 /* Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11).  Pinned by
  * statistical tests (uniformity, bit balance, avalanche). */

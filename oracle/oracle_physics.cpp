@@ -8,6 +8,7 @@
 
 #include "oracle.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -130,6 +131,26 @@ double beta_e(const Cosmo& c, double Tg) {
   return alpha_e<double>(c, Tg) * saha_phase(Tg) * std::exp(-kE2s / (kKB * Tg));
 }
 
+// Physical divergence of the peculiar velocity per cell, 1/s: central
+// differences of U (km/s, [n^3][3]) over the periodic grid, comoving cell side
+// h = L / n, and 1/a = 1 + z from comoving to physical gradients.
+void local_divergence(int n, const double* U, double L_m, double z, double* div) {
+  const int64_t n3 = (int64_t)n * n * n;
+  const double h = L_m / (double)n;  // m, comoving
+  const double fac = (1.0 + z) * 1.0e3 / (2.0 * h);
+  for (int64_t c = 0; c < n3; ++c) {
+    const int ix = (int)(c % n), iy = (int)((c / n) % n), iz = (int)(c / ((int64_t)n * n));
+    auto at = [&](int x, int y, int zz) {
+      x = (x + n) % n; y = (y + n) % n; zz = (zz + n) % n;
+      return ((int64_t)zz * n + y) * n + x;
+    };
+    const double dux = U[3 * at(ix + 1, iy, iz) + 0] - U[3 * at(ix - 1, iy, iz) + 0];
+    const double duy = U[3 * at(ix, iy + 1, iz) + 1] - U[3 * at(ix, iy - 1, iz) + 1];
+    const double duz = U[3 * at(ix, iy, iz + 1) + 2] - U[3 * at(ix, iy, iz - 1) + 2];
+    div[c] = fac * (dux + duy + duz);
+  }
+}
+
 // ---- one substep of the recombination update --------------------------------
 template <class R>
 struct SubStats {
@@ -160,7 +181,7 @@ R be_root(R A, R s, R G, R x_old, R* dxdG) {
 //   delta: overdensity rho_b/<rho_b> (Sec. II.C), static.
 //   afrac: absorbed-Ly-alpha fraction per cell (TALLY mode) or null.
 template <class R>
-void substep(const Cosmo& cm, int64_t n3, int mixing, double za, double zb, const R* delta, R* x, R* T,
+void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double za, double zb, const R* delta, R* x, R* T,
              double* U, const R* afrac, R* emis, SubStats<R>* st) {
   const double H = hubble(cm, zb);
   const double nH = nH_bar(cm, zb);
@@ -208,6 +229,49 @@ void substep(const Cosmo& cm, int64_t n3, int mixing, double za, double zb, cons
       if (val(S) > 0.0 && val(n1s_rel) > 0.0) w = afrac[i] * S / n1s_rel;
     }
     s[i] = dt * w;
+  }
+
+  if (mixing == 2) {
+    // No-mixing limit (Sec. III.A.2): recombination is local, Eq. (rec) with the
+    // cell's own n_e and n_1s, and R_alpha of Eq. (R-alpha) with H -> H + div v / 3
+    // (div v of the substep-start velocities).  Reading where the paper asks for
+    // care: a flow converging faster than the expansion (H + div v/3 < 0) lets no
+    // Ly-alpha photon escape, R_alpha = 0.  C per cell uses the substep-start n_1s
+    // (as R_alpha^mix does with <n_1s>); no global lambda.
+    std::vector<double> div(n3, 0.0);
+    if (U != nullptr) local_divergence(n, U, cm.L_m, zb, div.data());
+    const double KR0 = 8.0 * kPi / (kLambdaAlpha * kLambdaAlpha * kLambdaAlpha);
+    R sx = 0.0, sd = 0.0, sC = 0.0, num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < n3; ++i) {
+      const double Heff = std::max(H + div[i] / 3.0, 0.0);
+      const R n1s = nn[i] * (1.0 - x[i]);
+      R Ci = 1.0;
+      if (val(n1s) > 0.0) {
+        R Ri = KR0 * Heff / n1s;
+        Ci = (kLambda2g + Ri) / (beta + kLambda2g + Ri);
+      }
+      // dx/dt = -C (alpha n_H x^2 - beta e_alpha (1 - x)), backward Euler
+      R xr = be_root<R>(dt * Ci * al[i] * nn[i], dt * Ci, R(beta * ea), x[i], nullptr);
+      if (U != nullptr) {
+        double damp = std::exp(-(kd * val(xr) + H) * dt);
+        U[3 * i + 0] *= damp; U[3 * i + 1] *= damp; U[3 * i + 2] *= damp;
+      }
+      x[i] = xr;
+      T[i] = Tn[i];
+      if (emis) emis[i] = al[i] * (nn[i] * xr) * (nn[i] * xr);
+      sx += delta[i] * xr;
+      sd += delta[i];
+      sC += Ci;
+      num += al[i] * nn[i] * nn[i] * xr * xr;
+      den += nn[i] * (1.0 - xr);
+    }
+    st->lambda = num / den;
+    st->C = sC / (double)n3;  // volume mean of the local Peebles factors
+    st->Xe = sx / sd;
+    st->S1s = S;
+    st->iters = 0;
+    st->dt = dt;
+    return;
   }
 
   const R CBe = C * beta * ea;
@@ -279,10 +343,11 @@ double sub_z(double z_from, double z_to, int k, int n_sub) {
 }
 
 template <class R>
-void rec_step_t(const Cosmo& cm, int64_t n3, int mixing, int n_sub, double z_from, double z_to,
+void rec_step_t(const Cosmo& cm, int n, int mixing, int n_sub, double z_from, double z_to,
                 const R* delta, R* x, R* T, double* U, const R* afrac, R* emis, SubStats<R>* st) {
+  const int64_t n3 = (int64_t)n * n * n;
   for (int k = 0; k < n_sub; ++k)
-    substep<R>(cm, n3, mixing, sub_z(z_from, z_to, k, n_sub), sub_z(z_from, z_to, k + 1, n_sub), delta, x, T,
+    substep<R>(cm, n, n3, mixing, sub_z(z_from, z_to, k, n_sub), sub_z(z_from, z_to, k + 1, n_sub), delta, x, T,
                U, afrac, emis, st);
 }
 
@@ -316,7 +381,7 @@ R trajectory(const Cosmo& cm, int n, int mixing, int n_sub, int n_steps, const d
       }
     }
     SubStats<R> st;
-    rec_step_t<R>(cm, n3, mixing, n_sub, zs[s], zs[s + 1], delta, x.data(), T.data(), nullptr, afp, nullptr, &st);
+    rec_step_t<R>(cm, n, mixing, n_sub, zs[s], zs[s + 1], delta, x.data(), T.data(), nullptr, afp, nullptr, &st);
     Xe[s + 1] = st.Xe;
   }
   if (Xe_hist)
@@ -381,7 +446,7 @@ int orc_saha_xe(const orc_cosmo* cp, double z, int64_t n3, const double* delta, 
 int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_from, double z_to,
                  const double* delta, double* x, double* T, double* U, const uint32_t* tally, double* emis,
                  double* stats) {
-  if (!cp || n <= 0 || n_sub <= 0 || !delta || !x || !T || !(z_from > z_to) || (mixing != 0 && mixing != 1))
+  if (!cp || n <= 0 || n_sub <= 0 || !delta || !x || !T || !(z_from > z_to) || mixing < 0 || mixing > 2)
     return -1;
   Cosmo c = make_cosmo(cp);
   int64_t n3 = (int64_t)n * n * n;
@@ -397,7 +462,7 @@ int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_fro
     }
   }
   SubStats<double> st;
-  rec_step_t<double>(c, n3, mixing, n_sub, z_from, z_to, delta, x, T, U, afp, emis, &st);
+  rec_step_t<double>(c, n, mixing, n_sub, z_from, z_to, delta, x, T, U, afp, emis, &st);
   if (stats) {
     stats[0] = st.lambda;
     stats[1] = st.C;
@@ -406,6 +471,13 @@ int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_fro
     stats[4] = st.S1s;
     stats[5] = st.dt;
   }
+  return 0;
+}
+
+int orc_divergence(const orc_cosmo* cp, int n, double z, const double* U, double* div) {
+  if (!cp || n <= 0 || !U || !div) return -1;
+  Cosmo c = make_cosmo(cp);
+  local_divergence(n, U, c.L_m, z, div);
   return 0;
 }
 
