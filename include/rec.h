@@ -64,8 +64,12 @@ typedef enum { REC_PREC_FP64 = 0, REC_PREC_MIXED = 1 } rec_precision;
 /* REC_MIX_TALLY: the local 2s population follows the Ly-alpha packets absorbed
  *   in each cell during this step's transport (J_i proportional to absorptions
  *   per neutral atom).  REC_MIX_FULL: the paper's full-mixing limit,
- *   Eq. dotne-mix (tallies unused). */
-typedef enum { REC_MIX_TALLY = 0, REC_MIX_FULL = 1 } rec_mixing;
+ *   Eq. dotne-mix (tallies unused).  REC_MIX_LOCAL: the no-mixing limit of
+ *   Sec. III.A.2 — Eq. rec per cell with the cell's own n_e and n_1s and
+ *   Eq. R-alpha with H -> H + div v / 3 (div v by periodic central differences
+ *   of the substep-start velocities; no escape where H + div v / 3 < 0); tallies
+ *   unused.  REC_MIX_LOCAL needs a single-box context and has no adjoint. */
+typedef enum { REC_MIX_TALLY = 0, REC_MIX_FULL = 1, REC_MIX_LOCAL = 2 } rec_mixing;
 
 typedef struct {
   /* Cosmology, Sec. II.C defaults: 0.67, 0.0224, 0.12, 0.24. */
@@ -105,7 +109,8 @@ typedef struct {
   uint64_t queued;  /* packets that left their home cell (marched by the second kernel) */
   double X_e;     /* <rho_b x_e>/<rho_b> after the last rec_step (Sec. II.A) */
   double lambda;  /* <alpha_e n_e^2>/<n_1s> at the end state, 1/s */
-  double C_mix;   /* Peebles factor with R_alpha -> R_alpha^mix (Eq. Cfactor, Sec. IV.B) */
+  double C_mix;   /* Peebles factor with R_alpha -> R_alpha^mix (Eq. Cfactor, Sec. IV.B);
+                     REC_MIX_LOCAL: the volume mean of the cells' own factors */
   double S1s;     /* sum over cells of delta (1 - x_e) at the end state */
   int32_t newton_passes; /* Newton evaluations of the last substep */
   int32_t flags;         /* bit 0: Newton did not converge; bit 1: packets hit the crossing cap;

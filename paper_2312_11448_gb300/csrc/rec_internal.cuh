@@ -136,6 +136,7 @@ struct rec_ctx {
   uint32_t* P;               // packet prefix [n3 + 1]
   uint32_t* first;           // cell of every 32nd packet [n_packets/32 + 1]
   void* xy;                  // mixed form: binary32 (x, 1 - x) cache of the state [n3]
+  void* div;                 // local mixing: velocity divergence per cell, 1/s (float | double) [n3]
   unsigned long long* bcap;  // march-queue bucket capacities / offsets [super-tiles]
   unsigned long long* bfill; // packets queued per bucket [super-tiles]
   unsigned long long* cpre;  // first march chunk of each bucket [super-tiles + 1]

@@ -559,6 +559,147 @@ __global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st, const B
   if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st ? st + box : nullptr);
 }
 
+// ---------------------------------------------------------- no-mixing limit
+// Sec. III.A.2: recombination local to each cell, Eq. (rec) with the cell's own
+// n_e, n_1s and Eq. (R-alpha) at H + div v / 3.  k_divergence takes the
+// physical divergence of the substep-start velocities (periodic central
+// differences, fac = (1 + z) 1e3 / (2 h) with U in km/s and the comoving cell
+// side h in m); k_local then updates every cell on its own (no global lambda).
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_divergence(const void* vel4, int n, double fac, void* div) {
+  const int64_t n3 = (int64_t)n * n * n;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t c = (int64_t)blockIdx.x * NT + threadIdx.x; c < n3; c += stride) {
+    const int ix = (int)(c % n), iy = (int)((c / n) % n), iz = (int)(c / ((int64_t)n * n));
+    const int xp = ix + 1 == n ? 0 : ix + 1, xm = ix == 0 ? n - 1 : ix - 1;
+    const int yp = iy + 1 == n ? 0 : iy + 1, ym = iy == 0 ? n - 1 : iy - 1;
+    const int zp = iz + 1 == n ? 0 : iz + 1, zm = iz == 0 ? n - 1 : iz - 1;
+    const int64_t nn = (int64_t)n * n, row = (int64_t)iz * nn + (int64_t)iy * n;
+    const int64_t cxp = row + xp, cxm = row + xm;
+    const int64_t cyp = (int64_t)iz * nn + (int64_t)yp * n + ix, cym = (int64_t)iz * nn + (int64_t)ym * n + ix;
+    const int64_t czp = (int64_t)zp * nn + (int64_t)iy * n + ix, czm = (int64_t)zm * nn + (int64_t)iy * n + ix;
+    if (MIXED) {
+      const float4* U = (const float4*)vel4;
+      const float d = (U[cxp].x - U[cxm].x) + (U[cyp].y - U[cym].y) + (U[czp].z - U[czm].z);
+      ((float*)div)[c] = (float)fac * d;
+    } else {
+      const double4_32a* U = (const double4_32a*)vel4;
+      const double d = (U[cxp].x - U[cxm].x) + (U[cyp].y - U[cym].y) + (U[czp].z - U[czm].z);
+      ((double*)div)[c] = fac * d;
+    }
+  }
+}
+
+// Local Peebles factor from the substep-start n_1s and H + div v / 3 (no
+// escape when the flow converges faster than the expansion).
+__device__ __forceinline__ double local_C(const StepCoef& k, double div, double n1s) {
+  const double Heff = fmax(k.H + div / 3.0, 0.0);
+  if (!(n1s > 0.0)) return 1.0;
+  const double R = (k.KR / k.H) * Heff / n1s;
+  return (k.L2g + R) / (k.beta + k.L2g + R);
+}
+__device__ __forceinline__ float local_C_f32(const StepCoef& k, float div, float n1s) {
+  const float Heff = fmaxf((float)k.H + div / 3.0f, 0.0f);
+  if (!(n1s > 0.0f)) return 1.0f;
+  const float R = fdiv((float)(k.KR / k.H) * Heff, n1s);
+  return fdiv((float)k.L2g + R, (float)(k.beta + k.L2g) + R);
+}
+
+// One local substep over all cells: x, T (and the (x, 1 - x) cache), Compton
+// drag, emission weights, tally reset on the last substep; sums for the
+// statistics (X_e, lambda of the end state, mean C).
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_local(PassArgs a, const void* div, rec_stats* st) {
+  DevScalars* sc = a.sc;
+  const StepCoef& k = a.k;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  const bool zero_tally = k.last != 0;
+  const double bea = k.beta * k.ea;
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // S1s, Sdx, Sd, sum alpha n^2 x^2, sum n (1-x), sum C
+  if (!MIXED) {
+    const double* delta = (const double*)a.delta;
+    double* T = (double*)a.T;
+    double4_32a* U = (double4_32a*)a.vel4;
+    double* emis = (double*)a.emis;
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+      const double d = delta[i], x = a.x[i];
+      CellF64 c = cell_f64(k, d, x, T[i], 0u, 0.0, 0.0);
+      const double Ci = local_C(k, ((const double*)div)[i], c.n * (1.0 - x));
+      // dx/dt = -C (alpha n_H x^2 - beta e_alpha (1 - x)), backward Euler
+      const double xr = root_f64(c.A * Ci, c.s * Ci, bea, x, nullptr);
+      const double damp = exp(-(k.kd * xr + k.H) * k.dt);
+      double4_32a u = U[i];
+      u.x *= damp; u.y *= damp; u.z *= damp;
+      U[i] = u;
+      a.x[i] = xr;
+      T[i] = c.Tn;
+      emis[i] = c.al * (c.n * xr) * (c.n * xr);
+      if (zero_tally) a.tally[i] = 0u;
+      v[0] += d * (1.0 - xr);
+      v[1] += d * xr;
+      v[2] += d;
+      v[3] += c.al * c.n * c.n * xr * xr;
+      v[4] += c.n * (1.0 - xr);
+      v[5] += Ci;
+    }
+  } else {
+    Kahan32 s0, s1, s2, s3, s4, s5;
+    const CoefF32 f = coef_f32(k);
+    const float* delta = (const float*)a.delta;
+    float* T = (float*)a.T;
+    float4* U = (float4*)a.vel4;
+    float* emis = (float*)a.emis;
+    const float kdf = (float)k.kd, Hf = (float)k.H, dtf = (float)k.dt, beaf = (float)bea;
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += stride) {
+      const float d = delta[i];
+      const double x = a.x[i];
+      CellF32 c = cell_f32(f, REC_MIX_FULL, d, a.xy[i], T[i], 0u, 0.0f);
+      const float Ci = local_C_f32(k, ((const float*)div)[i], c.n * c.yf);
+      const float A = c.A * Ci, sG = c.s * Ci * beaf;
+      // binary32 roots and the binary64 increment of the state, as in k_final
+      const float B = 1.0f + sG;
+      const float sq = __fsqrt_rn(B * B + 4.0f * A * (c.xf + sG));
+      const float xr = __fdiv_rn(2.0f * (c.xf + sG), B + sq);
+      const float yr = __fdiv_rn(2.0f * (A + c.yf), 2.0f * A + B + sq);
+      const double y = 1.0 - x;
+      const double r0 = fma((double)A, x * x, -(double)sG * y);
+      const float dx = fdiv(-2.0f * __double2float_rn(r0), 2.0f * A * c.xf + B + sq);
+      const float damp = __expf(-(kdf * xr + Hf) * dtf);
+      float4 u = U[i];
+      u.x *= damp; u.y *= damp; u.z *= damp;
+      U[i] = u;
+      a.x[i] = x + (double)dx;
+      a.xy[i] = make_float2(xr, yr);
+      T[i] = c.Tn;
+      const float ne = c.n * xr;
+      emis[i] = c.al * ne * ne;
+      if (zero_tally) a.tally[i] = 0u;
+      s0.add(d * yr);
+      s1.add(d * xr);
+      s2.add(d);
+      s3.add(c.al * ne * ne);
+      s4.add(c.n * yr);
+      s5.add(Ci);
+    }
+    v[0] = s0.value(); v[1] = s1.value(); v[2] = s2.value(); v[3] = s3.value(); v[4] = s4.value(); v[5] = s5.value();
+  }
+  block_sum<6, NT>(v);
+  if (threadIdx.x == 0) {
+    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    for (int j = 0; j < 6; ++j) p[j] = v[j];
+  }
+  if (!last_block_done(&sc->counter)) return;
+  double S[6];
+  combine_partials<6, NT>(a.part, gridDim.x, kMaxSums, S);
+  if (threadIdx.x == 0) {
+    const double lam = S[4] > 0.0 ? S[3] / S[4] : 0.0;
+    sc->C = S[5] / (double)a.n3;
+    sc->passes = 0;
+    const double S3[3] = {S[0], S[1], S[2]};
+    finish_substep(sc, k, S3, lam, st);
+  }
+}
+
 // A whole substep in one cooperative launch: Newton evaluations separated by
 // grid barriers until converged, then the final pass.  Every block combines
 // the block partials itself, in the same fixed order, so all blocks take the
@@ -792,7 +933,9 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
     cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, 0);
     c->coop_grid = (attr && per_sm > 0) ? std::min(c->grid, per_sm * c->sm_count) : -1;
   }
-  GroupTimer t(c, kTStep, c->coop_grid > 0 ? ns : ns * (kNewtonMaxPasses + 2));
+  if (c->params.mixing == REC_MIX_LOCAL) c->coop_grid = -1;  // one pass per substep, no Newton
+  GroupTimer t(c, kTStep, c->params.mixing == REC_MIX_LOCAL ? 2 * ns
+                                                            : (c->coop_grid > 0 ? ns : ns * (kNewtonMaxPasses + 2)));
   for (int s = 0; s < ns; ++s) {
     double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
     double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
@@ -804,6 +947,17 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
       cudaError_t e = cudaLaunchCooperativeKernel(mixed ? (void*)k_substep_coop<true> : (void*)k_substep_coop<false>,
                                                   c->coop_grid, NT, args, 0, c->stream);
       if (e != cudaSuccess) return e;
+      continue;
+    }
+    if (c->params.mixing == REC_MIX_LOCAL) {
+      const double fac = (1.0 + zb) * 1.0e3 / (2.0 * c->cosmo.L_m / c->box.n);
+      if (mixed) {
+        k_divergence<true><<<c->grid, NT, 0, c->stream>>>(c->box.vel4, c->box.n, fac, c->div);
+        k_local<true><<<c->grid, NT, 0, c->stream>>>(a, c->div, st);
+      } else {
+        k_divergence<false><<<c->grid, NT, 0, c->stream>>>(c->box.vel4, c->box.n, fac, c->div);
+        k_local<false><<<c->grid, NT, 0, c->stream>>>(a, c->div, st);
+      }
       continue;
     }
     k_substep_begin<<<1, 32, 0, c->stream>>>(c->sc, k, (double)c->n3);

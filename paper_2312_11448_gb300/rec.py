@@ -22,7 +22,7 @@ from . import build as _build
 
 REC_OK, REC_EINVAL, REC_ENOMEM, REC_ECUDA, REC_ETIMEOUT, REC_ESTATE = range(6)
 PREC = {"fp64": 0, "mixed": 1}
-MIXING = {"tally": 0, "full": 1}
+MIXING = {"tally": 0, "full": 1, "local": 2}
 _lib = None
 
 

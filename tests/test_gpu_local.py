@@ -1,0 +1,90 @@
+"""GPU no-mixing (local) limit against the oracle, element by element: x_e, T,
+damped velocities and emission weights within 1e-9 (FP64 form) / 1e-4 (mixed
+form) on ragged boxes, with flows strong enough that some cells converge
+faster than the expansion (no escape) and others diverge strongly; substeps
+and a short trajectory; the cases that are rejected."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import new_box, oracle_fields, set_state
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "mixed": 1e-4}
+
+
+def _state(cosmo, d, z, rng):
+    x = np.clip(O.saha_xe(cosmo, z, d) * rng.uniform(0.9, 1.3, d.size), 1e-6, 0.999)
+    T = O.background(cosmo, z)["Tg"] * (1.0 + 0.01 * rng.standard_normal(d.size))
+    return x, T
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,sigma_v", [(13, 15.0), (32, 4.0)])
+@pytest.mark.parametrize("z_from,z_to,n_sub", [(1500.0, 1490.0, 1), (1150.0, 1140.0, 3), (900.0, 895.0, 1)])
+def test_local_step_matches_oracle(cosmo, precision, n, sigma_v, z_from, z_to, n_sub):
+    box = new_box(n, precision, "local", sigma_v=sigma_v, n_sub=n_sub)
+    rng = np.random.default_rng(n + int(z_from))
+    d, U, _ = oracle_fields(box)
+    H = O.background(cosmo, z_to)["H"]
+    div = O.divergence(cosmo, n, z_to, U)
+    assert (div / 3 < -H).any() and (div / 3 > H).any()  # both regimes present
+    x0, T0 = _state(cosmo, d, z_from, rng)
+    set_state(box, x0, T0, tally=rng.integers(0, 5, n ** 3).astype(np.uint32))
+    T_in = box.host("T").astype(np.float64)
+    box.refresh(z_from)
+    box.step(0, z_from, z_to)
+    st = box.stats()
+    x1, T1, U1, e1, so = O.rec_step(cosmo, n, z_from, z_to, d, x0, T_in, U=U, mixing="local", n_sub=n_sub)
+    tol = TOL[precision]
+    np.testing.assert_allclose(box.host("x"), x1, rtol=tol, atol=0)
+    np.testing.assert_allclose(box.host("T").astype(np.float64), T1, rtol=tol, atol=0)
+    np.testing.assert_allclose(box.host("vel4")[:, :3].astype(np.float64), U1, rtol=tol, atol=1e-12)
+    np.testing.assert_allclose(box.host("emis").astype(np.float64), e1, rtol=3 * max(tol, 1e-6), atol=0)
+    assert st["X_e"] == pytest.approx(so["Xe"], rel=tol)
+    assert st["C"] == pytest.approx(so["C"], rel=tol)
+    assert st["lam"] == pytest.approx(so["lam"], rel=10 * tol)
+    assert st["newton_passes"] == 0 and st["flags"] == 0
+    assert box.tally_np().sum() == 0  # tallies unused, reset at the end of the step
+    box.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_local_trajectory_with_transport(cosmo, precision):
+    """Ten steps with transport between them (tallies play no part in the local
+    update): the GPU state stays within the tolerance of the oracle started
+    from the same Saha state, and the transport keeps conserving packets."""
+    from paper_2312_11448_gb300.inputs import z_schedule
+    n = 16
+    box = new_box(n, precision, "local", n_packets=50_000, sigma_v=3.0)
+    zs = z_schedule(1300.0, 1200.0, 10)
+    d, U, _ = oracle_fields(box)
+    box.state_init(zs[0])
+    x = O.saha_xe(cosmo, zs[0], d)
+    T = np.full(n ** 3, O.background(cosmo, zs[0])["Tg"])
+    for s in range(10):
+        box.transport(s, zs[s])
+        st = box.stats()
+        assert st["emitted"] == st["absorbed"] + st["capped"] == 50_000
+        box.step(s, zs[s], zs[s + 1])
+        x, T, U, _, _ = O.rec_step(cosmo, n, zs[s], zs[s + 1], d, x, T, U=U, mixing="local")
+    tol = 10 * TOL[precision]
+    np.testing.assert_allclose(box.host("x"), x, rtol=tol, atol=0)
+    np.testing.assert_allclose(box.host("T").astype(np.float64), T, rtol=tol, atol=0)
+    box.close()
+
+
+def test_local_mode_rejections():
+    from gpu_helpers import make_fields
+    from paper_2312_11448_gb300 import rec
+    d, U = make_fields(8, 0.5, 1.0, seed=2)
+    with pytest.raises(rec.RecError, match="single-box"):
+        rec.Batch([(8, d, U, 10), (8, d, U, 10)], precision="fp64", mixing="local")
+    box = new_box(8, "fp64", "local")
+    with pytest.raises(rec.RecError, match="tally and full"):
+        box.step_noalloc(1400.0, 1390.0)
+    x = box.x
+    with pytest.raises(rec.RecError, match="tally and full"):
+        box.xe_adjoint(x, 1.0, x.clone(), x.clone())
+    box.close()
