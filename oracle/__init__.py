@@ -63,7 +63,7 @@ def _bind(L):
     L.orc_dt.restype = d
     L.orc_rates.argtypes = [P(Cosmo), d, d, P(d)]
     L.orc_saha_xe.argtypes = [P(Cosmo), d, i64, P(d), P(d)]
-    L.orc_rec_step.argtypes = [P(Cosmo), i, i, i, d, d, P(d), P(d), P(d), P(d), P(u32), P(d), P(d)]
+    L.orc_rec_step.argtypes = [P(Cosmo), i, i, i, d, d, P(d), P(d), P(d), P(d), P(u32), P(d), P(d), d]
     L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
     L.orc_philox4x32_10.restype = None
     L.orc_transport_params.argtypes = [P(Cosmo), i, d, P(d)]
@@ -120,7 +120,7 @@ def saha_xe(cp: Cosmo, z: float, delta) -> np.ndarray:
 
 
 def rec_step(cp: Cosmo, n: int, z_from: float, z_to: float, delta, x, T, U=None, tally=None, mixing="tally",
-             n_sub=1, want_emis=True):
+             n_sub=1, want_emis=True, f_alpha=1.0):
     """One step; returns (x', T', U', emis, stats).  Inputs are not modified."""
     d = _f64(delta).ravel()
     x1 = _f64(x).ravel().copy()
@@ -129,10 +129,10 @@ def rec_step(cp: Cosmo, n: int, z_from: float, z_to: float, delta, x, T, U=None,
     t = None if tally is None else np.ascontiguousarray(tally, dtype=np.uint32).ravel()
     em = np.empty_like(d) if want_emis else None
     st = np.zeros(6)
-    mix = {"tally": 0, "full": 1, "local": 2}[mixing]
+    mix = {"tally": 0, "full": 1, "local": 2, "partial": 3}[mixing]
     rc = lib().orc_rec_step(C.byref(cp), n, mix, n_sub, z_from, z_to, _p(d, C.c_double), _p(x1, C.c_double),
                             _p(T1, C.c_double), _p(U1, C.c_double), _p(t, C.c_uint32), _p(em, C.c_double),
-                            _p(st, C.c_double))
+                            _p(st, C.c_double), float(f_alpha))
     _check(rc, "rec_step")
     stats = dict(lam=st[0], C=st[1], Xe=st[2], iters=int(st[3]), S1s=st[4], dt=st[5])
     return x1, T1, U1, em, stats

@@ -61,7 +61,9 @@ int orc_saha_xe(const orc_cosmo* cp, double z, int64_t n3, const double* delta, 
  * population from the absorbed-Ly-alpha tallies), 1 = FULL (the paper's
  * full-mixing limit), 2 = LOCAL (the no-mixing limit of Sec. III.A.2: Eq. rec
  * per cell with H -> H + div v / 3 in Eq. R-alpha; div v from U, zero if U is
- * NULL; stats[1] = volume mean of the local C, stats[3] = 0).  In/out: x (ionisation fraction), T (K), U ([n^3][3],
+ * NULL; stats[1] = volume mean of the local C, stats[3] = 0), 3 = PARTIAL (the
+ * fraction f_alpha in [0, 1] of the full-mixing rate plus 1 - f_alpha of the
+ * local one; f_alpha is read in this mode only).  In/out: x (ionisation fraction), T (K), U ([n^3][3],
  * km/s, may be NULL).  tally may be NULL in FULL mode.  emis (may be NULL)
  * receives alpha_e n_e^2 at the end state.  stats[0]=lambda, [1]=C_mix,
  * [2]=X_e, [3]=Newton iterations of the last substep, [4]=S_1s used,
@@ -69,7 +71,7 @@ int orc_saha_xe(const orc_cosmo* cp, double z, int64_t n3, const double* delta, 
  * two-zone ODE system and the global-rate identity. */
 int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_from, double z_to,
                  const double* delta, double* x, double* T, double* U, const uint32_t* tally,
-                 double* emis, double* stats);
+                 double* emis, double* stats, double f_alpha);
 
 /* Physical divergence of the peculiar velocity U ([n^3][3], km/s) at redshift
  * z, 1/s: periodic central differences on the comoving grid of side L_box,

@@ -181,8 +181,9 @@ R be_root(R A, R s, R G, R x_old, R* dxdG) {
 //   delta: overdensity rho_b/<rho_b> (Sec. II.C), static.
 //   afrac: absorbed-Ly-alpha fraction per cell (TALLY mode) or null.
 template <class R>
-void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double za, double zb, const R* delta, R* x, R* T,
-             double* U, const R* afrac, R* emis, SubStats<R>* st) {
+void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double fmix, double za, double zb, const R* delta, R* x,
+             R* T, double* U, const R* afrac, R* emis, SubStats<R>* st) {
+  if (mixing == 3 && !(fmix > 0.0)) mixing = 2;  // no full-mixing share: the local mode
   const double H = hubble(cm, zb);
   const double nH = nH_bar(cm, zb);
   const double Tg = T_gamma(cm, zb);
@@ -231,6 +232,35 @@ void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double za, double z
     s[i] = dt * w;
   }
 
+  // Local Peebles factor of cell i (modes 2 and 3): R_alpha of Eq. (R-alpha) with
+  // the cell's substep-start n_1s and H + div v / 3, zero below zero.
+  std::vector<double> div;
+  if (mixing == 2 || mixing == 3) {
+    div.assign(n3, 0.0);
+    if (U != nullptr) local_divergence(n, U, cm.L_m, zb, div.data());
+  }
+  const double KR0 = 8.0 * kPi / (kLambdaAlpha * kLambdaAlpha * kLambdaAlpha);
+  auto local_C = [&](int64_t i) -> R {
+    const double Heff = std::max(H + div[i] / 3.0, 0.0);
+    const R n1s = nn[i] * (1.0 - x[i]);
+    if (!(val(n1s) > 0.0)) return R(1.0);
+    R Ri = KR0 * Heff / n1s;
+    return (kLambda2g + Ri) / (beta + kLambda2g + Ri);
+  };
+  // Partial mixing (mode 3, fraction f of the full-mixing rate): the net rate is
+  //   f [-alpha n_H x^2 + G (1 - x)] + (1 - f) C_i [-alpha n_H x^2 + beta e_alpha (1 - x)],
+  // the same quadratic with A_i scaled by f + (1 - f) C_i, s = dt f and G offset
+  // per cell by g_i = (1 - f)/f C_i beta e_alpha; lambda stays self-consistent.
+  std::vector<R> gofs(n3, R(0.0));
+  if (mixing == 3) {
+    for (int64_t i = 0; i < n3; ++i) {
+      const R Ci = local_C(i);
+      A[i] = A[i] * (fmix + (1.0 - fmix) * Ci);
+      s[i] = R(dt * fmix);
+      gofs[i] = ((1.0 - fmix) / fmix) * Ci * (beta * ea);
+    }
+  }
+
   if (mixing == 2) {
     // No-mixing limit (Sec. III.A.2): recombination is local, Eq. (rec) with the
     // cell's own n_e and n_1s, and R_alpha of Eq. (R-alpha) with H -> H + div v / 3
@@ -238,18 +268,9 @@ void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double za, double z
     // care: a flow converging faster than the expansion (H + div v/3 < 0) lets no
     // Ly-alpha photon escape, R_alpha = 0.  C per cell uses the substep-start n_1s
     // (as R_alpha^mix does with <n_1s>); no global lambda.
-    std::vector<double> div(n3, 0.0);
-    if (U != nullptr) local_divergence(n, U, cm.L_m, zb, div.data());
-    const double KR0 = 8.0 * kPi / (kLambdaAlpha * kLambdaAlpha * kLambdaAlpha);
     R sx = 0.0, sd = 0.0, sC = 0.0, num = 0.0, den = 0.0;
     for (int64_t i = 0; i < n3; ++i) {
-      const double Heff = std::max(H + div[i] / 3.0, 0.0);
-      const R n1s = nn[i] * (1.0 - x[i]);
-      R Ci = 1.0;
-      if (val(n1s) > 0.0) {
-        R Ri = KR0 * Heff / n1s;
-        Ci = (kLambda2g + Ri) / (beta + kLambda2g + Ri);
-      }
+      const R Ci = local_C(i);
       // dx/dt = -C (alpha n_H x^2 - beta e_alpha (1 - x)), backward Euler
       R xr = be_root<R>(dt * Ci * al[i] * nn[i], dt * Ci, R(beta * ea), x[i], nullptr);
       if (U != nullptr) {
@@ -289,7 +310,7 @@ void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double za, double z
     R F = 0.0, Fp = 0.0;
     for (int64_t i = 0; i < n3; ++i) {
       R dxdG;
-      R xr = be_root<R>(A[i], s[i], G, x[i], &dxdG);
+      R xr = be_root<R>(A[i], s[i], G + gofs[i], x[i], &dxdG);
       R an2 = al[i] * nn[i] * nn[i];
       F += an2 * xr * xr - lam * nn[i] * (1.0 - xr);
       Fp += (2.0 * an2 * xr + lam * nn[i]) * dxdG * omC - nn[i] * (1.0 - xr);
@@ -313,7 +334,7 @@ void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double za, double z
   R G = omC * lam + CBe;
   R sx = 0.0, sd = 0.0;
   for (int64_t i = 0; i < n3; ++i) {
-    R xr = be_root<R>(A[i], s[i], G, x[i], nullptr);
+    R xr = be_root<R>(A[i], s[i], G + gofs[i], x[i], nullptr);
     if (U != nullptr) {
       // Compton drag plus Hubble damping of peculiar velocity, Eq. (momentum):
       // d(a v)/dt = -alpha a v  =>  v' = v exp(-(alpha + H) dt), alpha at x'.
@@ -343,11 +364,11 @@ double sub_z(double z_from, double z_to, int k, int n_sub) {
 }
 
 template <class R>
-void rec_step_t(const Cosmo& cm, int n, int mixing, int n_sub, double z_from, double z_to,
+void rec_step_t(const Cosmo& cm, int n, int mixing, double fmix, int n_sub, double z_from, double z_to,
                 const R* delta, R* x, R* T, double* U, const R* afrac, R* emis, SubStats<R>* st) {
   const int64_t n3 = (int64_t)n * n * n;
   for (int k = 0; k < n_sub; ++k)
-    substep<R>(cm, n, n3, mixing, sub_z(z_from, z_to, k, n_sub), sub_z(z_from, z_to, k + 1, n_sub), delta, x, T,
+    substep<R>(cm, n, n3, mixing, fmix, sub_z(z_from, z_to, k, n_sub), sub_z(z_from, z_to, k + 1, n_sub), delta, x, T,
                U, afrac, emis, st);
 }
 
@@ -381,7 +402,8 @@ R trajectory(const Cosmo& cm, int n, int mixing, int n_sub, int n_steps, const d
       }
     }
     SubStats<R> st;
-    rec_step_t<R>(cm, n, mixing, n_sub, zs[s], zs[s + 1], delta, x.data(), T.data(), nullptr, afp, nullptr, &st);
+    rec_step_t<R>(cm, n, mixing, 1.0, n_sub, zs[s], zs[s + 1], delta, x.data(), T.data(), nullptr, afp, nullptr,
+                  &st);
     Xe[s + 1] = st.Xe;
   }
   if (Xe_hist)
@@ -445,9 +467,10 @@ int orc_saha_xe(const orc_cosmo* cp, double z, int64_t n3, const double* delta, 
 
 int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_from, double z_to,
                  const double* delta, double* x, double* T, double* U, const uint32_t* tally, double* emis,
-                 double* stats) {
-  if (!cp || n <= 0 || n_sub <= 0 || !delta || !x || !T || !(z_from > z_to) || mixing < 0 || mixing > 2)
+                 double* stats, double f_alpha) {
+  if (!cp || n <= 0 || n_sub <= 0 || !delta || !x || !T || !(z_from > z_to) || mixing < 0 || mixing > 3)
     return -1;
+  if (mixing == 3 && !(f_alpha >= 0.0 && f_alpha <= 1.0)) return -1;
   Cosmo c = make_cosmo(cp);
   int64_t n3 = (int64_t)n * n * n;
   std::vector<double> af;
@@ -462,7 +485,7 @@ int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_fro
     }
   }
   SubStats<double> st;
-  rec_step_t<double>(c, n, mixing, n_sub, z_from, z_to, delta, x, T, U, afp, emis, &st);
+  rec_step_t<double>(c, n, mixing, f_alpha, n_sub, z_from, z_to, delta, x, T, U, afp, emis, &st);
   if (stats) {
     stats[0] = st.lambda;
     stats[1] = st.C;

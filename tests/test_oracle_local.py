@@ -166,3 +166,93 @@ def test_one_cell_with_flow_against_ode(cosmo):
     # the flow matters: without it the cell ends elsewhere
     xs = O.rec_step(cosmo, n, z0, z1, d, x0, T0, U=np.zeros_like(U), mixing="local", n_sub=64)[0][0]
     assert abs(xs / xr - 1) > 5 * err[64]
+
+
+# ---- partial mixing: f times the full-mixing rate plus (1 - f) times the local one
+def _box_with_flow(n, z, seed):
+    rng = np.random.default_rng(seed)
+    d = rng.lognormal(0.0, 0.6, n ** 3)
+    x = np.clip(O.saha_xe(cosmo_default(), z, d) * rng.uniform(0.8, 1.2, n ** 3), 1e-6, 0.999)
+    T = O.background(cosmo_default(), z)["Tg"] * rng.uniform(0.98, 1.02, n ** 3)
+    U = rng.normal(0.0, 5.0, (n ** 3, 3))
+    return d, x, T, U
+
+
+def cosmo_default():
+    return O.default_cosmo()
+
+
+def test_partial_mixing_end_points(cosmo):
+    """f = 1 is the full-mixing update and f = 0 the local one, exactly."""
+    n, z0, z1 = 6, 1250.0, 1240.0
+    d, x, T, U = _box_with_flow(n, z0, 3)
+    full = O.rec_step(cosmo, n, z0, z1, d, x, T, U=U, mixing="full")
+    p1 = O.rec_step(cosmo, n, z0, z1, d, x, T, U=U, mixing="partial", f_alpha=1.0)
+    loc = O.rec_step(cosmo, n, z0, z1, d, x, T, U=U, mixing="local")
+    p0 = O.rec_step(cosmo, n, z0, z1, d, x, T, U=U, mixing="partial", f_alpha=0.0)
+    for k in (0, 1, 2, 3):
+        assert np.array_equal(p1[k], full[k]) and np.array_equal(p0[k], loc[k])
+
+
+def test_partial_mixing_uniform_box(cosmo):
+    n = 2
+    d = np.ones(n ** 3)
+    x = O.saha_xe(cosmo, 1200.0, d) * 0.97
+    T = np.full(n ** 3, O.background(cosmo, 1200.0)["Tg"])
+    full = O.rec_step(cosmo, n, 1200.0, 1190.0, d, x, T, U=np.zeros((n ** 3, 3)), mixing="full")[0]
+    part = O.rec_step(cosmo, n, 1200.0, 1190.0, d, x, T, U=np.zeros((n ** 3, 3)), mixing="partial",
+                      f_alpha=0.3)[0]
+    np.testing.assert_allclose(part, full, rtol=2e-11)
+
+
+def test_partial_mixing_two_zones_against_ode(cosmo):
+    """Two equal-volume zones Delta = 1 +- 0.7 at rest (div v = 0): each zone's
+    rate is f times Eq. (dotne-mix) plus (1 - f) times Eq. (rec) with the zone's
+    own n_1s, integrated by a stiff library solver; the backward-Euler history
+    converges to it at first order."""
+    from paper_2312_11448_gb300.inputs import z_schedule
+    f = 0.4
+    dz = np.array([1.7, 0.3])
+    zs = z_schedule(1400.0, 1000.0, 8)
+
+    def rhs(y, s):
+        z = math.expm1(y)
+        bg = O.background(cosmo, z)
+        H, nHb, Tg = bg["H"], bg["nH"], bg["Tg"]
+        x, T = s[:2], s[2:]
+        rg = O.rates(cosmo, z, Tg)
+        al = np.array([O.rates(cosmo, z, t)["alpha"] for t in T])
+        nH = nHb * dz
+        ne2, n1s = (x * nH) ** 2, (1 - x) * nH
+        Rmix = rg["K_R"] / n1s.mean()
+        Cm = (rg["Lambda"] + Rmix) / (rg["beta"] + rg["Lambda"] + Rmix)
+        lam = (al * ne2).mean() / n1s.mean()
+        full = -Cm * (al * ne2 - rg["beta"] * n1s * rg["e_alpha"]) - (1 - Cm) * (al * ne2 - n1s * lam)
+        Rl = rg["K_R"] / n1s
+        Cl = (rg["Lambda"] + Rl) / (rg["beta"] + rg["Lambda"] + Rl)
+        local = -Cl * (al * ne2 - rg["beta"] * n1s * rg["e_alpha"])
+        dxdt = (f * full + (1 - f) * local) / nH
+        dTdt = -2 * H * T + _KC0 * Tg ** 4 * x / (1 + _FHE + x) * (Tg - T)
+        return -np.concatenate([dxdt, dTdt]) / H
+
+    x0 = O.saha_xe(cosmo, zs[0], dz)
+    T0 = np.full(2, O.background(cosmo, zs[0])["Tg"])
+    ys = np.log1p(zs)
+    sol = solve_ivp(rhs, (ys[0], ys[-1]), np.concatenate([x0, T0]), method="Radau", t_eval=ys, rtol=1e-10,
+                    atol=1e-13)
+    assert sol.success
+    xr = sol.y[:2, -1]
+    cells = np.array([dz[0], dz[1]] * 4)  # a 2^3 box, four cells of each zone
+
+    def history(n_sub):
+        x = np.array([x0[0], x0[1]] * 4)
+        T = np.full(8, T0[0])
+        for s in range(len(zs) - 1):
+            x, T, _, _, _ = O.rec_step(cosmo, 2, zs[s], zs[s + 1], cells, x, T, U=np.zeros((8, 3)),
+                                       mixing="partial", f_alpha=f, n_sub=n_sub)
+        return x[:2]
+
+    got = {ns: history(ns) for ns in (4, 16, 64)}
+    err = {ns: np.max(np.abs(got[ns] / xr - 1)) for ns in got}
+    assert 3.3 < err[4] / err[16] < 4.7 and 3.3 < err[16] / err[64] < 4.7
+    assert np.max(np.abs(((4 * got[64] - got[16]) / 3) / xr - 1)) < 0.1 * err[64]
