@@ -68,8 +68,12 @@ typedef enum { REC_PREC_FP64 = 0, REC_PREC_MIXED = 1 } rec_precision;
  *   Sec. III.A.2 — Eq. rec per cell with the cell's own n_e and n_1s and
  *   Eq. R-alpha with H -> H + div v / 3 (div v by periodic central differences
  *   of the substep-start velocities; no escape where H + div v / 3 < 0); tallies
- *   unused.  REC_MIX_LOCAL needs a single-box context and has no adjoint. */
-typedef enum { REC_MIX_TALLY = 0, REC_MIX_FULL = 1, REC_MIX_LOCAL = 2 } rec_mixing;
+ *   unused.  REC_MIX_PARTIAL: the share f_alpha of the full-mixing rate plus
+ *   1 - f_alpha of the local one (the partial mixing of Sec. V with the mixing
+ *   fraction of Sec. III.B, given here as a parameter); lambda stays
+ *   self-consistent.  REC_MIX_LOCAL and REC_MIX_PARTIAL need a single-box
+ *   context and have no adjoint. */
+typedef enum { REC_MIX_TALLY = 0, REC_MIX_FULL = 1, REC_MIX_LOCAL = 2, REC_MIX_PARTIAL = 3 } rec_mixing;
 
 typedef struct {
   /* Cosmology, Sec. II.C defaults: 0.67, 0.0224, 0.12, 0.24. */
@@ -87,6 +91,8 @@ typedef struct {
   const double* emission_quantiles;  /* HOST array [n_quantiles]: inverse CDF of the
                                         emission-frequency profile in Doppler units at
                                         (k+1/2)/n_quantiles; copied at rec_init */
+  double f_alpha;    /* REC_MIX_PARTIAL: share of the full-mixing rate, in [0, 1] (0 = local,
+                        1 = full); read in that mode only */
 } rec_params;
 
 typedef struct {

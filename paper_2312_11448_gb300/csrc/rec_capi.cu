@@ -42,8 +42,13 @@ rec_status check_params(const rec_params* p, std::string* why) {
   }
   if (p->n_sub < 1 || p->n_sub > 4096) { *why = "n_sub must be in [1, 4096]"; return REC_EINVAL; }
   if (p->precision != REC_PREC_FP64 && p->precision != REC_PREC_MIXED) { *why = "unknown precision"; return REC_EINVAL; }
-  if (p->mixing != REC_MIX_TALLY && p->mixing != REC_MIX_FULL && p->mixing != REC_MIX_LOCAL) {
+  if (p->mixing != REC_MIX_TALLY && p->mixing != REC_MIX_FULL && p->mixing != REC_MIX_LOCAL &&
+      p->mixing != REC_MIX_PARTIAL) {
     *why = "unknown mixing mode";
+    return REC_EINVAL;
+  }
+  if (p->mixing == REC_MIX_PARTIAL && !(p->f_alpha >= 0.0 && p->f_alpha <= 1.0)) {
+    *why = "f_alpha must be in [0, 1]";
     return REC_EINVAL;
   }
   if (p->n_quantiles < 2 || !p->emission_quantiles) { *why = "emission profile table missing"; return REC_EINVAL; }
@@ -95,7 +100,8 @@ void layout_buckets(rec_ctx* c) {
 rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_boxes, void* cuda_stream,
                       rec_ctx** out) {
   if (n_boxes > rec::kMaxBoxes) return fail(nullptr, REC_EINVAL, "at most 128 boxes per context");
-  if (params->mixing == REC_MIX_LOCAL) return fail(nullptr, REC_EINVAL, "local mixing needs a single-box context");
+  if (params->mixing == REC_MIX_LOCAL || params->mixing == REC_MIX_PARTIAL)
+    return fail(nullptr, REC_EINVAL, "local and partial mixing need a single-box context");
   std::string why;
   for (int i = 0; i < n_boxes; ++i)
     if (check_box(boxes[i], &why) != REC_OK) return fail(nullptr, REC_EINVAL, "box " + std::to_string(i) + ": " + why);
@@ -277,7 +283,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   if (e == cudaSuccess) e = cudaMalloc(&c->first, sizeof(uint32_t) * (size_t)(b.n_packets / 32 + 2));
   if (e == cudaSuccess && params->precision == REC_PREC_MIXED) e = cudaMalloc(&c->xy, sizeof(float) * 2 * (size_t)c->n3);
   // local mixing: velocity divergence per cell (working precision)
-  if (e == cudaSuccess && params->mixing == REC_MIX_LOCAL)
+  if (e == cudaSuccess && (params->mixing == REC_MIX_LOCAL || params->mixing == REC_MIX_PARTIAL))
     e = cudaMalloc(&c->div, (params->precision == REC_PREC_MIXED ? 4 : 8) * (size_t)c->n3);
   {
     // super-tiles of the march queue, sized for the smallest tile side
@@ -441,8 +447,9 @@ rec_status rec_step_noalloc(const rec_params* params, const rec_box* box, double
   if (s != REC_OK) return fail(nullptr, s, why);
   if (params->precision != REC_PREC_FP64)
     return fail(nullptr, REC_EINVAL, "rec_step_noalloc needs the FP64 form (the mixed form keeps a per-cell cache)");
-  if (params->mixing == REC_MIX_LOCAL)
-    return fail(nullptr, REC_EINVAL, "rec_step_noalloc covers tally and full mixing (local mixing keeps a per-cell field)");
+  if (params->mixing == REC_MIX_LOCAL || params->mixing == REC_MIX_PARTIAL)
+    return fail(nullptr, REC_EINVAL,
+                "rec_step_noalloc covers tally and full mixing (local and partial mixing keep a per-cell field)");
   if (!box) return fail(nullptr, REC_EINVAL, "box is NULL");
   if (box->n < 1 || box->n > 1024) return fail(nullptr, REC_EINVAL, "box side n must be in [1, 1024]");
   if (!box->delta || !box->vel4 || !box->x_e || !box->T || !box->tally || !box->emis)
@@ -459,7 +466,8 @@ rec_status rec_step_adjoint(rec_ctx* c, int32_t step, double z_from, double z_to
   if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
   (void)step;
   if (c->n_boxes > 1) return fail(c, REC_EINVAL, "the adjoint works on single-box contexts");
-  if (c->params.mixing == REC_MIX_LOCAL) return fail(c, REC_EINVAL, "the adjoint covers tally and full mixing");
+  if (c->params.mixing == REC_MIX_LOCAL || c->params.mixing == REC_MIX_PARTIAL)
+    return fail(c, REC_EINVAL, "the adjoint covers tally and full mixing");
   if (c->params.precision != REC_PREC_FP64) return fail(c, REC_EINVAL, "the adjoint needs the FP64 form");
   if (c->params.n_sub != 1) return fail(c, REC_EINVAL, "the adjoint supports n_sub == 1");
   if (!(z_from > z_to) || !(z_to > 0)) return fail(c, REC_EINVAL, "need z_from > z_to > 0");
@@ -475,7 +483,8 @@ rec_status rec_step_adjoint(rec_ctx* c, int32_t step, double z_from, double z_to
 rec_status rec_xe_adjoint(rec_ctx* c, const double* x, double Xe_bar, double* xbar, double* g_delta) {
   if (!c) return fail(nullptr, REC_EINVAL, "ctx is NULL");
   if (c->n_boxes > 1) return fail(c, REC_EINVAL, "the adjoint works on single-box contexts");
-  if (c->params.mixing == REC_MIX_LOCAL) return fail(c, REC_EINVAL, "the adjoint covers tally and full mixing");
+  if (c->params.mixing == REC_MIX_LOCAL || c->params.mixing == REC_MIX_PARTIAL)
+    return fail(c, REC_EINVAL, "the adjoint covers tally and full mixing");
   if (c->params.precision != REC_PREC_FP64) return fail(c, REC_EINVAL, "the adjoint needs the FP64 form");
   if (!x || !xbar || !g_delta) return fail(c, REC_EINVAL, "a required buffer is NULL");
   cudaError_t e = rec::launch_xe_adjoint(c, x, Xe_bar, xbar, g_delta);

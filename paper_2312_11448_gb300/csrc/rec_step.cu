@@ -50,7 +50,8 @@ struct PassArgs {
   DevScalars* sc;
   double* part;
   StepCoef k;
-  int64_t n3_total;
+  const void* div;  // partial mixing: velocity divergence per cell (working precision)
+  double fmix;      // partial mixing: share f of the full-mixing rate (0 < f <= 1)
 };
 
 __device__ __forceinline__ int32_t ld_flag(const int32_t* p) { return *(volatile const int32_t*)p; }
@@ -203,9 +204,26 @@ __device__ void newton_update(DevScalars* sc, double S0, double S1, double S2, d
   else if (sc->passes >= kNewtonMaxPasses) sc->flags |= 1;
 }
 
+// Local Peebles factor from the substep-start n_1s and H + div v / 3 (no
+// escape when the flow converges faster than the expansion).
+__device__ __forceinline__ double local_C(const StepCoef& k, double div, double n1s) {
+  const double Heff = fmax(k.H + div / 3.0, 0.0);
+  if (!(n1s > 0.0)) return 1.0;
+  const double R = (k.KR / k.H) * Heff / n1s;
+  return (k.L2g + R) / (k.beta + k.L2g + R);
+}
+__device__ __forceinline__ float local_C_f32(const StepCoef& k, float div, float n1s) {
+  const float Heff = fmaxf((float)k.H + div / 3.0f, 0.0f);
+  if (!(n1s > 0.0f)) return 1.0f;
+  const float R = fdiv((float)(k.KR / k.H) * Heff, n1s);
+  return fdiv((float)k.L2g + R, (float)(k.beta + k.L2g) + R);
+}
+
 // Per-block partial sums of one Newton evaluation at lambda (result in thread 0):
 // v0 = sum alpha n^2 x'^2, v1 = sum n (1 - x'), v2 = sum (2 alpha n^2 x' + lambda n) dx'/dG.
-template <bool MIXED>
+// PART: partial mixing — per cell, A scaled by f + (1 - f) C_i, s = dt f and G
+// offset by (1 - f)/f C_i beta e_alpha (C_i the local Peebles factor).
+template <bool MIXED, bool PART = false>
 __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam, double G, double tot, double S1s,
                                                   int blk, int nblk, double (&v)[3]) {
   const int64_t stride = (int64_t)nblk * NT;
@@ -217,8 +235,15 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
       double d = delta[i], x = a.x[i];
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF64 c = cell_f64(a.k, d, x, T[i], tal, tot, S1s);
+      double Gc = G;
+      if (PART) {
+        const double Ci = local_C(a.k, ((const double*)a.div)[i], c.n * (1.0 - x));
+        c.A *= a.fmix + (1.0 - a.fmix) * Ci;
+        c.s = a.k.dt * a.fmix;
+        Gc = G + ((1.0 - a.fmix) / a.fmix) * Ci * (a.k.beta * a.k.ea);
+      }
       double dxdG;
-      double xr = root_f64(c.A, c.s, G, x, &dxdG);
+      double xr = root_f64(c.A, c.s, Gc, x, &dxdG);
       double an2 = c.al * c.n * c.n;
       v[0] += an2 * xr * xr;
       v[1] += c.n * (1.0 - xr);
@@ -234,8 +259,16 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
     for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF32 c = cell_f32(f, a.k.mixing, delta[i], a.xy[i], T[i], tal, wscale);
+      float Gc = Gf;
+      if (PART) {
+        const float fm = (float)a.fmix;
+        const float Ci = local_C_f32(a.k, ((const float*)a.div)[i], c.n * c.yf);
+        c.A *= fm + (1.0f - fm) * Ci;
+        c.s = f.dt * fm;
+        Gc = Gf + ((1.0f - fm) / fm) * Ci * (float)(a.k.beta * a.k.ea);
+      }
       float xr, yr, dxdG;
-      root_f32(c.A, c.s, Gf, c.xf, c.yf, &xr, &yr, &dxdG);
+      root_f32(c.A, c.s, Gc, c.xf, c.yf, &xr, &yr, &dxdG);
       float an2 = c.al * c.n * c.n;
       s0.add(an2 * xr * xr);
       s1.add(c.n * yr);
@@ -249,7 +282,7 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
 // Per-block final update at the converged lambda: writes x, T, U, emission
 // weights (zeroes the tallies on the last substep); partial sums (thread 0):
 // v0 = sum delta (1 - x'), v1 = sum delta x', v2 = sum delta.
-template <bool MIXED>
+template <bool MIXED, bool PART = false>
 __device__ __forceinline__ void final_block(const PassArgs& a, double G, double tot, double S1s, int blk, int nblk,
                                             double (&v)[3]) {
   const int64_t stride = (int64_t)nblk * NT;
@@ -264,7 +297,14 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
       double d = delta[i], x = a.x[i];
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF64 c = cell_f64(a.k, d, x, T[i], tal, tot, S1s);
-      double xr = root_f64(c.A, c.s, G, x, nullptr);
+      double Gc = G;
+      if (PART) {
+        const double Ci = local_C(a.k, ((const double*)a.div)[i], c.n * (1.0 - x));
+        c.A *= a.fmix + (1.0 - a.fmix) * Ci;
+        c.s = a.k.dt * a.fmix;
+        Gc = G + ((1.0 - a.fmix) / a.fmix) * Ci * (a.k.beta * a.k.ea);
+      }
+      double xr = root_f64(c.A, c.s, Gc, x, nullptr);
       double damp = exp(-(a.k.kd * xr + a.k.H) * a.k.dt);
       double4_32a u = U[i];
       u.x *= damp; u.y *= damp; u.z *= damp;
@@ -293,9 +333,20 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
       double x = a.x[i];
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
       CellF32 c = cell_f32(f, a.k.mixing, d, a.xy[i], T[i], tal, wscale);
+      float Gcf = Gf;
+      double Gc = G;
+      if (PART) {
+        const float fm = (float)a.fmix;
+        const float Ci = local_C_f32(a.k, ((const float*)a.div)[i], c.n * c.yf);
+        c.A *= fm + (1.0f - fm) * Ci;
+        c.s = f.dt * fm;
+        const float go = ((1.0f - fm) / fm) * Ci * (float)(a.k.beta * a.k.ea);
+        Gcf = Gf + go;
+        Gc = G + (double)go;
+      }
       // binary32 roots x' and y' = 1 - x' (both without cancellation) and the
       // discriminant D = B^2 + 4 A c
-      float sGf = c.s * Gf;
+      float sGf = c.s * Gcf;
       float B = 1.0f + sGf;
       float sq = __fsqrt_rn(B * B + 4.0f * c.A * (c.xf + sGf));
       float xr = __fdiv_rn(2.0f * (c.xf + sGf), B + sq);
@@ -307,7 +358,7 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
       // state, formed in binary64 since near Saha equilibrium the two terms cancel.
       // The discriminant of this equation is D again.
       double y = 1.0 - x;
-      double r0 = fma((double)c.A, x * x, -((double)c.s * G) * y);
+      double r0 = fma((double)c.A, x * x, -((double)c.s * Gc) * y);
       float dx = fdiv(-2.0f * __double2float_rn(r0), 2.0f * c.A * c.xf + B + sq);
       double xn = x + (double)dx;
       float damp = __expf(-(kdf * xr + Hf) * dtf);
@@ -559,6 +610,43 @@ __global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st, const B
   if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st ? st + box : nullptr);
 }
 
+// Newton evaluation and final pass of partial mixing (single-box contexts).
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_newton_part(PassArgs a) {
+  DevScalars* sc = a.sc;
+  if (ld_flag(&sc->conv)) return;
+  const double lam = sc->lam;
+  double v[3];
+  newton_block_sums<MIXED, true>(a, lam, sc->omC * lam + sc->G0, 0.0, sc->S1s, blockIdx.x, gridDim.x, v);
+  if (threadIdx.x == 0) {
+    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+  }
+  if (!last_block_done(&sc->counter)) return;
+  double S[3];
+  combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
+  if (threadIdx.x == 0) {
+    newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
+    sc->counter = 0;
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_final_part(PassArgs a, rec_stats* st) {
+  DevScalars* sc = a.sc;
+  const double lam = sc->lam;
+  double v[3];
+  final_block<MIXED, true>(a, sc->omC * lam + sc->G0, 0.0, sc->S1s, blockIdx.x, gridDim.x, v);
+  if (threadIdx.x == 0) {
+    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+  }
+  if (!last_block_done(&sc->counter)) return;
+  double S[3];
+  combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
+  if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st);
+}
+
 // ---------------------------------------------------------- no-mixing limit
 // Sec. III.A.2: recombination local to each cell, Eq. (rec) with the cell's own
 // n_e, n_1s and Eq. (R-alpha) at H + div v / 3.  k_divergence takes the
@@ -588,21 +676,6 @@ __global__ void __launch_bounds__(NT) k_divergence(const void* vel4, int n, doub
       ((double*)div)[c] = fac * d;
     }
   }
-}
-
-// Local Peebles factor from the substep-start n_1s and H + div v / 3 (no
-// escape when the flow converges faster than the expansion).
-__device__ __forceinline__ double local_C(const StepCoef& k, double div, double n1s) {
-  const double Heff = fmax(k.H + div / 3.0, 0.0);
-  if (!(n1s > 0.0)) return 1.0;
-  const double R = (k.KR / k.H) * Heff / n1s;
-  return (k.L2g + R) / (k.beta + k.L2g + R);
-}
-__device__ __forceinline__ float local_C_f32(const StepCoef& k, float div, float n1s) {
-  const float Heff = fmaxf((float)k.H + div / 3.0f, 0.0f);
-  if (!(n1s > 0.0f)) return 1.0f;
-  const float R = fdiv((float)(k.KR / k.H) * Heff, n1s);
-  return fdiv((float)k.L2g + R, (float)(k.beta + k.L2g) + R);
 }
 
 // One local substep over all cells: x, T (and the (x, 1 - x) cache), Compton
@@ -858,7 +931,8 @@ PassArgs pass_args(rec_ctx* c, const StepCoef& k) {
   a.sc = c->sc;
   a.part = c->part;
   a.k = k;
-  a.n3_total = c->n3;
+  a.div = c->div;
+  a.fmix = c->params.f_alpha;
   return a;
 }
 
@@ -933,9 +1007,12 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
     cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, 0);
     c->coop_grid = (attr && per_sm > 0) ? std::min(c->grid, per_sm * c->sm_count) : -1;
   }
-  if (c->params.mixing == REC_MIX_LOCAL) c->coop_grid = -1;  // one pass per substep, no Newton
-  GroupTimer t(c, kTStep, c->params.mixing == REC_MIX_LOCAL ? 2 * ns
-                                                            : (c->coop_grid > 0 ? ns : ns * (kNewtonMaxPasses + 2)));
+  const bool local_modes = c->params.mixing == REC_MIX_LOCAL || c->params.mixing == REC_MIX_PARTIAL;
+  if (local_modes) c->coop_grid = -1;  // the cooperative substep covers tally and full mixing
+  const bool one_pass = c->params.mixing == REC_MIX_LOCAL ||
+                        (c->params.mixing == REC_MIX_PARTIAL && !(c->params.f_alpha > 0.0));
+  GroupTimer t(c, kTStep, one_pass ? 2 * ns
+                                   : (c->coop_grid > 0 ? ns : ns * (kNewtonMaxPasses + 2 + (local_modes ? 1 : 0))));
   for (int s = 0; s < ns; ++s) {
     double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
     double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
@@ -949,7 +1026,8 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
       if (e != cudaSuccess) return e;
       continue;
     }
-    if (c->params.mixing == REC_MIX_LOCAL) {
+    const bool part = c->params.mixing == REC_MIX_PARTIAL && c->params.f_alpha > 0.0;
+    if (c->params.mixing == REC_MIX_LOCAL || (c->params.mixing == REC_MIX_PARTIAL && !part)) {
       const double fac = (1.0 + zb) * 1.0e3 / (2.0 * c->cosmo.L_m / c->box.n);
       if (mixed) {
         k_divergence<true><<<c->grid, NT, 0, c->stream>>>(c->box.vel4, c->box.n, fac, c->div);
@@ -958,6 +1036,19 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
         k_divergence<false><<<c->grid, NT, 0, c->stream>>>(c->box.vel4, c->box.n, fac, c->div);
         k_local<false><<<c->grid, NT, 0, c->stream>>>(a, c->div, st);
       }
+      continue;
+    }
+    if (part) {  // divergence, then the Newton passes and the final pass with the local shares
+      const double fac = (1.0 + zb) * 1.0e3 / (2.0 * c->cosmo.L_m / c->box.n);
+      if (mixed) k_divergence<true><<<c->grid, NT, 0, c->stream>>>(c->box.vel4, c->box.n, fac, c->div);
+      else k_divergence<false><<<c->grid, NT, 0, c->stream>>>(c->box.vel4, c->box.n, fac, c->div);
+      k_substep_begin<<<1, 32, 0, c->stream>>>(c->sc, k, (double)c->n3);
+      for (int it = 0; it < kNewtonMaxPasses; ++it) {
+        if (mixed) k_newton_part<true><<<c->grid, NT, 0, c->stream>>>(a);
+        else k_newton_part<false><<<c->grid, NT, 0, c->stream>>>(a);
+      }
+      if (mixed) k_final_part<true><<<c->grid, NT, 0, c->stream>>>(a, st);
+      else k_final_part<false><<<c->grid, NT, 0, c->stream>>>(a, st);
       continue;
     }
     k_substep_begin<<<1, 32, 0, c->stream>>>(c->sc, k, (double)c->n3);
@@ -1113,7 +1204,8 @@ rec_status launch_rec_step_noalloc(const rec_params& p, const rec_box& b, double
   a.emis = b.emis;
   a.sc = sc;
   a.part = part;
-  a.n3_total = n3;
+  a.div = nullptr;
+  a.fmix = 1.0;
   e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), stream);
   if (e != cudaSuccess) { *why = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e); return REC_ECUDA; }
   // sums and emission weights of the incoming state at z_from (as rec_refresh)

@@ -22,7 +22,7 @@ from . import build as _build
 
 REC_OK, REC_EINVAL, REC_ENOMEM, REC_ECUDA, REC_ETIMEOUT, REC_ESTATE = range(6)
 PREC = {"fp64": 0, "mixed": 1}
-MIXING = {"tally": 0, "full": 1, "local": 2}
+MIXING = {"tally": 0, "full": 1, "local": 2, "partial": 3}
 _lib = None
 
 
@@ -31,7 +31,7 @@ class Params(C.Structure):
                 ("T_cmb0", C.c_double), ("N_eff", C.c_double), ("L_box_kpc", C.c_double), ("fudge", C.c_double),
                 ("heating", C.c_double), ("seed", C.c_uint64), ("n_sub", C.c_int32), ("precision", C.c_int32),
                 ("mixing", C.c_int32), ("n_quantiles", C.c_int32),
-                ("emission_quantiles", C.POINTER(C.c_double))]
+                ("emission_quantiles", C.POINTER(C.c_double)), ("f_alpha", C.c_double)]
 
 
 class BoxDesc(C.Structure):
@@ -98,7 +98,7 @@ def make_params(precision="mixed", mixing="tally", seed=1, n_sub=1, quantiles=No
         quantiles = doppler_quantiles()
     q = np.ascontiguousarray(quantiles, dtype=np.float64)
     base = dict(h=0.67, omega_b_h2=0.0224, omega_c_h2=0.12, Y_p=0.24, T_cmb0=2.7255, N_eff=3.046, L_box_kpc=24.0,
-                fudge=1.14, heating=0.0)
+                fudge=1.14, heating=0.0, f_alpha=1.0)
     base.update(cosmo)
     p = Params(**base, seed=seed, n_sub=n_sub, precision=PREC[precision], mixing=MIXING[mixing],
                n_quantiles=q.size, emission_quantiles=q.ctypes.data_as(C.POINTER(C.c_double)))

@@ -88,3 +88,50 @@ def test_local_mode_rejections():
     with pytest.raises(rec.RecError, match="tally and full"):
         box.xe_adjoint(x, 1.0, x.clone(), x.clone())
     box.close()
+
+
+# ---- partial mixing: f_alpha of the full-mixing rate plus the rest local
+def _partial_box(n, precision, f, sigma_v, n_sub=1):
+    from gpu_helpers import make_fields
+    from paper_2312_11448_gb300 import rec
+    d, U = make_fields(n, 0.8, sigma_v, seed=1)
+    return rec.Box(n, d, U, 1000, precision=precision, mixing="partial", seed=7, n_sub=n_sub, f_alpha=f)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("f", [0.0, 0.3, 0.8, 1.0])
+@pytest.mark.parametrize("n,sigma_v,n_sub", [(13, 15.0, 1), (32, 4.0, 2)])
+def test_partial_step_matches_oracle(cosmo, precision, f, n, sigma_v, n_sub):
+    box = _partial_box(n, precision, f, sigma_v, n_sub)
+    rng = np.random.default_rng(n + int(10 * f))
+    d, U, _ = oracle_fields(box)
+    z_from, z_to = 1200.0, 1190.0
+    x0, T0 = _state(cosmo, d, z_from, rng)
+    set_state(box, x0, T0, tally=rng.integers(0, 5, n ** 3).astype(np.uint32))
+    T_in = box.host("T").astype(np.float64)
+    box.refresh(z_from)
+    box.step(0, z_from, z_to)
+    st = box.stats()
+    x1, T1, U1, e1, so = O.rec_step(cosmo, n, z_from, z_to, d, x0, T_in, U=U, mixing="partial", f_alpha=f,
+                                    n_sub=n_sub)
+    tol = TOL[precision]
+    np.testing.assert_allclose(box.host("x"), x1, rtol=tol, atol=0)
+    np.testing.assert_allclose(box.host("T").astype(np.float64), T1, rtol=tol, atol=0)
+    np.testing.assert_allclose(box.host("vel4")[:, :3].astype(np.float64), U1, rtol=tol, atol=1e-12)
+    assert st["X_e"] == pytest.approx(so["Xe"], rel=tol)
+    assert st["flags"] & 1 == 0
+    box.close()
+
+
+def test_partial_mode_rejections():
+    from gpu_helpers import make_fields
+    from paper_2312_11448_gb300 import rec
+    d, U = make_fields(8, 0.5, 1.0, seed=2)
+    with pytest.raises(rec.RecError, match="single-box"):
+        rec.Batch([(8, d, U, 10), (8, d, U, 10)], precision="fp64", mixing="partial", f_alpha=0.5)
+    with pytest.raises(rec.RecError, match="f_alpha"):
+        rec.Box(8, d, U, 10, precision="fp64", mixing="partial", f_alpha=1.5)
+    box = _partial_box(8, "fp64", 0.5, 1.0)
+    with pytest.raises(rec.RecError, match="tally and full"):
+        box.step_noalloc(1400.0, 1390.0)
+    box.close()
