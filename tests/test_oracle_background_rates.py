@@ -113,7 +113,7 @@ def test_saha_initial_state(cosmo):
         Tg = O.background(cosmo, z)["Tg"]
         for xi, d in zip(x, delta):
             assert xi == pytest.approx(_saha_textbook(Tg, nH * d), rel=1e-6)
-    # around 0.99 at z = 1600 for mean density (rough hand estimate of the blueprint)
+    # hydrogen is still about 99 % ionised at z = 1600 for mean density (textbook Saha curve)
     assert 0.98 < O.saha_xe(cosmo, 1600.0, np.ones(1))[0] < 0.995
 
 
