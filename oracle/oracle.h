@@ -78,8 +78,9 @@ int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_fro
  * times 1 + z.  Pinned by the closed form for sinusoidal fields. */
 int orc_divergence(const orc_cosmo* cp, int n, double z, const double* U, double* div);
 
-/* Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11).  Pinned by
- * statistical tests (uniformity, bit balance, avalanche). */
+/* Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11).  Pinned word for
+ * word against the cuRAND library's host Philox4_32_10 generator (random keys
+ * and counters) and by statistical tests (uniformity, bit balance, avalanche). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* Threads of the transport: 1 in the plain build; the OpenMP build (host-cores
  * timing baseline) sets its thread count to n (> 0) and returns it. */
