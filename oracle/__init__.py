@@ -32,6 +32,30 @@ class Packet(C.Structure):
                 ("f", C.c_double * 3), ("dir", C.c_double * 3), ("xi", C.c_double), ("u0", C.c_double)]
 
 
+class McParams(C.Structure):
+    """Mirror of orc_mc_params (oracle.h)."""
+    _fields_ = [("z", C.c_double), ("eps", C.c_double), ("x_lost", C.c_double), ("zeta", C.c_double),
+                ("lambda2g", C.c_double), ("A_alpha", C.c_double), ("seed", C.c_uint64), ("step", C.c_uint32),
+                ("box", C.c_uint32), ("max_steps", C.c_uint64)]
+
+
+class McPhoton(C.Structure):
+    """Mirror of orc_mc_photon (oracle.h)."""
+    _fields_ = [("home", C.c_uint32), ("j", C.c_uint32), ("fate", C.c_int32), ("n_scat", C.c_uint64),
+                ("n_steps", C.c_uint64), ("D_kpc", C.c_double), ("x_end", C.c_double)]
+
+
+MC_FATES = ("lost", "two_photon", "ionised", "capped")
+# 2p -> 1s decay rate (NIST, 6.2649e8 /s; the paper quotes about 6.3e8 /s).
+A_2P1S = 6.2649e8
+
+
+def mc_params(z, eps=0.1, x_lost=1.0e4, zeta=1.0, lambda2g=-1.0, A_alpha=A_2P1S, seed=1, step=0, box=0,
+              max_steps=10 ** 9) -> McParams:
+    return McParams(z=z, eps=eps, x_lost=x_lost, zeta=zeta, lambda2g=lambda2g, A_alpha=A_alpha, seed=seed,
+                    step=step, box=box, max_steps=max_steps)
+
+
 def default_cosmo(**kw) -> Cosmo:
     """Sec. II.C defaults (h, Omega_b h^2, Omega_c h^2, Y_p) and the 24 kpc box."""
     p = dict(h=0.67, omega_b_h2=0.0224, omega_c_h2=0.12, Y_p=0.24, T_cmb0=2.7255, N_eff=3.046,
@@ -78,6 +102,12 @@ def _bind(L):
                                    i, d, P(d)]
     L.orc_threads.argtypes = [i]
     L.orc_divergence.argtypes = [P(Cosmo), i, d, P(d), P(d)]
+    L.orc_faddeeva.argtypes = [d, d, P(d)]
+    L.orc_voigt_table.argtypes = [d, i64, P(d), P(d)]
+    L.orc_mc_setup.argtypes = [P(Cosmo), P(McParams), i, P(d)]
+    L.orc_mc_redistribution.argtypes = [d, d, P(d), u64, i64, P(d), P(d), P(d)]
+    L.orc_lya_mc.argtypes = [P(Cosmo), P(McParams), i, P(d), P(d), P(d), P(u32), u64, u64, P(McPhoton),
+                             P(u64)]
     return L
 
 
@@ -242,3 +272,64 @@ def traj_tangent(cp, n, zs, delta, x0, T0, d_delta=None, d_T0=None, d_a=None, ta
                                 objective, z_star, _p(J, C.c_double))
     _check(rc, "traj_tangent")
     return J[0], J[1]
+
+
+# ---- resonant-scattering Ly-alpha Monte Carlo (Appendix A) ----------------------
+def faddeeva(y: float, a: float) -> complex:
+    out = np.zeros(2)
+    _check(lib().orc_faddeeva(float(y), float(a), _p(out, C.c_double)), "faddeeva")
+    return complex(out[0], out[1])
+
+
+def voigt_table(a: float, y) -> np.ndarray:
+    yy = _f64(y).ravel()
+    H = np.empty_like(yy)
+    _check(lib().orc_voigt_table(float(a), yy.size, _p(yy, C.c_double), _p(H, C.c_double)), "voigt_table")
+    return H
+
+
+def mc_setup(cp: Cosmo, mp: McParams, n: int = 1) -> dict:
+    out = np.zeros(12)
+    _check(lib().orc_mc_setup(C.byref(cp), C.byref(mp), n, _p(out, C.c_double)), "mc_setup")
+    keys = ("a", "vth", "sig0", "dxdl", "p_ion", "p_2g", "beta", "Lambda", "H", "nH", "Tg", "cells_per_m")
+    return dict(zip(keys, out))
+
+
+def mc_redistribution(a: float, y: float, seed: int, m: int, kin=(0.0, 0.0, 1.0), want_k=False):
+    """(p_par, y_out - y[, k_out]) of m independent isotropic scatterings at
+    offset y of a photon travelling along kin."""
+    pp = np.empty(m)
+    dy = np.empty(m)
+    ko = np.empty((m, 3)) if want_k else None
+    k = _f64(kin)
+    _check(lib().orc_mc_redistribution(float(a), float(y), _p(k, C.c_double), seed, m, _p(pp, C.c_double),
+                                       _p(dy, C.c_double), _p(ko, C.c_double)), "mc_redistribution")
+    return (pp, dy, ko) if want_k else (pp, dy)
+
+
+def lya_mc(cp: Cosmo, mp: McParams, n: int, delta, xe, P, U=None, k0=0, k1=None, threads=0):
+    """Photons k0..k1-1 of the allocation prefix P through the Monte Carlo.
+    Returns (records, counters): records is a numpy structured array with
+    home, j, fate, n_scat, n_steps, D_kpc, x_end; counters = photons per fate
+    (lost, two_photon, ionised, capped) and the sampler-cap count.  threads > 0
+    uses the OpenMP build (same per-photon results)."""
+    d = _f64(delta).ravel()
+    x = _f64(xe).ravel()
+    if x.size == 1:
+        x = np.full_like(d, x[0])
+    Pa = np.ascontiguousarray(P, dtype=np.uint32).ravel()
+    U1 = None if U is None else _f64(U).reshape(-1, 3)
+    if k1 is None:
+        k1 = int(Pa[-1])
+    recs = (McPhoton * max(k1 - k0, 1))()
+    cnt = np.zeros(5, dtype=np.uint64)
+    L = lib(openmp=threads > 0)
+    if threads > 0:
+        L.orc_threads(int(threads))
+    rc = L.orc_lya_mc(C.byref(cp), C.byref(mp), n, _p(d, C.c_double), _p(x, C.c_double), _p(U1, C.c_double),
+                      _p(Pa, C.c_uint32), k0, k1, recs, _p(cnt, C.c_uint64))
+    _check(rc, "lya_mc")
+    dt = np.dtype([("home", np.uint32), ("j", np.uint32), ("fate", np.int32), ("n_scat", np.uint64),
+                   ("n_steps", np.uint64), ("D_kpc", np.float64), ("x_end", np.float64)], align=True)
+    arr = np.frombuffer(recs, dtype=dt, count=k1 - k0).copy()
+    return arr, cnt

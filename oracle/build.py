@@ -9,7 +9,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["oracle_physics.cpp", "oracle_transport.cpp"]
+SOURCES = ["oracle_physics.cpp", "oracle_transport.cpp", "oracle_scatter.cpp"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -139,6 +139,65 @@ int orc_traj_tangent(const orc_cosmo* cp, int n, int mixing, int n_sub, int n_st
                      const double* d_delta, const double* d_T0, const double* d_a, int objective,
                      double z_star, double* J);
 
+/* ---- Resonant-scattering Ly-alpha Monte Carlo (Appendix A) ----------------- */
+
+/* Faddeeva function w(y + i a), a > 0: w[0] = H(a, y) (Voigt function),
+ * w[1] = Im w.  Weideman's 48-term rational expansion for |z| < 10, the
+ * asymptotic series beyond.  Pinned against the library Faddeeva function
+ * and closed forms (H(a,0) = exp(a^2) erfc(a), H(0,y) = exp(-y^2),
+ * normalisation sqrt(pi)). */
+int orc_faddeeva(double y, double a, double* w);
+/* The Voigt table the Monte Carlo uses (cubic Hermite on 1/128 nodes for
+ * |y| < 10, asymptotic series beyond), at m points y. */
+int orc_voigt_table(double a, int64_t m, const double* y, double* H);
+
+typedef struct {
+  double z;         /* redshift of the snapshot */
+  double eps;       /* step (3): path of eps mean free paths per step */
+  double x_lost;    /* photons whose gas-frame offset falls below -x_lost are lost by redshifting */
+  double zeta;      /* expansion rate zeta H (1 normally; Fig. Cfact varies it) */
+  double lambda2g;  /* two-photon rate, 1/s; negative: the paper's 8.22 */
+  double A_alpha;   /* 2p -> 1s decay rate Gamma_alpha, 1/s */
+  uint64_t seed;
+  uint32_t step, box;
+  uint64_t max_steps;  /* per photon; photons reaching it end as CAPPED */
+} orc_mc_params;
+
+enum { ORC_MC_LOST = 0, ORC_MC_TWO_PHOTON = 1, ORC_MC_IONISED = 2, ORC_MC_CAPPED = 3 };
+
+typedef struct {
+  uint32_t home, j;   /* emitting cell, photon index in the cell */
+  int32_t fate;       /* ORC_MC_* */
+  uint64_t n_scat, n_steps;
+  double D_kpc;       /* comoving distance from injection to the end point */
+  double x_end;       /* final frequency offset, Doppler units, frame without peculiar velocity */
+} orc_mc_photon;
+
+/* Derived scalars: out[0]=a, [1]=v_th/c, [2]=sig0 (m^2, <sigma> = sig0 H(a,y)),
+ * [3]=dx per physical metre, [4]=p_ion, [5]=p_2gamma per scattering,
+ * [6]=beta_e, [7]=Lambda, [8]=zeta H, [9]=nbar_H, [10]=T_gamma,
+ * [11]=comoving cells per physical metre. */
+int orc_mc_setup(const orc_cosmo* cp, const orc_mc_params* mp, int n, double* out);
+
+/* m independent scatterings of a photon at gas-frame offset y travelling
+ * along kin (Eq. inout, isotropic): ppar[i] = scattering atom's parallel
+ * velocity, dy[i] = y_out - y, kout[3i..3i+2] = outgoing direction.  Any
+ * output may be NULL. */
+int orc_mc_redistribution(double a, double y, const double* kin, uint64_t seed, int64_t m, double* ppar,
+                          double* dy, double* kout);
+
+/* Photons k0..k1-1 of the allocation prefix P (n^3 + 1 entries, as from
+ * orc_allocate_*) through steps (1)-(8) in an n^3 periodic box at redshift z
+ * with overdensity delta, ionisation fraction xe and peculiar velocity U
+ * ([n^3][3] km/s, may be NULL); T = T_gamma(z) throughout.  out[k - k0] per
+ * photon; counters[0..3] = photons per fate, counters[4] = atom-velocity
+ * draws that hit the rejection cap.  Pinned by the redistribution moments,
+ * the first-flight distance law, Galilean invariance and the Sobolev
+ * escape / C factor (Fig. Cfact). */
+int orc_lya_mc(const orc_cosmo* cp, const orc_mc_params* mp, int n, const double* delta, const double* xe,
+               const double* U, const uint32_t* P, uint64_t k0, uint64_t k1, orc_mc_photon* out,
+               uint64_t* counters);
+
 #ifdef __cplusplus
 }
 #endif
