@@ -269,6 +269,79 @@ rec_status rec_transport_params(const rec_params* params, int32_t n, double z, d
 rec_status rec_timing(rec_ctx* ctx, int32_t enable);
 rec_status rec_kernel_times(rec_ctx* ctx, double* ms_out, int64_t* launches_out);
 
+/* ---- Resonant-scattering Ly-alpha Monte Carlo (Appendix A) ------------------
+ * Single photons followed through their scatterings on neutral hydrogen in
+ * the box's density, ionisation and velocity fields at one redshift: steps
+ * (1)-(8) of Appendix A.  A photon is injected at line centre in the gas frame
+ * of its cell, at a uniform point of the cell, along an isotropic direction.
+ * Each step evaluates the thermally averaged cross-section of Eq. MC,
+ * <sigma> = (3 lambda_alpha^2 / 8 pi) 4 a sqrt(pi) H(a, y), in the cell the
+ * photon is in (H the Voigt function, y the gas-frame offset in Doppler units
+ * v_th = sqrt(2 k T_gamma / m_H), a = Gamma_alpha / (2 omega_alpha v_th)).
+ * It advances eps mean free paths, redshifts by dx = -zeta H dl / v_th, and
+ * scatters with probability 1 - exp(-eps).  At a scattering the n = 2 atom
+ * (2s and 2p in statistical equilibrium, Sec. III.A.1) is photo-ionised,
+ * decays by two photons or re-emits, with weights beta_e : Lambda : 3 A_alpha.
+ * A re-emitted photon takes the frequency of Eq. inout (isotropic
+ * scattering, the atom's velocity drawn from the third factor of Eq. MC).
+ * A photon whose gas-frame offset falls below -x_lost is lost by redshifting.
+ * T = T_gamma(z) throughout.  All arithmetic is binary64 in both precision
+ * forms; the box's fields are read in their stored types. */
+typedef struct {
+  double z;          /* redshift of the snapshot (> 0) */
+  double eps;        /* step (3): path of eps mean free paths per step, (0, 1] */
+  double x_lost;     /* loss threshold on the red wing, Doppler units (> 0) */
+  double zeta;       /* expansion rate zeta H (> 0; 1 for the true rate, Fig. Cfact varies it) */
+  double lambda2g;   /* two-photon rate, 1/s (>= 0); negative: 8.22 (Sec. III.A.1) */
+  double A_alpha;    /* 2p -> 1s decay rate Gamma_alpha, 1/s (> 0; about 6.3e8) */
+  uint64_t n_photons;  /* photons, 1 .. 2^32 - 1 */
+  uint64_t max_steps;  /* per photon (>= 1); a photon reaching it ends as LYA_MC_CAPPED */
+  int32_t step;        /* keys the random streams (with rec_params.seed) */
+  int32_t pending;     /* lanes of a warp waiting to scatter before the warp runs the
+                          redistribution for them, 1..32; 0: 12.  Speed only: results
+                          do not depend on it. */
+} lya_mc_params;
+
+enum { LYA_MC_LOST = 0, LYA_MC_TWO_PHOTON = 1, LYA_MC_IONISED = 2, LYA_MC_CAPPED = 3 };
+
+typedef struct {
+  uint32_t home, j;   /* emitting cell and index of the photon in that cell */
+  int32_t fate;       /* LYA_MC_* */
+  uint32_t reserved;
+  uint64_t n_scat;    /* scatterings, the last one included */
+  uint64_t n_steps;
+  double D_kpc;       /* comoving distance from injection to the end point */
+  double x_end;       /* final frequency offset, Doppler units, frame without peculiar velocity */
+} lya_mc_photon;
+
+typedef struct {
+  uint64_t count[4];     /* photons per fate (LYA_MC_*) */
+  uint64_t sampler_caps; /* atom-velocity draws that hit their rejection cap (0 in practice) */
+  uint64_t steps, scatterings;
+  uint64_t nonfinite;    /* photons ended because their state stopped being finite (counted as CAPPED) */
+} lya_mc_stats;
+
+/* Run mp->n_photons photons through the Monte Carlo in the fields of a
+ * single-box context (delta, x_e, vel4 as they are when the stream reaches
+ * the call).  Photon k belongs to the cell c with dev_prefix[c] <= k <
+ * dev_prefix[c + 1] (device u32 [n^3 + 1], non-decreasing, dev_prefix[0] = 0,
+ * dev_prefix[n^3] = n_photons), or, with dev_prefix NULL, to the even
+ * allocation prefix_c = floor(c n_photons / n^3).  Photon (c, j) draws from the
+ * Philox stream with key (seed low word, seed high word XOR step) and counter
+ * (c, j, block, 2^31).  dev_photons (device, n_photons records, may be NULL)
+ * receives one record per photon in photon order; dev_stats (device, may be
+ * NULL) the totals.  Needs x_e < 1 and delta > 0 in the cells photons visit.
+ * Errors: REC_EINVAL (argument out of range, batched context), REC_ENOMEM,
+ * REC_ECUDA. */
+rec_status lya_scatter_mc(rec_ctx* ctx, const lya_mc_params* mp, const uint32_t* dev_prefix,
+                          lya_mc_photon* dev_photons, lya_mc_stats* dev_stats);
+
+/* The Voigt function H(a, y) as lya_scatter_mc evaluates it (cubic Hermite
+ * interpolation of nodes spaced 1/128 for |y| < 10, the asymptotic series of
+ * the Faddeeva function beyond), at m host points y; host computation.
+ * Errors: REC_EINVAL. */
+rec_status lya_voigt(double a, int64_t m, const double* y, double* H);
+
 /* Release the context and its scratch (NULL-safe).  Synchronises the stream. */
 void rec_free(rec_ctx* ctx);
 

@@ -16,7 +16,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librec.so")
-SOURCES = ["rec_capi.cu", "rec_cosmo.cu", "rec_step.cu", "rec_transport.cu", "rec_adjoint.cu"]
+SOURCES = ["rec_capi.cu", "rec_cosmo.cu", "rec_step.cu", "rec_transport.cu", "rec_adjoint.cu", "rec_scatter.cu"]
+# The scattering Monte Carlo rounds every operation as written (no contraction
+# into fused multiply-adds), like the oracle it is compared with.
+FILE_FLAGS = {"rec_scatter.cu": ["--fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--prec-div=true", "--prec-sqrt=true", "-I", INCLUDE, "-I", CSRC]
@@ -50,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + FILE_FLAGS.get(src, []) + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

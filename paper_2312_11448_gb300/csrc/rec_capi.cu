@@ -589,11 +589,43 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->bfill);
   cudaFree(c->cpre);
   cudaFree(c->div);
+  cudaFree(c->mc_scratch);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   cudaFree(c->bx);
   cudaFree(c->bstep);
   cudaFree(c->gsc);
   delete c;
+}
+
+rec_status lya_scatter_mc(rec_ctx* c, const lya_mc_params* mp, const uint32_t* dev_prefix,
+                          lya_mc_photon* dev_photons, lya_mc_stats* dev_stats) {
+  if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");
+  if (c->n_boxes != 1) return fail(c, REC_EINVAL, "the scattering Monte Carlo needs a single-box context");
+  if (!mp) return fail(c, REC_EINVAL, "lya_mc_params is NULL");
+  if (!(mp->z > 0.0) || !is_finite(mp->z)) return fail(c, REC_EINVAL, "z must be positive and finite");
+  if (!(mp->eps > 0.0 && mp->eps <= 1.0)) return fail(c, REC_EINVAL, "eps must be in (0, 1]");
+  if (!(mp->x_lost > 0.0) || !is_finite(mp->x_lost)) return fail(c, REC_EINVAL, "x_lost must be positive");
+  if (!(mp->zeta > 0.0) || !is_finite(mp->zeta)) return fail(c, REC_EINVAL, "zeta must be positive");
+  if (!is_finite(mp->lambda2g)) return fail(c, REC_EINVAL, "lambda2g must be finite");
+  if (!(mp->A_alpha > 0.0) || !is_finite(mp->A_alpha)) return fail(c, REC_EINVAL, "A_alpha must be positive");
+  if (mp->n_photons < 1 || mp->n_photons >= (1ull << 32))
+    return fail(c, REC_EINVAL, "n_photons must be in [1, 2^32)");
+  if (mp->max_steps < 1) return fail(c, REC_EINVAL, "max_steps must be at least 1");
+  if (mp->pending < 0 || mp->pending > 32) return fail(c, REC_EINVAL, "pending must be in [0, 32]");
+  rec::McSetup S;
+  if (!rec::scatter_setup(c->cosmo, c->params, c->box.n, mp, &S))
+    return fail(c, REC_EINVAL, "Monte-Carlo scalars are not finite at this redshift");
+  cudaError_t e = rec::run_scatter_mc(c, S, mp, dev_prefix, dev_photons, dev_stats);
+  if (e == cudaErrorMemoryAllocation) return fail(c, REC_ENOMEM, "Monte-Carlo scratch");
+  if (e != cudaSuccess) return cuda_fail(c, e, "lya_scatter_mc");
+  return REC_OK;
+}
+
+rec_status lya_voigt(double a, int64_t m, const double* y, double* H) {
+  if (!(a > 0.0) || !is_finite(a) || m < 0 || (m > 0 && (!y || !H)))
+    return fail(nullptr, REC_EINVAL, "lya_voigt: a must be positive, y and H non-NULL");
+  rec::scatter_voigt_host(a, m, y, H);
+  return REC_OK;
 }
 
 const char* rec_last_error(const rec_ctx* c) {

@@ -170,6 +170,10 @@ struct rec_ctx {
   int tot_pblk = 0;              // streaming-pass blocks of all boxes
   int tot_buckets = 0;           // march-queue buckets of all boxes
   uint64_t tot_pk = 0;           // batch packet space (each box padded to 32)
+  // resonant-scattering Monte Carlo (lya_scatter_mc): Voigt nodes and counters
+  void* mc_scratch = nullptr;
+  size_t mc_bytes = 0;
+  double mc_a = -1.0;            // Voigt parameter of the nodes held in mc_scratch
 };
 
 namespace rec {
@@ -232,6 +236,24 @@ void transport_limits(bool mixed, bool batch, int* emit_max, int* march_max);
 cudaError_t launch_state_init_batch(rec_ctx* c, double z);
 cudaError_t launch_refresh_batch(rec_ctx* c, double z);
 cudaError_t launch_rec_step_batch(rec_ctx* c, double z_from, double z_to, rec_stats* st);
+
+// rec_scatter.cu: resonant-scattering Monte Carlo (Appendix A)
+struct McSetup {
+  double a;         // Voigt parameter Gamma / (2 omega_alpha v_th)
+  double vth;       // sqrt(2 k T_gamma / m_H) / c
+  double sig0;      // <sigma> = sig0 H(a, y), m^2
+  double dxdl;      // frequency drift per physical metre, zeta H / (c v_th)
+  double cpm;       // comoving cells per physical metre
+  double ufac;      // Doppler units per km/s of peculiar velocity
+  double p_ion, p_2g;  // fates per scattering
+  double beta, Lam, Heff, nH, Tg;
+  double expm_eps;  // exp(-eps)
+  double kpc_cell;  // comoving kpc per cell
+};
+bool scatter_setup(const Cosmo& c, const rec_params& p, int n, const lya_mc_params* mp, McSetup* S);
+void scatter_voigt_host(double a, int64_t m, const double* y, double* H);
+cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp, const uint32_t* prefix,
+                           lya_mc_photon* out, lya_mc_stats* st);
 
 // rec_adjoint.cu
 cudaError_t launch_rec_step_adjoint(rec_ctx* c, double z_from, double z_to, const double* x_in, const double* T_in,

@@ -54,6 +54,25 @@ class Tuning(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class McParams(C.Structure):
+    """lya_mc_params: one resonant-scattering Monte-Carlo run (Appendix A)."""
+    _fields_ = [("z", C.c_double), ("eps", C.c_double), ("x_lost", C.c_double), ("zeta", C.c_double),
+                ("lambda2g", C.c_double), ("A_alpha", C.c_double), ("n_photons", C.c_uint64),
+                ("max_steps", C.c_uint64), ("step", C.c_int32), ("pending", C.c_int32)]
+
+
+class McStats(C.Structure):
+    _fields_ = [("count", C.c_uint64 * 4), ("sampler_caps", C.c_uint64), ("steps", C.c_uint64),
+                ("scatterings", C.c_uint64), ("nonfinite", C.c_uint64)]
+
+
+# lya_mc_photon as a numpy record
+MC_PHOTON = np.dtype([("home", np.uint32), ("j", np.uint32), ("fate", np.int32), ("reserved", np.uint32),
+                      ("n_scat", np.uint64), ("n_steps", np.uint64), ("D_kpc", np.float64), ("x_end", np.float64)])
+MC_FATES = ("lost", "two_photon", "ionised", "capped")
+A_2P1S = 6.2649e8  # 2p -> 1s decay rate, 1/s
+
+
 class RecError(RuntimeError):
     pass
 
@@ -80,12 +99,15 @@ def lib():
         L.rec_objective.argtypes = [P(Params), P(d), P(d), i32, i32, d, P(d), P(d)]
         L.rec_timing.argtypes = [vp, i32]
         L.rec_kernel_times.argtypes = [vp, P(d), P(C.c_int64)]
+        L.lya_scatter_mc.argtypes = [vp, P(McParams), vp, vp, vp]
+        L.lya_voigt.argtypes = [d, C.c_int64, P(d), P(d)]
         L.rec_free.argtypes = [vp]
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
         L.rec_last_error.restype = C.c_char_p
         for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc", "rec_graph_step", "rec_get_tuning", "rec_set_tuning",
-                  "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times"):
+                  "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times",
+                  "lya_scatter_mc", "lya_voigt"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -127,6 +149,23 @@ def objective(zs, Xe, objective=1, z_star=1100.0, **kw):
     if rc != REC_OK:
         raise RecError(lib().rec_last_error(None).decode())
     return J.value, dJ
+
+
+def voigt(a: float, y) -> np.ndarray:
+    """H(a, y) as the scattering Monte Carlo evaluates it (host computation)."""
+    yy = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    H = np.empty_like(yy)
+    dp = lambda v: v.ctypes.data_as(C.POINTER(C.c_double))
+    rc = lib().lya_voigt(float(a), yy.size, dp(yy), dp(H))
+    if rc != REC_OK:
+        raise RecError(lib().rec_last_error(None).decode())
+    return H
+
+
+def mc_params(z, n_photons, eps=0.1, x_lost=1.0e4, zeta=1.0, lambda2g=-1.0, A_alpha=A_2P1S, max_steps=10 ** 9,
+              step=0, pending=0) -> McParams:
+    return McParams(z=z, eps=eps, x_lost=x_lost, zeta=zeta, lambda2g=lambda2g, A_alpha=A_alpha,
+                    n_photons=int(n_photons), max_steps=int(max_steps), step=int(step), pending=int(pending))
 
 
 class Batch:
@@ -353,6 +392,32 @@ class Box:
         self._check(lib().rec_xe_adjoint(self.ctx, C.c_void_p(x.data_ptr()), float(Xe_bar),
                                          C.c_void_p(xbar.data_ptr()), C.c_void_p(g_delta.data_ptr())),
                     "rec_xe_adjoint")
+
+    def scatter_mc(self, z, n_photons, prefix=None, records=True, **kw):
+        """Resonant-scattering Monte Carlo (lya_scatter_mc) in this box's fields.
+        prefix: photons per cell as an exclusive prefix (n^3 + 1 integers), or
+        None for the even allocation.  kw: the other lya_mc_params fields.
+        Returns (records or None, stats dict); synchronises."""
+        torch = self.torch
+        mp = mc_params(z, n_photons, **kw)
+        dev = self.x.device
+        with torch.cuda.stream(self.stream):
+            pre = None
+            if prefix is not None:
+                pa = np.ascontiguousarray(prefix, dtype=np.int64).ravel()
+                if pa.size != self.n3 + 1:
+                    raise RecError("prefix must have n^3 + 1 entries")
+                pre = torch.as_tensor(pa.astype(np.uint32).view(np.int32)).to(dev)
+            rec = torch.empty(int(n_photons) * MC_PHOTON.itemsize if records else 0, dtype=torch.uint8, device=dev)
+            st = torch.zeros(C.sizeof(McStats), dtype=torch.uint8, device=dev)
+        ptr = lambda t: None if t is None or t.numel() == 0 else C.c_void_p(t.data_ptr())
+        self._check(lib().lya_scatter_mc(self.ctx, C.byref(mp), ptr(pre), ptr(rec), ptr(st)), "lya_scatter_mc")
+        self.stream.synchronize()
+        s = McStats.from_buffer_copy(st.cpu().numpy().tobytes())
+        stats = dict(count=[int(v) for v in s.count], sampler_caps=int(s.sampler_caps), steps=int(s.steps),
+                     scatterings=int(s.scatterings), nonfinite=int(s.nonfinite))
+        out = rec.cpu().numpy().view(MC_PHOTON) if records else None
+        return out, stats
 
     TIMER_GROUPS = ("alloc", "emit", "march", "transport_end", "rec_step", "adjoint", "other")
 
