@@ -22,6 +22,10 @@
  *   rec_step_adjoint  the reverse (adjoint) of rec_step with the tallies held
  *                  fixed, for gradients of X_e (Sec. II.A) and of the visibility
  *                  function.
+ *   lya_scatter_mc the paper's own resonant-scattering Monte Carlo (Appendix A):
+ *                  single photons scattered on neutral hydrogen (Eq. MC, Eq. inout)
+ *                  until they are lost by redshifting or destroyed, with their
+ *                  travel distances.
  *
  * Conventions (all entry points)
  *   - Every call returns a rec_status; no C++ exception crosses the ABI.
