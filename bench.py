@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prep", type=int, default=S0, help="untimed steps before the warm-up (profiling: 0)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-box measurement")
+    ap.add_argument("--no-scatter", action="store_true", help="skip the scattering Monte-Carlo measurement")
     return ap.parse_args()
 
 
@@ -321,6 +322,73 @@ def time_batched(W, K, prep=60, n_boxes=64):
             "tuning": dict(tuning, source="autotuner table" if tuned else "defaults")}
 
 
+# ---------------------------------------------------- resonant-scattering Monte Carlo
+FP64_DFMA_PER_S = 0.6e12  # measured DFMA-loop rate of a GB300 (1.2 TFLOP/s), FP64 instructions/s
+MC_OPS_PER_STEP, MC_OPS_PER_SCATTER = 70, 400  # FP64 instructions, counted from the kernel source
+
+
+def scatter_workload():
+    from paper_2312_11448_gb300.inputs import density_field, velocity_field
+    n, z = 32, 1700.0
+    return n, z, density_field(n, 0.8, 11).ravel(), velocity_field(n, 1.0, 11)
+
+
+def time_scatter(cpu=True):
+    """Appendix A Monte Carlo (lya_scatter_mc, FP64 arithmetic): one photon per
+    resident lane in a 32^3 box (sigma_lnrho 0.8, sigma_v 1 km/s, Saha x_e) at
+    z = 1700 with the true expansion rate; photons end by photo-ionisation after
+    ~2e4 scatterings.  Throughput over the whole launch, tail included."""
+    import torch
+    from paper_2312_11448_gb300 import rec
+    n, z, d, U = scatter_workload()
+    box = rec.Box(n, d, U, 1000, precision="mixed", mixing="full", seed=11)
+    box.state_init(z)
+    lanes = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 2 * 256
+    kw = dict(x_lost=2000.0, max_steps=1_500_000)
+    box.scatter_mc(z, 2048, records=False, **kw)  # warm-up (module load, Voigt nodes)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(box.stream)
+    _, st = box.scatter_mc(z, lanes, records=False, step=1, **kw)
+    e1.record(box.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    steps_s = st["steps"] / (ms * 1e-3)
+    scat_s = st["scatterings"] / (ms * 1e-3)
+    ach = MC_OPS_PER_STEP * steps_s + MC_OPS_PER_SCATTER * scat_s
+    out = {"workload": f"Appendix A Monte Carlo, {n}^3 box (24 kpc, sigma_lnrho 0.8, sigma_v 1 km/s), Saha x_e, "
+                       f"z = {z:.0f}, zeta = 1, eps = 0.1, {lanes} photons (one per resident lane), FP64 arithmetic",
+           "photons_per_s": lanes / (ms * 1e-3), "steps_per_s": steps_s, "scatterings_per_s": scat_s, "ms": ms,
+           "photons": lanes, "fates": dict(zip(rec.MC_FATES, st["count"])), "sampler_caps": st["sampler_caps"],
+           "steps_per_photon": st["steps"] / lanes,
+           "roofline": {"bound": "alu", "kernel": "k_scatter (FP64 pipe)", "achieved": ach / 1e9,
+                        "peak": FP64_DFMA_PER_S / 1e9, "unit": "G FP64 instructions/s", "frac": ach / FP64_DFMA_PER_S,
+                        "traffic": None,
+                        "note": f"{MC_OPS_PER_STEP} FP64 instructions per step and {MC_OPS_PER_SCATTER} per scattering "
+                                "counted from the source; peak = measured DFMA-loop rate"},
+           "gpu_launches": 2}
+    if cpu:
+        out["cpu_baseline"] = scatter_cpu_baseline(box, n, z, lanes, kw)
+    box.close()
+    return out
+
+
+def scatter_cpu_baseline(box, n, z, n_photons, kw, sample=32):
+    """The oracle's Monte Carlo on the first `sample` photons of the same run (one core)."""
+    import numpy as np
+    import oracle as O
+    cp = O.default_cosmo()
+    P = (np.arange(n ** 3 + 1, dtype=np.int64) * n_photons // n ** 3).astype(np.uint32)
+    mp = O.mc_params(z, seed=11, step=1, x_lost=kw["x_lost"], max_steps=kw["max_steps"])
+    t0 = time.perf_counter()
+    rec_, _ = O.lya_mc(cp, mp, n, box.host("delta").astype(np.float64), box.host("x"), P,
+                       U=box.host("vel4")[:, :3].astype(np.float64), k0=0, k1=sample)
+    dt = time.perf_counter() - t0
+    return {"value": float(rec_["n_steps"].sum()) / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "photons_per_s": sample / dt,
+            "sample": f"oracle Monte Carlo, first {sample} photons of the same run; {platform_name()}"}
+
+
 # ------------------------------------------------------------------------ oracle (CPU)
 def oracle_sample(cfg, zs, sample_packets, threads=0):
     """The oracle as it stands on one host core: one rec_step over every cell and
@@ -476,6 +544,14 @@ def run_ours(args):
         t0 = clocks.mark()
         batched = time_batched(W=2, K=max(3, K // 6))
         clocks.window(t0, clocks.mark())
+    scatter = None
+    if not args.no_scatter and world == 1:
+        t0 = clocks.mark()
+        try:
+            scatter = time_scatter(cpu=not args.no_cpu)
+        except Exception as exc:  # a secondary line: report, keep the main measurement
+            scatter = {"error": f"{type(exc).__name__}: {exc}"}
+        clocks.window(t0, clocks.mark())
     clk = clocks.summary()
 
     def max_over_ranks(v):
@@ -540,6 +616,8 @@ def run_ours(args):
                                "executable graph updated in place", "steps": K}
     if batched:
         out["batched"] = batched
+    if scatter:
+        out["scatter_mc"] = scatter
     out["clocks"] = clk
     if world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(cfg, zs)
