@@ -344,7 +344,7 @@ def time_scatter(cpu=True):
     box = rec.Box(n, d, U, 1000, precision="mixed", mixing="full", seed=11)
     box.state_init(z)
     lanes = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 2 * 256
-    kw = dict(x_lost=2000.0, max_steps=1_500_000)
+    kw = dict(x_lost=2000.0, max_steps=1_000_000)
     box.scatter_mc(z, 2048, records=False, **kw)  # warm-up (module load, Voigt nodes)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
