@@ -304,7 +304,15 @@ typedef struct {
   int32_t pending;     /* lanes of a warp waiting to scatter before the warp runs the
                           redistribution for them, 1..32; 0: 12.  Speed only: results
                           do not depend on it. */
+  int32_t arith;       /* LYA_MC_FP64 (0): binary64 throughout, the oracle's operation
+                          order.  LYA_MC_MIXED (1): binary32 with double-float pairs for
+                          the position inside the cell and the frequency, and integer
+                          thresholds for the scattering and fate decisions;
+                          statistically equivalent, not operation-for-operation equal. */
+  int32_t reserved;    /* 0 */
 } lya_mc_params;
+
+enum { LYA_MC_FP64 = 0, LYA_MC_MIXED = 1 };
 
 enum { LYA_MC_LOST = 0, LYA_MC_TWO_PHOTON = 1, LYA_MC_IONISED = 2, LYA_MC_CAPPED = 3 };
 

@@ -612,6 +612,7 @@ rec_status lya_scatter_mc(rec_ctx* c, const lya_mc_params* mp, const uint32_t* d
     return fail(c, REC_EINVAL, "n_photons must be in [1, 2^32)");
   if (mp->max_steps < 1) return fail(c, REC_EINVAL, "max_steps must be at least 1");
   if (mp->pending < 0 || mp->pending > 32) return fail(c, REC_EINVAL, "pending must be in [0, 32]");
+  if (mp->arith != LYA_MC_FP64 && mp->arith != LYA_MC_MIXED) return fail(c, REC_EINVAL, "unknown arith form");
   rec::McSetup S;
   if (!rec::scatter_setup(c->cosmo, c->params, c->box.n, mp, &S))
     return fail(c, REC_EINVAL, "Monte-Carlo scalars are not finite at this redshift");

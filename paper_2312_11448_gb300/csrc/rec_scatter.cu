@@ -274,6 +274,11 @@ struct McArgs {
   uint64_t max_steps;
   uint32_t k0, k1, box;
   int32_t pending;          // lanes waiting to scatter before a warp runs the redistribution
+  // mixed-arithmetic form
+  const float* tabf;        // Voigt nodes in binary32: H, then H'
+  float af, Kfac, Kx, ufacf, x_lostf;  // a; eps cpm / sig0 (cells of path times n_1s H); dx per cell of path
+  uint32_t thr_scatter;     // scatter when a 32-bit word is below it: (1 - exp(-eps)) 2^32
+  uint64_t thr_ion, thr_end;// fates from a 64-bit word: below thr_ion ionised, below thr_end two-photon
   unsigned long long* next; // photon counter
   unsigned long long* cnt;  // [8]: fates 0..3, sampler caps, steps, scatterings, non-finite photons
   lya_mc_photon* out;       // per photon, or null
@@ -461,6 +466,317 @@ __global__ void __launch_bounds__(ST) k_scatter(McArgs A) {
   if (my_bad) atomicAdd(A.cnt + 7, my_bad);
 }
 
+// ---- mixed-arithmetic form ------------------------------------------------------------
+// The same steps in binary32, with two exceptions.  The position inside the
+// current cell and the frequency are double-float pairs (hi + lo, Knuth's
+// error-free sum), because a step in the line core moves a photon by ~1e-10
+// cells and ~1e-10 Doppler widths.  The scattering and fate decisions compare
+// 32- and 64-bit words with integer thresholds, exact to 2^-32 and 2^-64
+// (p_ion is ~1e-7 at z ~ 1100).  The cell's n_1s and peculiar velocity are
+// cached in registers until the photon changes cell.  Statistically equivalent
+// to the binary64 form; not operation-for-operation equal to it.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (b - bb);
+  const float t = e + lo;
+  hi = s + t;
+  lo = t - (hi - s);
+}
+
+struct McRngF {
+  uint32_t cell, j, blk, tag, k0, k1, w0, w1, w2, w3;
+  int nw;
+  __device__ __forceinline__ void init(uint32_t c, uint32_t jj, uint32_t key0, uint32_t key1, uint32_t box) {
+    cell = c; j = jj; blk = 0; tag = 0x80000000u | box; k0 = key0; k1 = key1; nw = 0;
+    w0 = w1 = w2 = w3 = 0;
+  }
+  __device__ __forceinline__ uint32_t word() {
+    if (nw == 0) {
+      uint32_t r[4];
+      philox(cell, j, blk, tag, k0, k1, r);
+      ++blk;
+      w0 = r[0]; w1 = r[1]; w2 = r[2]; w3 = r[3];
+      nw = 4;
+    }
+    const uint32_t v = w0;
+    w0 = w1; w1 = w2; w2 = w3;
+    --nw;
+    return v;
+  }
+  __device__ __forceinline__ float u01() { return __uint2float_rn((word() >> 8) | 1u) * 0x1p-24f; }
+};
+
+__device__ __forceinline__ void disk_f(McRngF& s, float& v1, float& v2, float& r2) {
+  for (int it = 0; it < 64; ++it) {
+    v1 = 2.0f * s.u01() - 1.0f;
+    v2 = 2.0f * s.u01() - 1.0f;
+    r2 = v1 * v1 + v2 * v2;
+    if (r2 < 1.0f) return;
+  }
+  v1 = 0.3f; v2 = 0.4f; r2 = 0.25f;
+}
+
+// H(a, t) in binary32: cubic Hermite on the nodes for t < 10; beyond, the
+// first-order-in-a wing series (a / sqrt(pi)) sum_k (2k+1)!! / (2^k t^(2k+2)),
+// five terms (relative error below 1e-7 for t >= 10).
+__device__ __forceinline__ float voigt_f(const float* H, const float* dH, float y, float a) {
+  const float t = fabsf(y);
+  if (!(t < 10.0f)) {
+    const float q = 1.0f / (t * t);
+    return a * 0.5641895835f * q * (1.0f + q * (1.5f + q * (3.75f + q * (13.125f + q * 59.0625f))));
+  }
+  const float qq = t * 128.0f;
+  int k = (int)qq;
+  if (k > kVoigtNodes - 2) k = kVoigtNodes - 2;
+  const float s = qq - (float)k;
+  const float s1 = 1.0f - s;
+  const float h00 = (1.0f + 2.0f * s) * s1 * s1, h10 = s * s1 * s1;
+  const float h01 = s * s * (3.0f - 2.0f * s), h11 = s * s * (s - 1.0f);
+  const float st = (float)kVoigtStep;
+  return h00 * H[k] + h10 * st * dH[k] + h01 * H[k + 1] + h11 * st * dH[k + 1];
+}
+
+__device__ __forceinline__ float cut_u0_f(float t, float a) {
+  if (t < 1.2f) return -0.7f;
+  if (t >= 10.0f) return sqrtf(logf(t * t / a) + 4.0f);
+  if (t < 2.0f) return 1.1f + 0.875f * (t - 1.2f);
+  if (t < 3.0f) return 1.8f + 0.7f * (t - 2.0f);
+  if (t < 4.0f) return 2.5f + 0.45f * (t - 3.0f);
+  if (t < 6.0f) return 2.95f + 0.225f * (t - 4.0f);
+  return 3.4f + 0.1f * (t - 6.0f);
+}
+
+__device__ float sample_ppar_f(McRngF& s, float y, float a, unsigned long long* caps) {
+  const float t = fabsf(y);
+  const float u0 = cut_u0_f(t, a);
+  const float d0 = t - u0;
+  const float m0 = u0 > 0.0f ? u0 : 0.0f;
+  const float W1 = 0.8862269255f * (1.0f + erff(u0)) / (d0 * d0 + a * a);
+  const float W2 = expf(-m0 * m0) * (1.5707963268f + atanf(d0 / a)) / a;
+  const float P1 = W1 / (W1 + W2);
+  for (int it = 0; it < kMaxTries; ++it) {
+    float p, v1, v2, r2;
+    if (s.u01() < P1) {
+      disk_f(s, v1, v2, r2);
+      p = v1 * sqrtf(-logf(r2) / r2);
+      if (p > u0) continue;
+      const float d = t - p;
+      if (s.u01() * (d * d + a * a) >= d0 * d0 + a * a) continue;
+    } else {
+      disk_f(s, v1, v2, r2);
+      p = t + a * (v1 / v2);
+      if (p <= u0) continue;
+      if (s.u01() >= expf(m0 * m0 - p * p)) continue;
+    }
+    return y < 0.0f ? -p : p;
+  }
+  ++*caps;
+  return 0.0f;
+}
+
+__device__ float redistribute_f(McRngF& s, float y, float a, float k[3], unsigned long long* caps) {
+  const float p = sample_ppar_f(s, y, a, caps);
+  const float r = sqrtf(-logf(s.u01()));
+  const float mu = 2.0f * s.u01() - 1.0f;
+  float v1, v2, r2;
+  disk_f(s, v1, v2, r2);
+  const float cb = (v1 * v1 - v2 * v2) / r2;
+  disk_f(s, v1, v2, r2);
+  const float cphi = (v1 * v1 - v2 * v2) / r2, sphi = 2.0f * v1 * v2 / r2;
+  const float sm = sqrtf(fmaxf(1.0f - mu * mu, 0.0f));
+  const float sg = copysignf(1.0f, k[2]);
+  const float aa = -1.0f / (sg + k[2]);
+  const float bb = k[0] * k[1] * aa;
+  const float e1x = 1.0f + sg * k[0] * k[0] * aa, e1y = sg * bb, e1z = -sg * k[0];
+  const float e2x = bb, e2y = sg + k[1] * k[1] * aa, e2z = -k[1];
+  const float nx = mu * k[0] + sm * (cphi * e1x + sphi * e2x);
+  const float ny = mu * k[1] + sm * (cphi * e1y + sphi * e2y);
+  const float nz = mu * k[2] + sm * (cphi * e1z + sphi * e2z);
+  const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+  k[0] = nx * inv; k[1] = ny * inv; k[2] = nz * inv;
+  return y - p * (1.0f - mu) + r * sm * cb;
+}
+
+template <class R>
+__global__ void __launch_bounds__(ST) k_scatter_mixed(McArgs A) {
+  __shared__ float sH[kVoigtNodes], sD[kVoigtNodes];
+  for (int i = threadIdx.x; i < kVoigtNodes; i += blockDim.x) {
+    sH[i] = A.tabf[i];
+    sD[i] = A.tabf[kVoigtNodes + i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int n = A.n;
+  bool active = false, retired = false, pend = false;
+  uint64_t k = 0, steps = 0, nscat = 0;
+  uint32_t home = 0, j = 0;
+  int ic[3] = {0, 0, 0}, is[3] = {0, 0, 0};
+  float fh[3] = {0.f, 0.f, 0.f}, fl[3] = {0.f, 0.f, 0.f}, sf[3] = {0.f, 0.f, 0.f};
+  float kd[3] = {0.f, 0.f, 1.f}, U[3] = {0.f, 0.f, 0.f};
+  float xh = 0.f, xl = 0.f, up = 0.f, Kc = 0.f;
+  McRngF rng;
+  rng.init(0, 0, 0, 0, 0);
+  unsigned long long my_steps = 0, my_scat = 0, my_caps = 0, my_bad = 0;
+  unsigned long long f_lost = 0, f_2g = 0, f_ion = 0, f_cap = 0;
+
+  // cached quantities of the cell the photon is in
+  auto load_cell = [&]() {
+    int w[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int q = ic[d] % n;
+      w[d] = q < 0 ? q + n : q;
+    }
+    const int64_t c = ((int64_t)w[2] * n + w[1]) * n + w[0];
+    const double n1s = A.nH * Field<R>::delta(A.delta, c) * (1.0 - __ldg(A.x + c));
+    Kc = (float)(A.Kfac / n1s);
+    double u[3];
+    Field<R>::vel(A.vel, c, u);
+    U[0] = (float)u[0]; U[1] = (float)u[1]; U[2] = (float)u[2];
+  };
+  auto upar = [&]() { return (U[0] * kd[0] + U[1] * kd[1] + U[2] * kd[2]) * A.ufacf; };
+
+  auto finish = [&](int fate) {
+    if (fate == LYA_MC_LOST) ++f_lost;
+    else if (fate == LYA_MC_TWO_PHOTON) ++f_2g;
+    else if (fate == LYA_MC_IONISED) ++f_ion;
+    else ++f_cap;
+    my_steps += steps;
+    my_scat += nscat;
+    if (A.out) {
+      double dd = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double e = (double)(ic[d] - is[d]) + (((double)fh[d] + (double)fl[d]) - (double)sf[d]);
+        dd += e * e;
+      }
+      lya_mc_photon o;
+      o.home = home;
+      o.j = j;
+      o.fate = fate;
+      o.reserved = 0;
+      o.n_scat = nscat;
+      o.n_steps = steps;
+      o.D_kpc = sqrt(dd) * A.kpc_cell;
+      o.x_end = (double)xh + (double)xl;
+      A.out[k] = o;
+    }
+    active = false;
+  };
+
+  for (;;) {
+    const unsigned need = __ballot_sync(kFull, !active && !retired);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(A.next, (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (need & (1u << lane)) {
+        k = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+        if (k < A.N) {
+          uint64_t p0;
+          const int64_t h = home_of(A, k, &p0);
+          home = (uint32_t)h;
+          j = (uint32_t)(k - p0);
+          rng.init(home, j, A.k0, A.k1, A.box);
+          ic[0] = (int)(h % n); ic[1] = (int)((h / n) % n); ic[2] = (int)(h / ((int64_t)n * n));
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            is[d] = ic[d];
+            fh[d] = rng.u01();
+            fl[d] = 0.0f;
+            sf[d] = fh[d];
+          }
+          float v1, v2, r2;
+          disk_f(rng, v1, v2, r2);
+          const float q = 2.0f * sqrtf(1.0f - r2);
+          kd[0] = v1 * q; kd[1] = v2 * q; kd[2] = 1.0f - 2.0f * r2;
+          load_cell();
+          up = upar();
+          xh = up;  // line centre in the gas frame of the emitting cell
+          xl = 0.0f;
+          steps = 0;
+          nscat = 0;
+          pend = false;
+          active = true;
+        } else {
+          retired = true;
+        }
+      }
+    }
+    if (__ballot_sync(kFull, active) == 0) break;
+
+    if (active && !pend) {
+      const float y = (xh - up) + xl;
+      if (y < -A.x_lostf) {
+        finish(LYA_MC_LOST);
+      } else {
+        const float dcell = __fdividef(Kc, voigt_f(sH, sD, y, A.af));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) df_add(fh[d], fl[d], kd[d] * dcell);
+        df_add(xh, xl, -(A.Kx * dcell));
+        ++steps;
+        if (!(dcell < 1e30f) || !(fabsf(xh) < 1e30f)) {
+          ++my_bad;
+          finish(LYA_MC_CAPPED);
+        } else {
+          if (fh[0] < 0.0f || fh[0] >= 1.0f || fh[1] < 0.0f || fh[1] >= 1.0f || fh[2] < 0.0f || fh[2] >= 1.0f) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              const float m = floorf(fh[d]);
+              if (m != 0.0f) {
+                ic[d] += (int)m;
+                fh[d] -= m;
+                const float s2 = fh[d] + fl[d];  // renormalise the pair
+                fl[d] = fl[d] - (s2 - fh[d]);
+                fh[d] = s2;
+              }
+            }
+            load_cell();
+            up = upar();
+          }
+          if (rng.word() < A.thr_scatter) pend = true;
+          else if (steps >= A.max_steps) finish(LYA_MC_CAPPED);
+        }
+      }
+    }
+
+    const unsigned waiting = __ballot_sync(kFull, pend);
+    const unsigned stepping = __ballot_sync(kFull, active && !pend);
+    if (waiting && (__popc(waiting) >= A.pending || stepping == 0)) {
+      if (pend) {
+        pend = false;
+        ++nscat;
+        const uint64_t hi = rng.word();
+        const uint64_t uf = (hi << 32) | rng.word();
+        if (uf < A.thr_ion) {
+          finish(LYA_MC_IONISED);
+        } else if (uf < A.thr_end) {
+          finish(LYA_MC_TWO_PHOTON);
+        } else {
+          const float y = (xh - up) + xl;
+          const float yo = redistribute_f(rng, y, A.af, kd, &my_caps);
+          up = upar();
+          const float s2 = yo + up;  // x = y_out + u_par as a double-float pair
+          const float bb = s2 - yo;
+          xl = (yo - (s2 - bb)) + (up - bb);
+          xh = s2;
+          if (steps >= A.max_steps) finish(LYA_MC_CAPPED);
+        }
+      }
+    }
+  }
+  if (f_lost) atomicAdd(A.cnt + 0, f_lost);
+  if (f_2g) atomicAdd(A.cnt + 1, f_2g);
+  if (f_ion) atomicAdd(A.cnt + 2, f_ion);
+  if (f_cap) atomicAdd(A.cnt + 3, f_cap);
+  if (my_caps) atomicAdd(A.cnt + 4, my_caps);
+  if (my_steps) atomicAdd(A.cnt + 5, my_steps);
+  if (my_scat) atomicAdd(A.cnt + 6, my_scat);
+  if (my_bad) atomicAdd(A.cnt + 7, my_bad);
+}
+
 __global__ void k_scatter_stats(const unsigned long long* cnt, lya_mc_stats* st) {
   if (threadIdx.x != 0 || !st) return;
   for (int f = 0; f < 4; ++f) st->count[f] = cnt[f];
@@ -515,9 +831,12 @@ void scatter_voigt_host(double a, int64_t m, const double* y, double* H) {
 
 cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp, const uint32_t* prefix,
                            lya_mc_photon* out, lya_mc_stats* st) {
-  // Voigt nodes and counters in one scratch allocation owned by the context
+  // Voigt nodes (binary64 and binary32) and counters in one scratch
+  // allocation owned by the context
   const size_t tab_bytes = sizeof(double) * 2 * kVoigtNodes;
-  const size_t need = tab_bytes + sizeof(unsigned long long) * 9;
+  const size_t tabf_bytes = sizeof(float) * 2 * kVoigtNodes;
+  const size_t cnt_off = tab_bytes + ((tabf_bytes + 255) / 256) * 256;
+  const size_t need = cnt_off + sizeof(unsigned long long) * 9;
   if (c->mc_bytes < need) {
     if (c->mc_scratch) cudaFree(c->mc_scratch);
     c->mc_scratch = nullptr;
@@ -527,11 +846,16 @@ cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp
     c->mc_bytes = need;
   }
   double* tab = (double*)c->mc_scratch;
-  unsigned long long* cnt = (unsigned long long*)((char*)c->mc_scratch + tab_bytes);
+  float* tabf = (float*)((char*)c->mc_scratch + tab_bytes);
+  unsigned long long* cnt = (unsigned long long*)((char*)c->mc_scratch + cnt_off);
   if (S.a != c->mc_a) {
     std::vector<double> h(2 * kVoigtNodes);
     voigt_nodes(S.a, h.data(), h.data() + kVoigtNodes);
+    std::vector<float> hf(2 * kVoigtNodes);
+    for (int i = 0; i < 2 * kVoigtNodes; ++i) hf[i] = (float)h[i];
     cudaError_t e = cudaMemcpyAsync(tab, h.data(), tab_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(tabf, hf.data(), tabf_bytes, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(c->stream);  // the host buffer goes out of scope
     if (e != cudaSuccess) return e;
@@ -565,15 +889,32 @@ cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp
   A.k1 = (uint32_t)(c->params.seed >> 32) ^ (uint32_t)mp->step;
   A.box = 0;
   A.pending = mp->pending > 0 ? mp->pending : 12;
+  A.tabf = tabf;
+  A.af = (float)S.a;
+  A.Kfac = (float)(mp->eps * S.cpm / S.sig0);
+  A.Kx = (float)(S.dxdl / S.cpm);
+  A.ufacf = (float)S.ufac;
+  A.x_lostf = (float)mp->x_lost;
+  {
+    const double ps = -std::expm1(-mp->eps);  // 1 - exp(-eps)
+    const double t32 = std::floor(std::ldexp(ps, 32) + 0.5);
+    A.thr_scatter = t32 >= 4294967295.0 ? 0xffffffffu : (uint32_t)t32;
+    const double ti = std::ldexp(S.p_ion, 64), te = std::ldexp(S.p_ion + S.p_2g, 64);
+    A.thr_ion = ti >= 18446744073709549568.0 ? ~0ull : (uint64_t)ti;
+    A.thr_end = te >= 18446744073709549568.0 ? ~0ull : (uint64_t)te;
+  }
   A.next = cnt + 8;
   A.cnt = cnt;
   A.out = out;
   // one persistent pass: blocks per SM limited by the kernel's resources
   int per_sm = 0;
-  if (c->params.precision == REC_PREC_MIXED)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<float>, ST, 0);
+  const bool fmix = c->params.precision == REC_PREC_MIXED, amix = mp->arith == LYA_MC_MIXED;
+  if (amix)
+    e = fmix ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter_mixed<float>, ST, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter_mixed<double>, ST, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<double>, ST, 0);
+    e = fmix ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<float>, ST, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<double>, ST, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const uint64_t warps_needed = (mp->n_photons + 31) / 32;
@@ -583,10 +924,13 @@ cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp
   if (blocks < 1) blocks = 1;
   {
     GroupTimer t(c, kTOther, 2);
-    if (c->params.precision == REC_PREC_MIXED)
-      k_scatter<float><<<(unsigned)blocks, ST, 0, c->stream>>>(A);
-    else
-      k_scatter<double><<<(unsigned)blocks, ST, 0, c->stream>>>(A);
+    if (amix) {
+      if (fmix) k_scatter_mixed<float><<<(unsigned)blocks, ST, 0, c->stream>>>(A);
+      else k_scatter_mixed<double><<<(unsigned)blocks, ST, 0, c->stream>>>(A);
+    } else {
+      if (fmix) k_scatter<float><<<(unsigned)blocks, ST, 0, c->stream>>>(A);
+      else k_scatter<double><<<(unsigned)blocks, ST, 0, c->stream>>>(A);
+    }
     k_scatter_stats<<<1, 32, 0, c->stream>>>(cnt, st);
   }
   return cudaGetLastError();

@@ -58,7 +58,8 @@ class McParams(C.Structure):
     """lya_mc_params: one resonant-scattering Monte-Carlo run (Appendix A)."""
     _fields_ = [("z", C.c_double), ("eps", C.c_double), ("x_lost", C.c_double), ("zeta", C.c_double),
                 ("lambda2g", C.c_double), ("A_alpha", C.c_double), ("n_photons", C.c_uint64),
-                ("max_steps", C.c_uint64), ("step", C.c_int32), ("pending", C.c_int32)]
+                ("max_steps", C.c_uint64), ("step", C.c_int32), ("pending", C.c_int32), ("arith", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class McStats(C.Structure):
@@ -162,10 +163,14 @@ def voigt(a: float, y) -> np.ndarray:
     return H
 
 
+MC_ARITH = {"fp64": 0, "mixed": 1}
+
+
 def mc_params(z, n_photons, eps=0.1, x_lost=1.0e4, zeta=1.0, lambda2g=-1.0, A_alpha=A_2P1S, max_steps=10 ** 9,
-              step=0, pending=0) -> McParams:
+              step=0, pending=0, arith="fp64") -> McParams:
     return McParams(z=z, eps=eps, x_lost=x_lost, zeta=zeta, lambda2g=lambda2g, A_alpha=A_alpha,
-                    n_photons=int(n_photons), max_steps=int(max_steps), step=int(step), pending=int(pending))
+                    n_photons=int(n_photons), max_steps=int(max_steps), step=int(step), pending=int(pending),
+                    arith=MC_ARITH[arith], reserved=0)
 
 
 class Batch:
