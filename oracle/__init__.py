@@ -102,6 +102,7 @@ def _bind(L):
                                    i, d, P(d)]
     L.orc_threads.argtypes = [i]
     L.orc_divergence.argtypes = [P(Cosmo), i, d, P(d), P(d)]
+    L.orc_rec_step_trbdf2.argtypes = [P(Cosmo), i, i, i, d, d, P(d), P(d), P(d), P(d), P(u32), P(d), P(d)]
     L.orc_faddeeva.argtypes = [d, d, P(d)]
     L.orc_voigt_table.argtypes = [d, i64, P(d), P(d)]
     L.orc_mc_setup.argtypes = [P(Cosmo), P(McParams), i, P(d)]
@@ -150,8 +151,11 @@ def saha_xe(cp: Cosmo, z: float, delta) -> np.ndarray:
 
 
 def rec_step(cp: Cosmo, n: int, z_from: float, z_to: float, delta, x, T, U=None, tally=None, mixing="tally",
-             n_sub=1, want_emis=True, f_alpha=1.0):
-    """One step; returns (x', T', U', emis, stats).  Inputs are not modified."""
+             n_sub=1, want_emis=True, f_alpha=1.0, integrator="be"):
+    """One step; returns (x', T', U', emis, stats).  Inputs are not modified.
+    integrator: "be" (backward Euler) or "trbdf2" (second order; tally and full mixing)."""
+    if integrator == "trbdf2":
+        return _rec_step_trbdf2(cp, n, z_from, z_to, delta, x, T, U, tally, mixing, n_sub, want_emis)
     d = _f64(delta).ravel()
     x1 = _f64(x).ravel().copy()
     T1 = _f64(T).ravel().copy()
@@ -272,6 +276,25 @@ def traj_tangent(cp, n, zs, delta, x0, T0, d_delta=None, d_T0=None, d_a=None, ta
                                 objective, z_star, _p(J, C.c_double))
     _check(rc, "traj_tangent")
     return J[0], J[1]
+
+
+def _rec_step_trbdf2(cp, n, z_from, z_to, delta, x, T, U, tally, mixing, n_sub, want_emis):
+    d = _f64(delta).ravel()
+    x1 = _f64(x).ravel().copy()
+    T1 = _f64(T).ravel().copy()
+    U1 = None if U is None else _f64(U).reshape(-1, 3).copy()
+    t = None if tally is None else np.ascontiguousarray(tally, dtype=np.uint32).ravel()
+    em = np.empty_like(d) if want_emis else None
+    st = np.zeros(6)
+    if mixing not in ("tally", "full"):
+        raise ValueError("the TR-BDF2 step covers tally and full mixing")
+    mix = {"tally": 0, "full": 1}[mixing]
+    rc = lib().orc_rec_step_trbdf2(C.byref(cp), n, mix, n_sub, z_from, z_to, _p(d, C.c_double), _p(x1, C.c_double),
+                                   _p(T1, C.c_double), _p(U1, C.c_double), _p(t, C.c_uint32), _p(em, C.c_double),
+                                   _p(st, C.c_double))
+    _check(rc, "rec_step_trbdf2")
+    stats = dict(lam=st[0], C=st[1], Xe=st[2], iters=int(st[3]), S1s=st[4], dt=st[5])
+    return x1, T1, U1, em, stats
 
 
 # ---- resonant-scattering Ly-alpha Monte Carlo (Appendix A) ----------------------

@@ -73,6 +73,17 @@ int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_fro
                  const double* delta, double* x, double* T, double* U, const uint32_t* tally,
                  double* emis, double* stats, double f_alpha);
 
+/* The same step as orc_rec_step (modes 0 = TALLY and 1 = FULL) advanced by the
+ * second-order TR-BDF2 scheme per substep: a trapezoidal stage to t + gamma h
+ * (gamma = 2 - sqrt 2) and a BDF2 stage to t + h, each stage end fully
+ * implicit in x, T, lambda and the Peebles factor; drag with the trapezoidal
+ * exponent.  Returns -3 where a stage has no positive root (step too long).
+ * Pinned by second-order convergence to stiff ODE integrations of the
+ * standard three-level atom and of the two-zone system. */
+int orc_rec_step_trbdf2(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_from, double z_to,
+                        const double* delta, double* x, double* T, double* U, const uint32_t* tally, double* emis,
+                        double* stats);
+
 /* Physical divergence of the peculiar velocity U ([n^3][3], km/s) at redshift
  * z, 1/s: periodic central differences on the comoving grid of side L_box,
  * times 1 + z.  Pinned by the closed form for sinusoidal fields. */

@@ -355,6 +355,188 @@ void substep(const Cosmo& cm, int n, int64_t n3, int mixing, double fmix, double
   st->dt = dt;
 }
 
+// ---- second-order substep: TR-BDF2 ------------------------------------------
+// The same per-cell system as the backward-Euler substep (Eq. dotne-mix per
+// hydrogen atom, dx/dt = -alpha(T) n_H x^2 + w G (1 - x) with
+// G = (1 - C) lambda + C beta e_alpha, lambda = <alpha n_e^2>/<n_1s> and C the
+// Peebles factor of Eq. Cfactor with R_alpha^mix from <n_1s>; Eq. Tb-evolution
+// for T) advanced by TR-BDF2 (Bank et al., IEEE Trans. CAD 4, 436 (1985)):
+// a trapezoidal stage to t + gamma h, gamma = 2 - sqrt 2, then a BDF2 stage to
+// t + h.  Every coefficient is taken at the time it belongs to, and each stage
+// end is fully implicit: x, T, lambda and C all at the stage end.
+
+// Coefficients that depend only on the redshift.
+struct Coef {
+  double H, nH, Tg, kc, kd, hq, beta, ea, KR;
+};
+
+Coef coef_at(const Cosmo& cm, double z) {
+  Coef k;
+  k.H = hubble(cm, z);
+  k.nH = nH_bar(cm, z);
+  k.Tg = T_gamma(cm, z);
+  const double Tg4 = k.Tg * k.Tg * k.Tg * k.Tg;
+  k.kc = 8.0 * kSigmaT * kARad * Tg4 / (3.0 * kMe * kC);
+  k.kd = 4.0 * kSigmaT * kARad * Tg4 * (1.0 - cm.Yp) / (3.0 * kC * kMH);
+  k.hq = 2.0 * cm.heat * kEV / (3.0 * kKB);
+  k.beta = beta_e(cm, k.Tg);
+  k.ea = std::exp(-kEalpha / (kKB * k.Tg));
+  k.KR = 8.0 * kPi * k.H / (kLambdaAlpha * kLambdaAlpha * kLambdaAlpha);
+  return k;
+}
+
+// Peebles factor with R_alpha^mix at the state x (Eq. Cfactor, Sec. IV.A.2).
+double peebles_mix(const Coef& k, int64_t n3, const double* delta, const double* x) {
+  double S = 0.0;
+  for (int64_t i = 0; i < n3; ++i) S += delta[i] * (1.0 - x[i]);
+  const double Rmix = k.KR / (k.nH * S / (double)n3);
+  return (kLambda2g + Rmix) / (k.beta + kLambda2g + Rmix);
+}
+
+// Time derivatives of x and T at a state, with lambda and C of that state.
+void rates_at(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta, const double* w, const double* x,
+              const double* T, double* fx, double* fT) {
+  const double C = peebles_mix(k, n3, delta, x);
+  double num = 0.0, den = 0.0;
+  for (int64_t i = 0; i < n3; ++i) {
+    const double nn = k.nH * delta[i];
+    num += alpha_e<double>(cm, T[i]) * nn * nn * x[i] * x[i];
+    den += nn * (1.0 - x[i]);
+  }
+  const double lam = num / den;
+  const double G = (1.0 - C) * lam + C * k.beta * k.ea;
+  for (int64_t i = 0; i < n3; ++i) {
+    const double nn = k.nH * delta[i];
+    fx[i] = -alpha_e<double>(cm, T[i]) * nn * x[i] * x[i] + w[i] * G * (1.0 - x[i]);
+    const double g = k.kc * x[i] / (1.0 + cm.fHe + x[i]);
+    const double hh = k.hq / (delta[i] * (1.0 + cm.fHe + x[i]));
+    fT[i] = -2.0 * k.H * T[i] + g * (k.Tg - T[i]) + hh;
+  }
+}
+
+// One implicit stage: find x, T (and lambda, C) at the stage end with
+//   x_i = bx_i + h fx_i(x, T),   T_i = bT_i + h fT_i(x_i, T_i).
+// T is linear given x; x is the positive root of the backward-Euler quadratic
+// with x_old -> bx for a given G, and lambda solves its Newton equation as in the
+// backward-Euler substep.  The outer iteration repeats T, alpha(T), C(x) and the
+// lambda solve until x and T no longer change.  x, T hold the initial guess and
+// receive the result.  Returns the Newton iterations, or -1 where a stage has no
+// positive root (the step is too long for the explicit part of the stage).
+int stage_solve(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta, const double* w, double h,
+                const double* bx, const double* bT, double* x, double* T, double* lam_out, double* C_out) {
+  std::vector<double> Tn(n3), al(n3), nn(n3), A(n3), sv(n3), xn(n3);
+  int iters = 0;
+  double lam = 0.0, C = 0.0;
+  for (int outer = 0; outer < 200; ++outer) {
+    C = peebles_mix(k, n3, delta, x);
+    for (int64_t i = 0; i < n3; ++i) {
+      const double g = k.kc * x[i] / (1.0 + cm.fHe + x[i]);
+      const double hh = k.hq / (delta[i] * (1.0 + cm.fHe + x[i]));
+      Tn[i] = (bT[i] + h * (g * k.Tg + hh)) / (1.0 + h * (2.0 * k.H + g));
+      al[i] = alpha_e<double>(cm, Tn[i]);
+      nn[i] = k.nH * delta[i];
+      A[i] = h * al[i] * nn[i];
+      sv[i] = h * w[i];
+      if (!(bx[i] + sv[i] * C * k.beta * k.ea > 0.0)) return -1;
+    }
+    const double CBe = C * k.beta * k.ea, omC = 1.0 - C;
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < n3; ++i) {
+      num += al[i] * nn[i] * nn[i] * x[i] * x[i];
+      den += nn[i] * (1.0 - x[i]);
+    }
+    lam = num / den;
+    for (int it = 1; it <= 200; ++it) {
+      ++iters;
+      const double G = omC * lam + CBe;
+      double F = 0.0, Fp = 0.0;
+      for (int64_t i = 0; i < n3; ++i) {
+        double dxdG;
+        const double xr = be_root<double>(A[i], sv[i], G, bx[i], &dxdG);
+        const double an2 = al[i] * nn[i] * nn[i];
+        F += an2 * xr * xr - lam * nn[i] * (1.0 - xr);
+        Fp += (2.0 * an2 * xr + lam * nn[i]) * dxdG * omC - nn[i] * (1.0 - xr);
+      }
+      const double step = F / Fp;
+      double lnew = lam - step;
+      if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
+      const bool conv = std::fabs(step) <= 1e-13 * std::fabs(lam);
+      lam = lnew;
+      if (conv) break;
+    }
+    const double G = omC * lam + CBe;
+    double dmax = 0.0;
+    for (int64_t i = 0; i < n3; ++i) {
+      xn[i] = be_root<double>(A[i], sv[i], G, bx[i], nullptr);
+      dmax = std::max(dmax, std::fabs(xn[i] - x[i]) / xn[i]);
+      dmax = std::max(dmax, std::fabs(Tn[i] - T[i]) / Tn[i]);
+    }
+    for (int64_t i = 0; i < n3; ++i) { x[i] = xn[i]; T[i] = Tn[i]; }
+    if (dmax <= 1e-14) break;
+  }
+  *lam_out = lam;
+  *C_out = C;
+  return iters;
+}
+
+// Redshift z_g in [z_b, z_a] at which the cosmic time since z_a is tau.
+double z_after(const Cosmo& cm, double za, double zb, double tau) {
+  double lo = zb, hi = za;  // cosmic_dt(za, z) grows as z falls
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (cosmic_dt(cm, za, mid) < tau) hi = mid; else lo = mid;
+    if (hi - lo <= 1e-13 * za) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// One TR-BDF2 substep z_a -> z_b.  The cosmic times use the same Simpson rule
+// as the backward-Euler substep.  Drag: U' = U exp(-int (alpha_C + H) dt) with
+// the trapezoidal rule for the exponent.  Returns -1 as stage_solve does.
+int substep_trbdf2(const Cosmo& cm, int64_t n3, double za, double zb, const double* delta, const double* w,
+                   double* x, double* T, double* U, double* emis, SubStats<double>* st) {
+  const double gam = 2.0 - std::sqrt(2.0);
+  const double h = cosmic_dt(cm, za, zb);
+  const double zg = z_after(cm, za, zb, gam * h);
+  const Coef ka = coef_at(cm, za), kg = coef_at(cm, zg), kb = coef_at(cm, zb);
+  std::vector<double> fx(n3), fT(n3), bx(n3), bT(n3), xg(x, x + n3), Tg(T, T + n3);
+  rates_at(cm, ka, n3, delta, w, x, T, fx.data(), fT.data());
+  // trapezoidal stage to t + gamma h
+  const double h1 = 0.5 * gam * h;
+  for (int64_t i = 0; i < n3; ++i) { bx[i] = x[i] + h1 * fx[i]; bT[i] = T[i] + h1 * fT[i]; }
+  double lam, C;
+  const int it1 = stage_solve(cm, kg, n3, delta, w, h1, bx.data(), bT.data(), xg.data(), Tg.data(), &lam, &C);
+  if (it1 < 0) return -1;
+  // BDF2 stage to t + h
+  const double h2 = (1.0 - gam) / (2.0 - gam) * h;
+  const double c1 = 1.0 / (gam * (2.0 - gam)), c0 = (1.0 - gam) * (1.0 - gam) / (gam * (2.0 - gam));
+  std::vector<double> xb(xg), Tb(Tg);
+  for (int64_t i = 0; i < n3; ++i) { bx[i] = c1 * xg[i] - c0 * x[i]; bT[i] = c1 * Tg[i] - c0 * T[i]; }
+  const int it2 = stage_solve(cm, kb, n3, delta, w, h2, bx.data(), bT.data(), xb.data(), Tb.data(), &lam, &C);
+  if (it2 < 0) return -1;
+  double sx = 0.0, sd = 0.0, S = 0.0;
+  for (int64_t i = 0; i < n3; ++i) {
+    if (U != nullptr) {
+      const double damp = std::exp(-0.5 * h * ((ka.kd * x[i] + ka.H) + (kb.kd * xb[i] + kb.H)));
+      U[3 * i + 0] *= damp; U[3 * i + 1] *= damp; U[3 * i + 2] *= damp;
+    }
+    x[i] = xb[i];
+    T[i] = Tb[i];
+    const double nn = kb.nH * delta[i];
+    if (emis) emis[i] = alpha_e<double>(cm, Tb[i]) * (nn * xb[i]) * (nn * xb[i]);
+    sx += delta[i] * xb[i];
+    sd += delta[i];
+    S += delta[i] * (1.0 - xb[i]);
+  }
+  st->lambda = lam;
+  st->C = C;
+  st->Xe = sx / sd;
+  st->S1s = S;
+  st->iters = it1 + it2;
+  st->dt = h;
+  return 0;
+}
+
 // n_sub substeps uniform in ln(1+z) between z_from and z_to.
 double sub_z(double z_from, double z_to, int k, int n_sub) {
   if (k == 0) return z_from;
@@ -486,6 +668,45 @@ int orc_rec_step(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_fro
   }
   SubStats<double> st;
   rec_step_t<double>(c, n, mixing, f_alpha, n_sub, z_from, z_to, delta, x, T, U, afp, emis, &st);
+  if (stats) {
+    stats[0] = st.lambda;
+    stats[1] = st.C;
+    stats[2] = st.Xe;
+    stats[3] = st.iters;
+    stats[4] = st.S1s;
+    stats[5] = st.dt;
+  }
+  return 0;
+}
+
+int orc_rec_step_trbdf2(const orc_cosmo* cp, int n, int mixing, int n_sub, double z_from, double z_to,
+                        const double* delta, double* x, double* T, double* U, const uint32_t* tally, double* emis,
+                        double* stats) {
+  if (!cp || n <= 0 || n_sub <= 0 || !delta || !x || !T || !(z_from > z_to) || (mixing != 0 && mixing != 1))
+    return -1;
+  Cosmo c = make_cosmo(cp);
+  const int64_t n3 = (int64_t)n * n * n;
+  // w_i = J_i / <J> from the absorbed-Ly-alpha fractions (TALLY), 1 otherwise; held
+  // over the step as in the backward-Euler substep (it uses the step-start n_1s)
+  std::vector<double> w(n3, 1.0);
+  if (mixing == 0 && tally != nullptr) {
+    uint64_t tot = 0;
+    for (int64_t i = 0; i < n3; ++i) tot += tally[i];
+    double S = 0.0;
+    for (int64_t i = 0; i < n3; ++i) S += delta[i] * (1.0 - x[i]);
+    if (tot > 0 && S > 0.0) {
+      for (int64_t i = 0; i < n3; ++i) {
+        const double n1s_rel = delta[i] * (1.0 - x[i]);
+        if (n1s_rel > 0.0) w[i] = ((double)tally[i] / (double)tot) * S / n1s_rel;
+      }
+    }
+  }
+  SubStats<double> st;
+  for (int k = 0; k < n_sub; ++k) {
+    if (substep_trbdf2(c, n3, sub_z(z_from, z_to, k, n_sub), sub_z(z_from, z_to, k + 1, n_sub), delta, w.data(), x,
+                       T, U, emis, &st) != 0)
+      return -3;
+  }
   if (stats) {
     stats[0] = st.lambda;
     stats[1] = st.C;
