@@ -23,7 +23,11 @@ import pytest
 from scipy import integrate, stats
 from scipy.special import erfcx, wofz
 
+import json
+
 import oracle as O
+
+PV = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 
 # Independent constants for the checks (SI, CODATA 2018).
 C_LIGHT = 2.99792458e8
@@ -105,9 +109,40 @@ def test_wing_balance_x50_and_mean_free_path():
     sigma = S["sig0"] * O.voigt_table(S["a"], xs)
     lhs = S["dxdl"] / (sigma * n1s)      # H l / v_th per mean free path
     x50 = xs[np.argmin(np.abs(lhs - 1.0 / xs))]
-    assert 45.0 < x50 < 75.0
+    lo, hi = PV["x50"]["band"]
+    assert lo < x50 < hi
     l_com_kpc = (1.0 + 1100.0) / (S["sig0"] * O.voigt_table(S["a"], [x50])[0] * n1s) / KPC
-    assert 0.05 < l_com_kpc < 0.2
+    lo, hi = PV["mfp_at_x50_kpc"]["band"]
+    assert lo < l_com_kpc < hi
+
+
+def test_escape_and_two_photon_fractions_at_1100():
+    """Sec. III.B: without bulk flows about 5e-3 of the Ly-alpha photons are lost
+    by redshifting and about 1.5e-2 to two-photon decay at z ~ 1100.  The
+    Sobolev chain of the Monte Carlo's branching (an absorbed photon's atom is
+    photo-ionised, decays by two photons or re-emits with weights
+    beta : Lambda : 3 A; each emission escapes with P = R_alpha / (3 A)) on the
+    homogeneous full-mixing history gives both."""
+    from paper_2312_11448_gb300.inputs import z_schedule
+    cp = O.default_cosmo()
+    zs = z_schedule(1700.0, 1100.0, 120)
+    d = np.ones(1)
+    x = O.saha_xe(cp, zs[0], d)
+    T = np.full(1, O.background(cp, zs[0])["Tg"])
+    for s in range(len(zs) - 1):
+        x, T, _, _, _ = O.rec_step(cp, 1, zs[s], zs[s + 1], d, x, T, mixing="full", n_sub=4)
+    S = O.mc_setup(cp, O.mc_params(1100.0))
+    n1s = S["nH"] * (1 - x[0])
+    R = O.rates(cp, 1100.0, T[0])["K_R"] / n1s
+    A = O.A_2P1S
+    Pe = R / (3 * A)
+    pa = 1 - S["p_ion"] - S["p_2g"]
+    den = 1 - (1 - Pe) * pa
+    fz, f2 = Pe / den, (1 - Pe) * S["p_2g"] / den
+    lo, hi = PV["f_z_at_1100"]["band"]
+    assert lo < fz < hi
+    lo, hi = PV["f_2gamma_at_1100"]["band"]
+    assert lo < f2 < hi
 
 
 # ---- redistribution (Eq. inout) ------------------------------------------------
