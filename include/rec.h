@@ -188,6 +188,21 @@ rec_status rec_step(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_
  * Errors: REC_EINVAL, REC_ESTATE, REC_ECUDA. */
 rec_status rec_graph_step(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
 
+/* Second-order variant of rec_step: each of the n_sub substeps is one TR-BDF2
+ * step (Bank et al. 1985) of the same per-cell system (Eq. dotne-mix per
+ * hydrogen atom, Eq. Tb-evolution, drag of Eq. alpha-def).  A trapezoidal
+ * stage to t + gamma h (gamma = 2 - sqrt 2) is followed by a BDF2 stage to
+ * t + h. Each stage end is fully implicit in x_e, T_b, lambda and the Peebles factor;
+ * an outer fixed point over T_b, alpha(T_b) and C converges to 1e-14 relative.
+ * Coefficients are taken at their own times, and the drag uses the trapezoidal
+ * exponent.  Global error falls as the square of the step (backward Euler: linearly).  Same
+ * outputs as rec_step: state, emission weights, tallies zeroed, statistics (flags bit 0: a stage did
+ * not converge within its launches or had no positive root).  Single-box
+ * context, FP64 form, tally or full mixing.  Scratch: 7 doubles per cell,
+ * allocated on first use.
+ * Errors: REC_EINVAL, REC_ESTATE (no state yet), REC_ENOMEM, REC_ECUDA. */
+rec_status rec_step_trbdf2(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
+
 /* Current transport tuning of a context (defaults after rec_init). */
 rec_status rec_get_tuning(const rec_ctx* ctx, rec_tuning* out);
 

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librec.so")
-SOURCES = ["rec_capi.cu", "rec_cosmo.cu", "rec_step.cu", "rec_transport.cu", "rec_adjoint.cu", "rec_scatter.cu"]
+SOURCES = ["rec_capi.cu", "rec_cosmo.cu", "rec_step.cu", "rec_transport.cu", "rec_adjoint.cu", "rec_scatter.cu",
+           "rec_trbdf2.cu"]
 # The scattering Monte Carlo rounds every operation as written (no contraction
 # into fused multiply-adds), like the oracle it is compared with.
 FILE_FLAGS = {"rec_scatter.cu": ["--fmad=false"]}

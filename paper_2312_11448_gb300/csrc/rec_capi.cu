@@ -590,11 +590,27 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->cpre);
   cudaFree(c->div);
   cudaFree(c->mc_scratch);
+  cudaFree(c->trb_scratch);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   cudaFree(c->bx);
   cudaFree(c->bstep);
   cudaFree(c->gsc);
   delete c;
+}
+
+rec_status rec_step_trbdf2(rec_ctx* c, int32_t step, double z_from, double z_to, rec_stats* st) {
+  (void)step;
+  if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");
+  if (c->n_boxes != 1) return fail(c, REC_EINVAL, "the TR-BDF2 step needs a single-box context");
+  if (c->params.precision != REC_PREC_FP64) return fail(c, REC_EINVAL, "the TR-BDF2 step needs the FP64 form");
+  if (c->params.mixing != REC_MIX_TALLY && c->params.mixing != REC_MIX_FULL)
+    return fail(c, REC_EINVAL, "the TR-BDF2 step covers tally and full mixing");
+  if (!(z_from > z_to) || !is_finite(z_from) || !(z_to > 0.0)) return fail(c, REC_EINVAL, "need z_from > z_to > 0");
+  if (!c->emis_ready) return fail(c, REC_ESTATE, "rec_state_init or rec_refresh first");
+  cudaError_t e = rec::launch_rec_step_trbdf2(c, z_from, z_to, st);
+  if (e == cudaErrorMemoryAllocation) return fail(c, REC_ENOMEM, "TR-BDF2 scratch");
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_step_trbdf2");
+  return REC_OK;
 }
 
 rec_status lya_scatter_mc(rec_ctx* c, const lya_mc_params* mp, const uint32_t* dev_prefix,

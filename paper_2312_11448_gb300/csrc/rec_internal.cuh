@@ -174,6 +174,9 @@ struct rec_ctx {
   void* mc_scratch = nullptr;
   size_t mc_bytes = 0;
   double mc_a = -1.0;            // Voigt parameter of the nodes held in mc_scratch
+  // second-order step (rec_step_trbdf2): stage arrays and scalars
+  void* trb_scratch = nullptr;
+  size_t trb_bytes = 0;
 };
 
 namespace rec {
@@ -254,6 +257,9 @@ bool scatter_setup(const Cosmo& c, const rec_params& p, int n, const lya_mc_para
 void scatter_voigt_host(double a, int64_t m, const double* y, double* H);
 cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp, const uint32_t* prefix,
                            lya_mc_photon* out, lya_mc_stats* st);
+
+// rec_trbdf2.cu: second-order (TR-BDF2) step, FP64 form, tally and full mixing
+cudaError_t launch_rec_step_trbdf2(rec_ctx* c, double z_from, double z_to, rec_stats* st);
 
 // rec_adjoint.cu
 cudaError_t launch_rec_step_adjoint(rec_ctx* c, double z_from, double z_to, const double* x_in, const double* T_in,

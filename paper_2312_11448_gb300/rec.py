@@ -100,6 +100,7 @@ def lib():
         L.rec_objective.argtypes = [P(Params), P(d), P(d), i32, i32, d, P(d), P(d)]
         L.rec_timing.argtypes = [vp, i32]
         L.rec_kernel_times.argtypes = [vp, P(d), P(C.c_int64)]
+        L.rec_step_trbdf2.argtypes = [vp, i32, d, d, vp]
         L.lya_scatter_mc.argtypes = [vp, P(McParams), vp, vp, vp]
         L.lya_voigt.argtypes = [d, C.c_int64, P(d), P(d)]
         L.rec_free.argtypes = [vp]
@@ -108,7 +109,7 @@ def lib():
         L.rec_last_error.restype = C.c_char_p
         for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc", "rec_graph_step", "rec_get_tuning", "rec_set_tuning",
                   "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times",
-                  "lya_scatter_mc", "lya_voigt"):
+                  "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -376,6 +377,10 @@ class Box:
     def graph_step(self, step, z_from, z_to, slot=0):
         """transport(step, z_from) + step(step, z_from, z_to) as one CUDA graph launch."""
         self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_graph_step")
+
+    def step_trbdf2(self, step, z_from, z_to, slot=0):
+        """rec_step_trbdf2: the second-order (TR-BDF2) step (FP64 form, tally or full mixing)."""
+        self._check(lib().rec_step_trbdf2(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_step_trbdf2")
 
     def step_noalloc(self, z_from, z_to, slot=0):
         """rec_step_noalloc on this machine's fields and parameters (the context is not used)."""
