@@ -351,7 +351,7 @@ cudaError_t launch_rec_step_trbdf2(rec_ctx* c, double z_from, double z_to, rec_s
   const double ya = std::log1p(z_from), yb = std::log1p(z_to);
   const double gam = 2.0 - std::sqrt(2.0);
   const double c1 = 1.0 / (gam * (2.0 - gam)), c0 = (1.0 - gam) * (1.0 - gam) / (gam * (2.0 - gam));
-  GroupTimer t(c, kTStep, ns * (5 + 2 * (kOuterMax * (kNewtonMax + 2) + 1)));
+  GroupTimer t(c, kTStep, ns * (4 + 2 * (kOuterMax * (kNewtonMax + 2) + 1)));
   for (int sidx = 0; sidx < ns; ++sidx) {
     const double za = (sidx == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)sidx / ns);
     const double zb = (sidx == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(sidx + 1) / ns);
