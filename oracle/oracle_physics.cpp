@@ -420,8 +420,13 @@ void rates_at(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta, c
 // with x_old -> bx for a given G, and lambda solves its Newton equation as in the
 // backward-Euler substep.  The outer iteration repeats T, alpha(T), C(x) and the
 // lambda solve until x and T no longer change.  x, T hold the initial guess and
-// receive the result.  Returns the Newton iterations, or -1 where a stage has no
-// positive root (the step is too long for the explicit part of the stage).
+// receive the result.
+// The quadratic of cell i has a positive root while c_i = bx_i + h w_i G > 0.  A
+// stiff cell can have bx_i < 0 (its explicit part overshoots), so lambda is kept
+// above lambda_min = max_i (-bx_i / (h w_i) - C beta e_alpha) / (1 - C): Newton
+// iterates that fall below it are pulled back halfway.  Returns the Newton
+// iterations, or -1 if the converged lambda leaves a cell without a positive
+// root (the step is too long for the stage).
 int stage_solve(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta, const double* w, double h,
                 const double* bx, const double* bT, double* x, double* T, double* lam_out, double* C_out) {
   std::vector<double> Tn(n3), al(n3), nn(n3), A(n3), sv(n3), xn(n3);
@@ -437,15 +442,20 @@ int stage_solve(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta,
       nn[i] = k.nH * delta[i];
       A[i] = h * al[i] * nn[i];
       sv[i] = h * w[i];
-      if (!(bx[i] + sv[i] * C * k.beta * k.ea > 0.0)) return -1;
     }
     const double CBe = C * k.beta * k.ea, omC = 1.0 - C;
+    double lam_min = -1e300;
+    for (int64_t i = 0; i < n3; ++i) {
+      if (sv[i] > 0.0) lam_min = std::max(lam_min, (-bx[i] / sv[i] - CBe) / omC);
+      else if (!(bx[i] > 0.0)) return -1;  // no photo-ionisation term and no positive root
+    }
     double num = 0.0, den = 0.0;
     for (int64_t i = 0; i < n3; ++i) {
       num += al[i] * nn[i] * nn[i] * x[i] * x[i];
       den += nn[i] * (1.0 - x[i]);
     }
     lam = num / den;
+    if (!(lam > lam_min)) lam = lam_min + std::max(std::fabs(lam_min), std::fabs(lam));
     for (int it = 1; it <= 200; ++it) {
       ++iters;
       const double G = omC * lam + CBe;
@@ -460,10 +470,12 @@ int stage_solve(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta,
       const double step = F / Fp;
       double lnew = lam - step;
       if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
-      const bool conv = std::fabs(step) <= 1e-13 * std::fabs(lam);
+      if (!(lnew > lam_min)) lnew = 0.5 * (lam + lam_min);
+      const bool conv = std::fabs(lnew - lam) <= 1e-13 * std::fabs(lam);
       lam = lnew;
       if (conv) break;
     }
+    if (!(lam > lam_min)) return -1;
     const double G = omC * lam + CBe;
     double dmax = 0.0;
     for (int64_t i = 0; i < n3; ++i) {

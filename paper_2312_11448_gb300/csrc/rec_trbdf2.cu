@@ -7,10 +7,13 @@
 // to t + h.  Each stage end is fully implicit in x, T, lambda and the Peebles
 // factor (R_alpha^mix from the stage-end <n_1s>): T is linear given x; x is the
 // positive root of the backward-Euler quadratic with the stage's explicit part
-// in place of x_old; lambda solves its Newton equation; an outer fixed point
-// repeats T, alpha(T), C(x) and the lambda solve until x and T stop changing
-// (relative change below 1e-14).  Every coefficient is taken at its own time;
-// drag uses the trapezoidal exponent.  FP64 form, tally and full mixing.
+// in place of x_old; lambda and the neutral sum S_1s (which sets C) solve their
+// two equations by a 2x2 Newton iteration; an outer iteration repeats T and
+// alpha(T) until x and T stop changing (relative change below 1e-12; the parity target is 1e-9).  Every
+// coefficient is taken at its own time; drag uses the trapezoidal exponent.
+// FP64 form, tally and full mixing.  (The oracle reaches the same stage end by
+// a fixed point over T, alpha and C around a Newton iteration on lambda alone;
+// the 2x2 iteration converges in a few passes where that fixed point is slow.)
 //
 // Launch organisation: the outer and Newton iterations are launched a fixed
 // number of times per stage; once converged (device flags) the remaining
@@ -26,13 +29,14 @@ namespace rec {
 namespace {
 
 constexpr int NT = kPassThreads;
-constexpr int kOuterMax = 16;   // outer (T, alpha, C) iterations launched per stage
-constexpr int kNewtonMax = 10;  // Newton evaluations launched per outer iteration
+constexpr int kOuterMax = 8;    // outer (T, alpha) iterations launched per stage
+constexpr int kNewtonMax = 16;  // 2x2 Newton evaluations launched per outer iteration
 
 struct TrbScal {
-  double lam, C, CBe, omC;   // current stage iterate
+  double lam, S;             // current iterate: lambda and the neutral sum S_1s
+  double M;                  // max_i (-bx_i / (h w_i)): lambda_min = (M - C beta e_alpha) / (1 - C)
   double Ga, Sa;             // G and S_1s of the substep-start state
-  double dmax;               // unused slot (alignment)
+  double C;                  // Peebles factor at the last S
   int32_t newton_conv, outer_done, bad, unconverged;
   int32_t passes;            // Newton evaluations of the current substep
   uint32_t counter;          // last-block-done ticket
@@ -56,6 +60,20 @@ struct TrbArgs {
   int tally_mode;
 };
 
+// Block maximum of values that may be negative (block_max starts from 0).
+__device__ __forceinline__ double block_max_signed(double v) {
+  __shared__ double sm[NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  __syncthreads();
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < NT / 32; ++w) v = fmax(v, sm[w]);
+  return v;
+}
+
 __device__ __forceinline__ double alpha_e(const StepCoef& k, double T) {
   const double lt = log(T * 1.0e-4);
   return k.fa * exp(k.pb * lt) / (1.0 + k.pc * exp(k.pd * lt));
@@ -64,6 +82,18 @@ __device__ __forceinline__ double alpha_e(const StepCoef& k, double T) {
 __device__ __forceinline__ double peebles(const StepCoef& k, double S, double n3) {
   const double Rmix = k.KR / (k.nH * S / n3);
   return (k.L2g + Rmix) / (k.beta + k.L2g + Rmix);
+}
+
+// dC/dS_1s: R = K_R n3 / (nH S), dR/dS = -R/S, dC/dR = beta / (beta + Lambda + R)^2.
+__device__ __forceinline__ double peebles_dS(const StepCoef& k, double S, double n3) {
+  const double Rmix = k.KR / (k.nH * S / n3);
+  const double den = k.beta + k.L2g + Rmix;
+  return -k.beta * Rmix / (S * den * den);
+}
+
+// Lower bound on lambda for the current S: every cell keeps c_i = bx_i + h w_i G > 0.
+__device__ __forceinline__ double lam_min(const StepCoef& k, const TrbScal* s, double C) {
+  return (s->M - C * k.beta * k.ea) / (1.0 - C);
 }
 
 // Positive root of A x^2 + (1 + sG) x - (b + sG) = 0 and d x / d G.
@@ -137,12 +167,13 @@ __global__ void __launch_bounds__(NT) k_trb_explicit2(TrbArgs a, double c1, doub
   if (blockIdx.x == 0 && threadIdx.x == 0) a.s->outer_done = 0;
 }
 
-// Outer iteration, first pass: T from the current x iterate (linear), alpha(T),
-// and S_1s of the iterate for the Peebles factor; on the first outer pass of a
-// stage also the lambda start <alpha n_e^2>/<n_1s> of the iterate.
+// Outer iteration, first pass: T from the current x iterate (linear) and
+// alpha(T); the bound M = max_i (-bx_i / (h w_i)); on the first outer pass of a
+// stage also the starts lambda = <alpha n_e^2>/<n_1s> and S_1s of the iterate.
 __global__ void __launch_bounds__(NT) k_trb_prep(TrbArgs a, StepCoef k, double h, int first) {
   if (a.s->outer_done) return;
   double v[3] = {0.0, 0.0, 0.0};
+  double m = -1e300;
   for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += (int64_t)gridDim.x * NT) {
     const double d = a.delta[i], x = a.xg[i], n = k.nH * d;
     const double g = k.kc * x / (1.0 + k.fHe + x);
@@ -151,70 +182,107 @@ __global__ void __launch_bounds__(NT) k_trb_prep(TrbArgs a, StepCoef k, double h
     const double al = alpha_e(k, Tn);
     a.Tn[i] = Tn;
     a.al[i] = al;
+    const double sw = h * a.w[i];
+    if (sw > 0.0) m = fmax(m, -a.bx[i] / sw);
+    else if (!(a.bx[i] > 0.0)) m = 1e300;  // no photo-ionisation term and no positive root
     v[0] += d * (1.0 - x);
     v[1] += al * n * n * x * x;
     v[2] += n * (1.0 - x);
   }
   block_sum<3, NT>(v);
-  if (threadIdx.x == 0)
+  m = block_max_signed(m);
+  if (threadIdx.x == 0) {
     for (int j = 0; j < 3; ++j) a.part[(size_t)blockIdx.x * kMaxSums + j] = v[j];
+    a.part[(size_t)blockIdx.x * kMaxSums + 3] = m;
+  }
   if (last_block_done(&a.s->counter)) {
     double S[3];
     combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
+    double M = -1e300;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) M = fmax(M, __ldcg(a.part + (size_t)b * kMaxSums + 3));
+    M = block_max_signed(M);
     if (threadIdx.x == 0) {
-      const double C = peebles(k, S[0], (double)a.n3);
-      a.s->C = C;
-      a.s->CBe = C * k.beta * k.ea;
-      a.s->omC = 1.0 - C;
-      if (first) a.s->lam = S[1] / S[2];
-      a.s->newton_conv = 0;
-      a.s->counter = 0;
+      TrbScal* s = a.s;
+      s->M = M;
+      if (first) {
+        s->lam = S[1] / S[2];
+        s->S = S[0];
+      }
+      const double C = peebles(k, s->S, (double)a.n3);
+      const double lmin = lam_min(k, s, C);
+      if (!(s->lam > lmin)) s->lam = lmin + fmax(fabs(lmin), fabs(s->lam));
+      s->newton_conv = 0;
+      s->counter = 0;
     }
   }
 }
 
-// One Newton evaluation of F(lambda) = sum alpha n^2 x^2 - lambda sum n (1 - x)
-// over the roots x(G), G = (1 - C) lambda + C beta e_alpha.
+// One 2x2 Newton evaluation for (lambda, S_1s):
+//   F1 = sum alpha n^2 x^2 - lambda sum n (1 - x),   F2 = sum delta (1 - x) - S_1s,
+// x_i the roots at G = (1 - C(S)) lambda + C(S) beta e_alpha.
 __global__ void __launch_bounds__(NT) k_trb_newton(TrbArgs a, StepCoef k, double h) {
   if (a.s->outer_done || a.s->newton_conv) return;
-  const double lam = a.s->lam, omC = a.s->omC, G = omC * lam + a.s->CBe;
-  double v[3] = {0.0, 0.0, 0.0};
+  const double n3 = (double)a.n3;
+  const double lam = a.s->lam, S = a.s->S;
+  const double C = peebles(k, S, n3), omC = 1.0 - C, CBe = C * k.beta * k.ea;
+  const double G = omC * lam + CBe;
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += (int64_t)gridDim.x * NT) {
-    const double n = k.nH * a.delta[i], al = a.al[i];
-    const double s = h * a.w[i];
+    const double d = a.delta[i], n = k.nH * d, al = a.al[i];
+    const double sw = h * a.w[i];
     const double b = a.bx[i];
-    if (!(b + s * a.s->CBe > 0.0)) v[2] += 1.0;  // no positive root: step too long
+    if (!(b + sw * G > 0.0)) v[5] += 1.0;  // no positive root at this G
     double dxdG;
-    const double xr = root(h * al * n, s, G, b, &dxdG);
+    const double xr = root(h * al * n, sw, G, b, &dxdG);
     const double an2 = al * n * n;
     v[0] += an2 * xr * xr - lam * n * (1.0 - xr);
-    v[1] += (2.0 * an2 * xr + lam * n) * dxdG * omC - n * (1.0 - xr);
+    v[1] += d * (1.0 - xr);
+    v[2] += (2.0 * an2 * xr + lam * n) * dxdG;
+    v[3] += n * (1.0 - xr);
+    v[4] += d * dxdG;
   }
-  block_sum<3, NT>(v);
+  block_sum<6, NT>(v);
   if (threadIdx.x == 0)
-    for (int j = 0; j < 3; ++j) a.part[(size_t)blockIdx.x * kMaxSums + j] = v[j];
+    for (int j = 0; j < 6; ++j) a.part[(size_t)blockIdx.x * kMaxSums + j] = v[j];
   if (last_block_done(&a.s->counter)) {
-    double S[3];
-    combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
+    double R[6];
+    combine_partials<6, NT>(a.part, gridDim.x, kMaxSums, R);
     if (threadIdx.x == 0) {
-      const double F = S[0], Fp = S[1];
-      const double step = F / Fp;
-      double lnew = lam - step;
-      if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
-      if (fabs(step) <= 1e-13 * fabs(lam)) a.s->newton_conv = 1;
-      if (S[2] > 0.0) a.s->bad = 1;
-      a.s->lam = lnew;
-      a.s->passes += 1;
-      a.s->counter = 0;
+      TrbScal* s = a.s;
+      const double F1 = R[0], F2 = R[1] - S, P = R[2], Q = R[3], Dd = R[4];
+      const double Gs = (k.beta * k.ea - lam) * peebles_dS(k, S, n3);
+      const double J11 = P * omC - Q, J12 = P * Gs, J21 = -Dd * omC, J22 = -Dd * Gs - 1.0;
+      const double det = J11 * J22 - J12 * J21;
+      double ln = lam, Sn = S;
+      if (det != 0.0 && isfinite(det)) {
+        ln = lam - (F1 * J22 - J12 * F2) / det;
+        Sn = S - (J11 * F2 - J21 * F1) / det;
+      }
+      // trust region: S within a factor 2 and lambda within a factor 4 per pass
+      // (from a start far from the stage end the joint step can overshoot)
+      if (!(Sn > 0.5 * S)) Sn = 0.5 * S;
+      if (!(Sn < 2.0 * S)) Sn = 2.0 * S;
+      if (!(ln < 4.0 * lam)) ln = 4.0 * lam;
+      if (!(ln > 0.25 * lam)) ln = 0.25 * lam;
+      const double lmin = lam_min(k, s, peebles(k, Sn, n3));
+      if (!(ln > lmin)) ln = (lam > lmin) ? 0.5 * (lam + lmin) : lmin + fmax(fabs(lmin), fabs(lam));
+      if (fabs(ln - lam) <= 1e-13 * fabs(lam) && fabs(Sn - S) <= 1e-13 * fabs(S)) s->newton_conv = 1;
+      if (R[5] > 0.0) s->bad = 1; else s->bad = 0;
+      s->lam = ln;
+      s->S = Sn;
+      s->passes += 1;
+      s->counter = 0;
     }
   }
 }
 
-// Outer iteration, last pass: the roots at the converged lambda become the
-// iterate, with T; the stage is done when neither changed by more than 1e-14.
+// Outer iteration, last pass: the roots at the converged (lambda, S_1s) become
+// the iterate, with T; the stage is done when neither changed by more than 1e-12 (rounding keeps
+// near-equilibrium cells changing at a few 1e-14).
 __global__ void __launch_bounds__(NT) k_trb_update(TrbArgs a, StepCoef k, double h) {
   if (a.s->outer_done) return;
-  const double G = a.s->omC * a.s->lam + a.s->CBe;
+  const double C = peebles(k, a.s->S, (double)a.n3);
+  const double G = (1.0 - C) * a.s->lam + C * k.beta * k.ea;
   double m = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += (int64_t)gridDim.x * NT) {
     const double n = k.nH * a.delta[i];
@@ -230,7 +298,8 @@ __global__ void __launch_bounds__(NT) k_trb_update(TrbArgs a, StepCoef k, double
   if (last_block_done(&a.s->counter)) {
     const double M = combine_max<NT>(a.part, gridDim.x, kMaxSums, 0);
     if (threadIdx.x == 0) {
-      if (M <= 1e-14) a.s->outer_done = 1;
+      if (M <= 1e-12) a.s->outer_done = 1;
+      a.s->C = C;
       a.s->counter = 0;
     }
   }
