@@ -199,9 +199,11 @@ rec_status rec_graph_step(rec_ctx* ctx, int32_t step, double z_from, double z_to
  * outputs as rec_step: state, emission weights, tallies zeroed, statistics (flags bit 0: a stage did
  * not converge within its launches or had no positive root).  Single-box
  * context, FP64 form, tally or full mixing.  Scratch: 7 doubles per cell,
- * allocated on first use.  Meant for states near ionisation equilibrium: far
- * above it (x_e well over its Saha value at z >~ 1600) with steps longer than
- * the equilibration time, the stage equations can have more than one solution.
+ * allocated on first use.  Meant for states near the quasi-equilibrium a run
+ * reaches: with steps longer than the cells' relaxation time, a start far from
+ * it can make the trapezoidal stage infeasible (it overshoots to about
+ * 2 x_eq - x_n; flags bit 0 is set) or, far above ionisation equilibrium,
+ * give stage equations with more than one solution.
  * Errors: REC_EINVAL, REC_ESTATE (no state yet), REC_ENOMEM, REC_ECUDA. */
 rec_status rec_step_trbdf2(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
 

@@ -455,7 +455,8 @@ int stage_solve(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta,
       den += nn[i] * (1.0 - x[i]);
     }
     lam = num / den;
-    if (!(lam > lam_min)) lam = lam_min + std::max(std::fabs(lam_min), std::fabs(lam));
+    const double lam_lo = std::max(lam_min, 0.0);  // lambda > 0 as well (G > 0)
+    if (!(lam > lam_lo)) lam = lam_lo > 0.0 ? 2.0 * lam_lo : lam;
     for (int it = 1; it <= 200; ++it) {
       ++iters;
       const double G = omC * lam + CBe;
@@ -470,12 +471,12 @@ int stage_solve(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta,
       const double step = F / Fp;
       double lnew = lam - step;
       if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
-      if (!(lnew > lam_min)) lnew = 0.5 * (lam + lam_min);
+      if (!(lnew > lam_lo)) lnew = 0.5 * (lam + lam_lo);
       const bool conv = std::fabs(lnew - lam) <= 1e-13 * std::fabs(lam);
       lam = lnew;
       if (conv) break;
     }
-    if (!(lam > lam_min)) return -1;
+    if (!(lam > lam_lo)) return -1;
     const double G = omC * lam + CBe;
     double dmax = 0.0;
     for (int64_t i = 0; i < n3; ++i) {
@@ -484,6 +485,7 @@ int stage_solve(const Cosmo& cm, const Coef& k, int64_t n3, const double* delta,
       dmax = std::max(dmax, std::fabs(Tn[i] - T[i]) / Tn[i]);
     }
     for (int64_t i = 0; i < n3; ++i) { x[i] = xn[i]; T[i] = Tn[i]; }
+    if (!(dmax < 1e300)) return -1;  // not finite
     if (dmax <= 1e-14) break;
   }
   *lam_out = lam;
