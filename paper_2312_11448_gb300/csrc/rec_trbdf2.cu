@@ -284,20 +284,29 @@ __global__ void __launch_bounds__(NT) k_trb_update(TrbArgs a, StepCoef k, double
   const double C = peebles(k, a.s->S, (double)a.n3);
   const double G = (1.0 - C) * a.s->lam + C * k.beta * k.ea;
   double m = 0.0;
+  double nbad[1] = {0.0};
   for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += (int64_t)gridDim.x * NT) {
     const double n = k.nH * a.delta[i];
     const double xn = root(h * a.al[i] * n, h * a.w[i], G, a.bx[i], nullptr);
     const double Tn = a.Tn[i];
+    if (!(xn > 0.0 && xn < 1e300) || !(Tn > 0.0 && Tn < 1e300)) nbad[0] += 1.0;  // fmax would hide a NaN
     m = fmax(m, fabs(xn - a.xg[i]) / xn);
     m = fmax(m, fabs(Tn - a.Tg[i]) / Tn);
     a.xg[i] = xn;
     a.Tg[i] = Tn;
   }
   m = block_max<NT>(m);
-  if (threadIdx.x == 0) a.part[(size_t)blockIdx.x * kMaxSums] = m;
+  block_sum<1, NT>(nbad);
+  if (threadIdx.x == 0) {
+    a.part[(size_t)blockIdx.x * kMaxSums] = m;
+    a.part[(size_t)blockIdx.x * kMaxSums + 1] = nbad[0];
+  }
   if (last_block_done(&a.s->counter)) {
     const double M = combine_max<NT>(a.part, gridDim.x, kMaxSums, 0);
+    double B[1];
+    combine_partials<1, NT>(a.part + 1, gridDim.x, kMaxSums, B);
     if (threadIdx.x == 0) {
+      if (B[0] > 0.0) a.s->unconverged = 1;  // non-finite or non-positive stage end
       if (M <= 1e-12) a.s->outer_done = 1;
       a.s->C = C;
       a.s->counter = 0;
