@@ -367,6 +367,16 @@ typedef struct {
 rec_status lya_scatter_mc(rec_ctx* ctx, const lya_mc_params* mp, const uint32_t* dev_prefix,
                           lya_mc_photon* dev_photons, lya_mc_stats* dev_stats);
 
+/* Scalars of a Monte-Carlo snapshot as lya_scatter_mc uses them (host
+ * computation, no GPU needed): out[0] = a, out[1] = v_th / c,
+ * out[2] = sig0 (m^2; <sigma> = sig0 H(a, y)), out[3] = frequency drift per
+ * physical metre zeta H / (c v_th), out[4] = p_ion and out[5] = p_2gamma
+ * (fates per scattering), out[6] = beta_e, out[7] = Lambda_2gamma,
+ * out[8] = zeta H, out[9] = nbar_H (1/m^3), out[10] = T_gamma,
+ * out[11] = comoving cells per physical metre of an n^3 box.
+ * Errors: REC_EINVAL. */
+rec_status lya_mc_scalars(const rec_params* params, const lya_mc_params* mp, int32_t n, double* out);
+
 /* The Voigt function H(a, y) as lya_scatter_mc evaluates it (cubic Hermite
  * interpolation of nodes spaced 1/128 for |y| < 10, the asymptotic series of
  * the Faddeeva function beyond), at m host points y; host computation.

@@ -638,6 +638,21 @@ rec_status lya_scatter_mc(rec_ctx* c, const lya_mc_params* mp, const uint32_t* d
   return REC_OK;
 }
 
+rec_status lya_mc_scalars(const rec_params* p, const lya_mc_params* mp, int32_t n, double* out) {
+  std::string why;
+  rec_status st = check_params(p, &why);
+  if (st != REC_OK) return fail(nullptr, st, why);
+  if (!mp || !out || n < 1 || !(mp->z > 0.0) || !(mp->eps > 0.0 && mp->eps <= 1.0) || !(mp->zeta > 0.0) ||
+      !(mp->A_alpha > 0.0))
+    return fail(nullptr, REC_EINVAL, "lya_mc_scalars: bad arguments");
+  rec::McSetup S;
+  if (!rec::scatter_setup(rec::make_cosmo(*p), *p, n, mp, &S))
+    return fail(nullptr, REC_EINVAL, "Monte-Carlo scalars are not finite at this redshift");
+  out[0] = S.a; out[1] = S.vth; out[2] = S.sig0; out[3] = S.dxdl; out[4] = S.p_ion; out[5] = S.p_2g;
+  out[6] = S.beta; out[7] = S.Lam; out[8] = S.Heff; out[9] = S.nH; out[10] = S.Tg; out[11] = S.cpm;
+  return REC_OK;
+}
+
 rec_status lya_voigt(double a, int64_t m, const double* y, double* H) {
   if (!(a > 0.0) || !is_finite(a) || m < 0 || (m > 0 && (!y || !H)))
     return fail(nullptr, REC_EINVAL, "lya_voigt: a must be positive, y and H non-NULL");

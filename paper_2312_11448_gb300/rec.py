@@ -103,13 +103,14 @@ def lib():
         L.rec_step_trbdf2.argtypes = [vp, i32, d, d, vp]
         L.lya_scatter_mc.argtypes = [vp, P(McParams), vp, vp, vp]
         L.lya_voigt.argtypes = [d, C.c_int64, P(d), P(d)]
+        L.lya_mc_scalars.argtypes = [P(Params), P(McParams), i32, P(d)]
         L.rec_free.argtypes = [vp]
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
         L.rec_last_error.restype = C.c_char_p
         for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc", "rec_graph_step", "rec_get_tuning", "rec_set_tuning",
                   "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times",
-                  "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2"):
+                  "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2", "lya_mc_scalars"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -165,6 +166,21 @@ def voigt(a: float, y) -> np.ndarray:
 
 
 MC_ARITH = {"fp64": 0, "mixed": 1}
+
+
+def mc_scalars(z, n=1, **kw) -> dict:
+    """Monte-Carlo snapshot scalars as lya_scatter_mc uses them (host only).
+    kw: lya_mc_params fields (zeta, lambda2g, eps, A_alpha, ...) and
+    cosmology overrides of make_params."""
+    mkeys = {"eps", "x_lost", "zeta", "lambda2g", "A_alpha", "max_steps", "step", "pending", "arith"}
+    mp = mc_params(z, 1, **{k: v for k, v in kw.items() if k in mkeys})
+    p, _q = make_params(**{k: v for k, v in kw.items() if k not in mkeys})
+    out = (C.c_double * 12)()
+    rc = lib().lya_mc_scalars(C.byref(p), C.byref(mp), int(n), out)
+    if rc != REC_OK:
+        raise RecError(lib().rec_last_error(None).decode())
+    keys = ("a", "vth", "sig0", "dxdl", "p_ion", "p_2g", "beta", "Lambda", "H", "nH", "Tg", "cells_per_m")
+    return dict(zip(keys, list(out)))
 
 
 def mc_params(z, n_photons, eps=0.1, x_lost=1.0e4, zeta=1.0, lambda2g=-1.0, A_alpha=A_2P1S, max_steps=10 ** 9,

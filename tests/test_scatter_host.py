@@ -31,3 +31,15 @@ def test_library_voigt_rejects_bad_arguments():
         rec.voigt(0.0, [1.0])
     with pytest.raises(rec.RecError):
         rec.voigt(-1e-3, [1.0])
+
+
+@pytest.mark.parametrize("z,zeta,lam,n", [(1100.0, 1.0, -1.0, 256), (1700.0, 3e4, 0.0, 4), (1400.0, 10.0, 5e3, 33)])
+def test_library_mc_scalars_match_oracle(z, zeta, lam, n):
+    """The snapshot scalars the GPU Monte Carlo uses equal the oracle's (the two
+    compute them independently from the same definitions)."""
+    import oracle as O
+    from paper_2312_11448_gb300 import rec
+    lib = rec.mc_scalars(z, n=n, zeta=zeta, lambda2g=lam)
+    orc = O.mc_setup(O.default_cosmo(), O.mc_params(z, zeta=zeta, lambda2g=lam), n)
+    for key, v in orc.items():
+        assert lib[key] == pytest.approx(v, rel=1e-13), key
