@@ -377,11 +377,27 @@ rec_status lya_scatter_mc(rec_ctx* ctx, const lya_mc_params* mp, const uint32_t*
  * Errors: REC_EINVAL. */
 rec_status lya_mc_scalars(const rec_params* params, const lya_mc_params* mp, int32_t n, double* out);
 
+/* The redistribution of the LYA_MC_MIXED form (Eq. inout, isotropic; the
+ * same source compiled for the host): m independent scatterings of a photon at
+ * gas-frame offset y travelling along kin (host double[3], not normalised),
+ * with the random streams of photon (i, i >> 32) of seed.  Outputs (host, may be NULL):
+ * ppar[i] = scattering atom's parallel velocity, dy[i] = y_out - y,
+ * kout[3i..3i+2] = outgoing direction; caps (may be NULL) = draws that hit the
+ * rejection cap.  Host computation, for checking the kernel's sampler on a CPU.
+ * Errors: REC_EINVAL. */
+rec_status lya_mc_redistribution_host(double a, double y, const double* kin, uint64_t seed, int64_t m,
+                                      double* ppar, double* dy, double* kout, uint64_t* caps);
+
 /* The Voigt function H(a, y) as lya_scatter_mc evaluates it (cubic Hermite
  * interpolation of nodes spaced 1/128 for |y| < 10, the asymptotic series of
  * the Faddeeva function beyond), at m host points y; host computation.
  * Errors: REC_EINVAL. */
 rec_status lya_voigt(double a, int64_t m, const double* y, double* H);
+
+/* The same for the LYA_MC_MIXED form: binary32 nodes and interpolation for
+ * |y| < 10, the first-order wing series (a / sqrt(pi)) sum_k (2k+1)!! /
+ * (2^k y^(2k+2)) beyond; host computation.  Errors: REC_EINVAL. */
+rec_status lya_voigt_mixed(double a, int64_t m, const double* y, double* H);
 
 /* Release the context and its scratch (NULL-safe).  Synchronises the stream. */
 void rec_free(rec_ctx* ctx);

@@ -653,10 +653,28 @@ rec_status lya_mc_scalars(const rec_params* p, const lya_mc_params* mp, int32_t 
   return REC_OK;
 }
 
+rec_status lya_mc_redistribution_host(double a, double y, const double* kin, uint64_t seed, int64_t m,
+                                      double* ppar, double* dy, double* kout, uint64_t* caps) {
+  if (!(a > 0.0) || !is_finite(a) || !is_finite(y) || !kin || m < 0)
+    return fail(nullptr, REC_EINVAL, "lya_mc_redistribution_host: bad arguments");
+  const double kn = std::sqrt(kin[0] * kin[0] + kin[1] * kin[1] + kin[2] * kin[2]);
+  if (!(kn > 0.0) || !is_finite(kn)) return fail(nullptr, REC_EINVAL, "lya_mc_redistribution_host: kin is zero");
+  const uint64_t c = rec::scatter_redistribution_mixed_host(a, y, kin, seed, m, ppar, dy, kout);
+  if (caps) *caps = c;
+  return REC_OK;
+}
+
 rec_status lya_voigt(double a, int64_t m, const double* y, double* H) {
   if (!(a > 0.0) || !is_finite(a) || m < 0 || (m > 0 && (!y || !H)))
     return fail(nullptr, REC_EINVAL, "lya_voigt: a must be positive, y and H non-NULL");
   rec::scatter_voigt_host(a, m, y, H);
+  return REC_OK;
+}
+
+rec_status lya_voigt_mixed(double a, int64_t m, const double* y, double* H) {
+  if (!(a > 0.0) || !is_finite(a) || m < 0 || (m > 0 && (!y || !H)))
+    return fail(nullptr, REC_EINVAL, "lya_voigt_mixed: a must be positive, y and H non-NULL");
+  rec::scatter_voigt_mixed_host(a, m, y, H);
   return REC_OK;
 }
 

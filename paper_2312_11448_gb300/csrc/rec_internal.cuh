@@ -255,6 +255,9 @@ struct McSetup {
 };
 bool scatter_setup(const Cosmo& c, const rec_params& p, int n, const lya_mc_params* mp, McSetup* S);
 void scatter_voigt_host(double a, int64_t m, const double* y, double* H);
+void scatter_voigt_mixed_host(double a, int64_t m, const double* y, double* H);
+uint64_t scatter_redistribution_mixed_host(double a, double y, const double* kin, uint64_t seed, int64_t m,
+                                           double* ppar, double* dy, double* kout);
 cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp, const uint32_t* prefix,
                            lya_mc_photon* out, lya_mc_stats* st);
 

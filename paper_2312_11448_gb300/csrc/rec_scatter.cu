@@ -484,17 +484,35 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float b) {
   lo = t - (hi - s);
 }
 
+// The mixed form's helpers below are host and device code: the host build
+// runs the same redistribution (lya_mc_redistribution_host) for CPU checks.
+__host__ __device__ __forceinline__ void philox_hd(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                   uint32_t k1, uint32_t out[4]) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
 struct McRngF {
   uint32_t cell, j, blk, tag, k0, k1, w0, w1, w2, w3;
   int nw;
-  __device__ __forceinline__ void init(uint32_t c, uint32_t jj, uint32_t key0, uint32_t key1, uint32_t box) {
+  __host__ __device__ __forceinline__ void init(uint32_t c, uint32_t jj, uint32_t key0, uint32_t key1, uint32_t box) {
     cell = c; j = jj; blk = 0; tag = 0x80000000u | box; k0 = key0; k1 = key1; nw = 0;
     w0 = w1 = w2 = w3 = 0;
   }
-  __device__ __forceinline__ uint32_t word() {
+  __host__ __device__ __forceinline__ uint32_t word() {
     if (nw == 0) {
       uint32_t r[4];
-      philox(cell, j, blk, tag, k0, k1, r);
+      philox_hd(cell, j, blk, tag, k0, k1, r);
       ++blk;
       w0 = r[0]; w1 = r[1]; w2 = r[2]; w3 = r[3];
       nw = 4;
@@ -504,10 +522,11 @@ struct McRngF {
     --nw;
     return v;
   }
-  __device__ __forceinline__ float u01() { return __uint2float_rn((word() >> 8) | 1u) * 0x1p-24f; }
+  // (w >> 8) | 1 has at most 24 bits: the conversion to binary32 is exact
+  __host__ __device__ __forceinline__ float u01() { return (float)((word() >> 8) | 1u) * 0x1p-24f; }
 };
 
-__device__ __forceinline__ void disk_f(McRngF& s, float& v1, float& v2, float& r2) {
+__host__ __device__ __forceinline__ void disk_f(McRngF& s, float& v1, float& v2, float& r2) {
   for (int it = 0; it < 64; ++it) {
     v1 = 2.0f * s.u01() - 1.0f;
     v2 = 2.0f * s.u01() - 1.0f;
@@ -520,7 +539,7 @@ __device__ __forceinline__ void disk_f(McRngF& s, float& v1, float& v2, float& r
 // H(a, t) in binary32: cubic Hermite on the nodes for t < 10; beyond, the
 // first-order-in-a wing series (a / sqrt(pi)) sum_k (2k+1)!! / (2^k t^(2k+2)),
 // five terms (relative error below 1e-7 for t >= 10).
-__device__ __forceinline__ float voigt_f(const float* H, const float* dH, float y, float a) {
+__host__ __device__ __forceinline__ float voigt_f(const float* H, const float* dH, float y, float a) {
   const float t = fabsf(y);
   if (!(t < 10.0f)) {
     const float q = 1.0f / (t * t);
@@ -537,7 +556,7 @@ __device__ __forceinline__ float voigt_f(const float* H, const float* dH, float 
   return h00 * H[k] + h10 * st * dH[k] + h01 * H[k + 1] + h11 * st * dH[k + 1];
 }
 
-__device__ __forceinline__ float cut_u0_f(float t, float a) {
+__host__ __device__ __forceinline__ float cut_u0_f(float t, float a) {
   if (t < 1.2f) return -0.7f;
   if (t >= 10.0f) return sqrtf(logf(t * t / a) + 4.0f);
   if (t < 2.0f) return 1.1f + 0.875f * (t - 1.2f);
@@ -547,7 +566,7 @@ __device__ __forceinline__ float cut_u0_f(float t, float a) {
   return 3.4f + 0.1f * (t - 6.0f);
 }
 
-__device__ float sample_ppar_f(McRngF& s, float y, float a, unsigned long long* caps) {
+__host__ __device__ float sample_ppar_f(McRngF& s, float y, float a, unsigned long long* caps) {
   const float t = fabsf(y);
   const float u0 = cut_u0_f(t, a);
   const float d0 = t - u0;
@@ -575,8 +594,10 @@ __device__ float sample_ppar_f(McRngF& s, float y, float a, unsigned long long* 
   return 0.0f;
 }
 
-__device__ float redistribute_f(McRngF& s, float y, float a, float k[3], unsigned long long* caps) {
+__host__ __device__ float redistribute_f(McRngF& s, float y, float a, float k[3], unsigned long long* caps,
+                                         float* p_out = nullptr) {
   const float p = sample_ppar_f(s, y, a, caps);
+  if (p_out) *p_out = p;
   const float r = sqrtf(-logf(s.u01()));
   const float mu = 2.0f * s.u01() - 1.0f;
   float v1, v2, r2;
@@ -593,7 +614,11 @@ __device__ float redistribute_f(McRngF& s, float y, float a, float k[3], unsigne
   const float nx = mu * k[0] + sm * (cphi * e1x + sphi * e2x);
   const float ny = mu * k[1] + sm * (cphi * e1y + sphi * e2y);
   const float nz = mu * k[2] + sm * (cphi * e1z + sphi * e2z);
+#ifdef __CUDA_ARCH__
   const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+#else
+  const float inv = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+#endif
   k[0] = nx * inv; k[1] = ny * inv; k[2] = nz * inv;
   return y - p * (1.0f - mu) + r * sm * cb;
 }
@@ -817,6 +842,40 @@ bool scatter_setup(const Cosmo& c, const rec_params& p, int n, const lya_mc_para
   S->expm_eps = std::exp(-mp->eps);
   S->kpc_cell = p.L_box_kpc / n;
   return std::isfinite(S->a) && S->a > 0.0 && std::isfinite(S->sig0) && S->Heff > 0.0 && S->nH > 0.0;
+}
+
+// The mixed form's redistribution (Eq. inout) run on the host: m independent
+// scatterings at gas-frame offset y along kin (streams (i, i >> 32) of seed).
+// Returns the number of atom-velocity draws that hit the rejection cap.
+uint64_t scatter_redistribution_mixed_host(double a, double y, const double* kin, uint64_t seed, int64_t m,
+                                           double* ppar, double* dy, double* kout) {
+  unsigned long long caps = 0;
+  const double kn = std::sqrt(kin[0] * kin[0] + kin[1] * kin[1] + kin[2] * kin[2]);
+  for (int64_t i = 0; i < m; ++i) {
+    McRngF s;
+    s.init((uint32_t)i, (uint32_t)(i >> 32), (uint32_t)seed, (uint32_t)(seed >> 32), 0);
+    float k[3] = {(float)(kin[0] / kn), (float)(kin[1] / kn), (float)(kin[2] / kn)};
+    float p = 0.0f;
+    const float yo = redistribute_f(s, (float)y, (float)a, k, &caps, &p);
+    if (ppar) ppar[i] = p;
+    if (dy) dy[i] = (double)yo - (double)(float)y;
+    if (kout) for (int d = 0; d < 3; ++d) kout[3 * i + d] = k[d];
+  }
+  return caps;
+}
+
+// The mixed form's binary32 Voigt evaluation (nodes rounded to binary32, the
+// wing series beyond |y| = 10) on the host.
+void scatter_voigt_mixed_host(double a, int64_t m, const double* y, double* H) {
+  static thread_local double last_a = -1.0;
+  static thread_local float tH[kVoigtNodes], tD[kVoigtNodes];
+  if (a != last_a) {
+    std::vector<double> h(2 * kVoigtNodes);
+    voigt_nodes(a, h.data(), h.data() + kVoigtNodes);
+    for (int i = 0; i < kVoigtNodes; ++i) { tH[i] = (float)h[i]; tD[i] = (float)h[kVoigtNodes + i]; }
+    last_a = a;
+  }
+  for (int64_t i = 0; i < m; ++i) H[i] = voigt_f(tH, tD, (float)y[i], (float)a);
 }
 
 void scatter_voigt_host(double a, int64_t m, const double* y, double* H) {

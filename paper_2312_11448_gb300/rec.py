@@ -103,14 +103,18 @@ def lib():
         L.rec_step_trbdf2.argtypes = [vp, i32, d, d, vp]
         L.lya_scatter_mc.argtypes = [vp, P(McParams), vp, vp, vp]
         L.lya_voigt.argtypes = [d, C.c_int64, P(d), P(d)]
+        L.lya_voigt_mixed.argtypes = [d, C.c_int64, P(d), P(d)]
         L.lya_mc_scalars.argtypes = [P(Params), P(McParams), i32, P(d)]
+        L.lya_mc_redistribution_host.argtypes = [d, d, P(d), C.c_uint64, C.c_int64, P(d), P(d), P(d),
+                                                 P(C.c_uint64)]
         L.rec_free.argtypes = [vp]
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
         L.rec_last_error.restype = C.c_char_p
         for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc", "rec_graph_step", "rec_get_tuning", "rec_set_tuning",
                   "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times",
-                  "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2", "lya_mc_scalars"):
+                  "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2", "lya_mc_scalars",
+                  "lya_mc_redistribution_host", "lya_voigt_mixed"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -154,18 +158,33 @@ def objective(zs, Xe, objective=1, z_star=1100.0, **kw):
     return J.value, dJ
 
 
-def voigt(a: float, y) -> np.ndarray:
-    """H(a, y) as the scattering Monte Carlo evaluates it (host computation)."""
+def voigt(a: float, y, mixed=False) -> np.ndarray:
+    """H(a, y) as the scattering Monte Carlo evaluates it (host computation);
+    mixed=True: the binary32 evaluation of the mixed-arithmetic form."""
     yy = np.ascontiguousarray(y, dtype=np.float64).ravel()
     H = np.empty_like(yy)
     dp = lambda v: v.ctypes.data_as(C.POINTER(C.c_double))
-    rc = lib().lya_voigt(float(a), yy.size, dp(yy), dp(H))
+    fn = lib().lya_voigt_mixed if mixed else lib().lya_voigt
+    rc = fn(float(a), yy.size, dp(yy), dp(H))
     if rc != REC_OK:
         raise RecError(lib().rec_last_error(None).decode())
     return H
 
 
 MC_ARITH = {"fp64": 0, "mixed": 1}
+
+
+def mc_redistribution_mixed(a, y, seed, m, kin=(0.0, 0.0, 1.0)):
+    """The mixed form's redistribution run on the host: (p_par, y_out - y, k_out, caps)."""
+    dp = lambda v: v.ctypes.data_as(C.POINTER(C.c_double))
+    k = np.ascontiguousarray(kin, dtype=np.float64)
+    pp, dy, ko = np.empty(m), np.empty(m), np.empty((m, 3))
+    caps = C.c_uint64(0)
+    rc = lib().lya_mc_redistribution_host(float(a), float(y), dp(k), int(seed), int(m), dp(pp), dp(dy), dp(ko),
+                                          C.byref(caps))
+    if rc != REC_OK:
+        raise RecError(lib().rec_last_error(None).decode())
+    return pp, dy, ko, caps.value
 
 
 def mc_scalars(z, n=1, **kw) -> dict:
