@@ -308,8 +308,9 @@ rec_status rec_kernel_times(rec_ctx* ctx, double* ms_out, int64_t* launches_out)
  * A re-emitted photon takes the frequency of Eq. inout (isotropic
  * scattering, the atom's velocity drawn from the third factor of Eq. MC).
  * A photon whose gas-frame offset falls below -x_lost is lost by redshifting.
- * T = T_gamma(z) throughout.  All arithmetic is binary64 in both precision
- * forms; the box's fields are read in their stored types. */
+ * T = T_gamma(z) throughout.  The arithmetic is set by lya_mc_params.arith
+ * (binary64 by default) independently of the context's precision form; the
+ * box's fields are read in their stored types. */
 typedef struct {
   double z;          /* redshift of the snapshot (> 0) */
   double eps;        /* step (3): path of eps mean free paths per step, (0, 1] */
