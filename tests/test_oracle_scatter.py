@@ -338,3 +338,16 @@ def test_max_steps_caps_photons():
     d, P = _uniform_box(2, 16)
     rec, cnt = O.lya_mc(cp, mp, 2, d, np.full(8, 0.5), P)
     assert cnt[3] == 16 and np.all(rec["n_steps"] == 1000)
+
+
+def test_openmp_build_gives_the_same_photons():
+    """The tests run the Monte Carlo in the oracle's OpenMP build (photons are
+    independent); its records equal the plain build's."""
+    cp = O.default_cosmo()
+    mp = O.mc_params(1700.0, zeta=3e4, lambda2g=2e4, seed=12)
+    S = O.mc_setup(cp, mp, 2)
+    mp.x_lost = 50 * _x50(S, 0.5 * S["nH"])
+    d, P = _uniform_box(2, 64)
+    a, _ = O.lya_mc(cp, mp, 2, d, np.full(8, 0.5), P)
+    b, _ = O.lya_mc(cp, mp, 2, d, np.full(8, 0.5), P, threads=4)
+    assert np.array_equal(a, b)
