@@ -207,6 +207,15 @@ rec_status rec_graph_step(rec_ctx* ctx, int32_t step, double z_from, double z_to
  * Errors: REC_EINVAL, REC_ESTATE (no state yet), REC_ENOMEM, REC_ECUDA. */
 rec_status rec_step_trbdf2(rec_ctx* ctx, int32_t step, double z_from, double z_to, rec_stats* dev_stats);
 
+/* Partial mixing: set the share f_alpha of the full-mixing rate (REC_MIX_PARTIAL
+ * contexts) for the following rec_step and rec_graph_step calls.  Sec. V takes
+ * the share from the Monte-Carlo mixing fraction f_alpha(D) of Sec. III.B (the
+ * fraction of Ly-alpha photons destroyed farther than D from where they were
+ * emitted), which changes with redshift; lya_scatter_mc gives it.  Host-side
+ * only: takes effect from the next call enqueued.
+ * Errors: REC_EINVAL (not a partial-mixing context, f_alpha outside [0, 1]). */
+rec_status rec_set_f_alpha(rec_ctx* ctx, double f_alpha);
+
 /* Current transport tuning of a context (defaults after rec_init). */
 rec_status rec_get_tuning(const rec_ctx* ctx, rec_tuning* out);
 

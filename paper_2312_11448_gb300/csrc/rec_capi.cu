@@ -598,6 +598,14 @@ void rec_free(rec_ctx* c) {
   delete c;
 }
 
+rec_status rec_set_f_alpha(rec_ctx* c, double f_alpha) {
+  if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");
+  if (c->params.mixing != REC_MIX_PARTIAL) return fail(c, REC_EINVAL, "f_alpha applies to partial mixing only");
+  if (!(f_alpha >= 0.0 && f_alpha <= 1.0)) return fail(c, REC_EINVAL, "f_alpha must be in [0, 1]");
+  c->params.f_alpha = f_alpha;
+  return REC_OK;
+}
+
 rec_status rec_step_trbdf2(rec_ctx* c, int32_t step, double z_from, double z_to, rec_stats* st) {
   (void)step;
   if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");

@@ -101,6 +101,7 @@ def lib():
         L.rec_timing.argtypes = [vp, i32]
         L.rec_kernel_times.argtypes = [vp, P(d), P(C.c_int64)]
         L.rec_step_trbdf2.argtypes = [vp, i32, d, d, vp]
+        L.rec_set_f_alpha.argtypes = [vp, d]
         L.lya_scatter_mc.argtypes = [vp, P(McParams), vp, vp, vp]
         L.lya_voigt.argtypes = [d, C.c_int64, P(d), P(d)]
         L.lya_voigt_mixed.argtypes = [d, C.c_int64, P(d), P(d)]
@@ -114,7 +115,7 @@ def lib():
         for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc", "rec_graph_step", "rec_get_tuning", "rec_set_tuning",
                   "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times",
                   "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2", "lya_mc_scalars",
-                  "lya_mc_redistribution_host", "lya_voigt_mixed"):
+                  "lya_mc_redistribution_host", "lya_voigt_mixed", "rec_set_f_alpha"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -172,6 +173,21 @@ def voigt(a: float, y, mixed=False) -> np.ndarray:
 
 
 MC_ARITH = {"fp64": 0, "mixed": 1}
+
+
+def mixing_fraction(records, D_kpc) -> np.ndarray:
+    """f_alpha(D) of Sec. III.B from Monte-Carlo records: the fraction of the
+    photons destroyed (photo-ionisation or two-photon decay) farther than D
+    (comoving kpc, scalar or array) from their emission point.  Photons lost
+    by redshifting or stopped by the step cap are not destroyed and do not
+    count.  Host post-processing of lya_scatter_mc's records."""
+    fate = np.asarray(records["fate"])
+    D = np.asarray(records["D_kpc"])[(fate == 1) | (fate == 2)]
+    Dq = np.atleast_1d(np.asarray(D_kpc, dtype=np.float64))
+    if D.size == 0:
+        return np.full(Dq.shape, np.nan)
+    Ds = np.sort(D)
+    return 1.0 - np.searchsorted(Ds, Dq, side="right") / Ds.size
 
 
 def mc_redistribution_mixed(a, y, seed, m, kin=(0.0, 0.0, 1.0)):
@@ -412,6 +428,10 @@ class Box:
     def graph_step(self, step, z_from, z_to, slot=0):
         """transport(step, z_from) + step(step, z_from, z_to) as one CUDA graph launch."""
         self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_graph_step")
+
+    def set_f_alpha(self, f_alpha):
+        """Partial mixing: the share of the full-mixing rate for the following steps."""
+        self._check(lib().rec_set_f_alpha(self.ctx, float(f_alpha)), "rec_set_f_alpha")
 
     def step_trbdf2(self, step, z_from, z_to, slot=0):
         """rec_step_trbdf2: the second-order (TR-BDF2) step (FP64 form, tally or full mixing)."""

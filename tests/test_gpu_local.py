@@ -135,3 +135,28 @@ def test_partial_mode_rejections():
     with pytest.raises(rec.RecError, match="tally and full"):
         box.step_noalloc(1400.0, 1390.0)
     box.close()
+
+
+@pytest.mark.skip(reason="rec_set_f_alpha has not been run on a GPU yet")
+def test_set_f_alpha_equals_a_context_made_with_it(cosmo):
+    """Changing the partial-mixing share on a context gives the step of a
+    context created with that share (Sec. V's redshift-dependent f_alpha)."""
+    from gpu_helpers import make_fields
+    from paper_2312_11448_gb300 import rec
+    d, U = make_fields(12, 0.8, 3.0, seed=1)
+    a = rec.Box(12, d, U, 1000, precision="fp64", mixing="partial", seed=7, f_alpha=0.9)
+    b = rec.Box(12, d, U, 1000, precision="fp64", mixing="partial", seed=7, f_alpha=0.4)
+    for box in (a, b):
+        box.state_init(1300.0)
+    a.set_f_alpha(0.4)
+    a.step(0, 1300.0, 1290.0)
+    b.step(0, 1300.0, 1290.0)
+    for name in ("x", "T", "vel4", "emis"):
+        assert np.array_equal(a.host(name), b.host(name)), name
+    with pytest.raises(rec.RecError, match="0, 1"):
+        a.set_f_alpha(1.2)
+    full = rec.Box(8, d[:512], U[:512], 10, precision="fp64", mixing="full")
+    with pytest.raises(rec.RecError, match="partial"):
+        full.set_f_alpha(0.5)
+    for box in (a, b, full):
+        box.close()
