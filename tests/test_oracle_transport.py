@@ -236,3 +236,124 @@ def test_openmp_build_same_integers(cosmo, precision):
     t4, c4, _ = O.transport(cosmo, n, 1150.0, 5, 3, 150000, emis, vel4, T, q, precision=precision, threads=4)
     assert np.array_equal(t1, t4) and c1 == c4
     assert O.lib().orc_threads(0) == 1 and O.lib(openmp=True).orc_threads(4) == 4
+
+
+# ---- the emission-frame Doppler term (omega_r = omega (1 - U_par), App. A) ------------
+def _closed_form_cell(pk, n, s, eps):
+    """Cell containing p + n_hat s per packet, and a mask of the points that lie
+    farther than eps (cells) from every face."""
+    home = _cell_xyz(pk["home"], n)
+    end = home + pk["f"] + pk["dir"] * s[:, None]
+    ok = ~(np.abs(end - np.round(end)) < eps).any(axis=1)
+    cell = np.floor(end).astype(np.int64) % n
+    return (cell[:, 2] * n + cell[:, 1]) * n + cell[:, 0], ok
+
+
+@pytest.mark.parametrize("precision,eps", [("f32", 2e-3), ("f64", 1e-9)])
+def test_galilean_invariance_uniform_flow(cosmo, precision, eps):
+    """A bulk flow that is the same in every cell is a change of frame: in the
+    gas frame every packet is emitted and absorbed exactly as with no flow, so
+    the absorbing cells must equal the zero-flow ones.  The home-cell Doppler
+    term (emission frame) and the per-cell term (absorption frame) must cancel;
+    a sign error in either moves most packets by kappa n.U ~ 2 cells here."""
+    n, z, Np = 16, 1100.0, 20000
+    emis, vel4, T, q = _inputs(n, 0.0, seed=5, precision=precision)
+    U = np.array([3.0, -4.0, 2.5])  # km/s, along no axis
+    vel_u = pack_vel4(np.tile(U, (n ** 3, 1)), vel4.dtype)
+    t0, c0, p0 = O.transport(cosmo, n, z, 29, 4, Np, emis, vel4, T, q, precision=precision, dump=Np)
+    t1, c1, p1 = O.transport(cosmo, n, z, 29, 4, Np, emis, vel_u, T, q, precision=precision, dump=Np)
+    # same random draws: positions, directions and frequencies are frame independent
+    assert np.array_equal(p0["f"], p1["f"]) and np.array_equal(p0["dir"], p1["dir"])
+    assert np.array_equal(p0["xi"], p1["xi"])
+    kappa, _ = O.transport_params(cosmo, n, z)
+    assert kappa * np.linalg.norm(U) > 2.0  # the flow shifts resonance by more than two cells
+    _, ok = _closed_form_cell(p0, n, np.maximum(p0["u0"], 0.0), eps)
+    ok &= ~(np.abs(p0["u0"]) < eps)  # absorbed-at-home boundary
+    assert ok.mean() > 0.97
+    assert np.array_equal(p1["absorb"][ok], p0["absorb"][ok])
+    assert c1["absorbed"] == Np and c0["absorbed"] == Np
+    assert np.abs(t1.astype(np.int64) - t0.astype(np.int64)).sum() <= 2 * (~ok).sum()
+
+
+def _slab_walk(pk, n, s0, shift, sig):
+    """Absorption distance along each ray in a two-slab flow, U_z = +V for
+    iz < n/2 and -V above, derived from the physics rather than from the
+    traversal: the packet is emitted at gas-frame offset xi in its home cell,
+    so in the Hubble frame its resonance distance is s0 = kappa xi v_th plus
+    kappa n.U_home (emitter moving along n blue-shifts the packet); in a cell
+    moving with U_c the resonance point is kappa n.U_c earlier.  In a segment
+    of the other slab the distance is therefore s0 + 2 kappa V n_z sigma_home
+    (shift = 2 kappa V n_z sigma_home); a packet entering a segment already past
+    its resonance point is absorbed in the first cell it enters.  Returns
+    (s, boundary-safe mask)."""
+    half = n // 2
+    z0 = (pk["home"] // (n * n)) + pk["f"][:, 2]
+    nz = pk["dir"][:, 2]
+    out = np.full(len(z0), np.nan)
+    safe = np.ones(len(z0), dtype=bool)
+    for i in range(len(z0)):
+        zz, d = z0[i], nz[i]
+        s_start = 0.0
+        # the boundaries the ray meets, in order
+        nxt = (np.floor(zz / half) + 1) * half if d > 0 else np.floor(zz / half) * half
+        seg_sig = sig[i]
+        for _ in range(64):
+            s_end = (nxt - zz) / d if d != 0 else np.inf
+            r = s0[i] if seg_sig == sig[i] else s0[i] + shift[i]
+            if r <= s_end:
+                s_hit = max(r, s_start)
+                if abs(r - s_start) < 1e-6 or abs(r - s_end) < 1e-6:
+                    safe[i] = False
+                if s_hit == s_start and s_start > 0:
+                    s_hit = s_start + 1e-7  # just inside the entered cell
+                out[i] = s_hit
+                break
+            s_start = s_end
+            seg_sig = -seg_sig
+            nxt = nxt + half if d > 0 else nxt - half
+        else:
+            safe[i] = False
+    return out, safe
+
+
+@pytest.mark.parametrize("precision,eps", [("f32", 2e-3), ("f64", 1e-9)])
+def test_two_slab_flow_closed_form(cosmo, precision, eps):
+    """Closed-form absorbing cells in a flow with a velocity jump: every packet
+    has the same frequency offset xi0 (a one-point profile table) and uniform
+    temperature, so its resonance distance follows from the slab it is in and
+    its direction alone.  Pins the sign and the frame of the home-cell
+    Doppler term independently of the traversal code."""
+    n, z, Np, V, xi0, T0 = 16, 1100.0, 6000, 8.0, 1.5, 3000.0
+    R = np.float32 if precision == "f32" else np.float64
+    emis = np.random.default_rng(3).uniform(0.5, 1.5, n ** 3).astype(R)
+    iz = np.arange(n ** 3) // (n * n)
+    Uz = np.where(iz < n // 2, V, -V)
+    vel4 = pack_vel4(np.stack([np.zeros(n ** 3), np.zeros(n ** 3), Uz], axis=1), R)
+    T = np.full(n ** 3, T0, dtype=R)
+    q = np.full(8, xi0, dtype=R)
+    tally, cnt, pk = O.transport(cosmo, n, z, 41, 6, Np, emis, vel4, T, q, precision=precision, dump=Np)
+    assert cnt["absorbed"] == Np
+    kappa, cth = O.transport_params(cosmo, n, z)
+    s0 = np.full(Np, xi0 * math.sqrt(T0 * cth))  # kappa xi0 v_th, in cells
+    assert s0[0] > 3.0 and 2 * kappa * V > 5.0
+    sig = np.where(pk["home"] // (n * n) < n // 2, 1.0, -1.0)
+    shift = 2.0 * kappa * V * pk["dir"][:, 2] * sig
+    s, safe = _slab_walk(pk, n, s0, shift, sig)
+    home = _cell_xyz(pk["home"], n)
+    end = home + pk["f"] + pk["dir"] * s[:, None]
+    cell = np.floor(end).astype(np.int64) % n
+    cell = (cell[:, 2] * n + cell[:, 1]) * n + cell[:, 0]
+    # away from x and y faces; z faces only matter where the packet resonates
+    # inside a segment (an entered cell's point sits on its z face by construction)
+    ok = safe & ~(np.abs(end[:, :2] - np.round(end[:, :2])) < eps).any(axis=1)
+    inside = np.isclose(s, s0) | np.isclose(s, s0 + shift)
+    ok &= ~(inside & (np.abs(end[:, 2] - np.round(end[:, 2])) < eps))
+    assert ok.mean() > 0.9
+    assert np.array_equal(pk["absorb"][ok], cell[ok])
+    # the flow matters: the zero-flow cells, and the cells a reversed home-cell
+    # term would give, both disagree with the oracle for many packets
+    c_noflow, _ = _closed_form_cell(pk, n, s0, eps)
+    assert (c_noflow[ok] != pk["absorb"][ok]).mean() > 0.2
+    s_wrong, _ = _slab_walk(pk, n, s0 - shift, shift, sig)
+    c_wrong, _ = _closed_form_cell(pk, n, np.maximum(np.nan_to_num(s_wrong), 0.0), eps)
+    assert (c_wrong[ok] != pk["absorb"][ok]).mean() > 0.2
