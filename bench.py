@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--prep", type=int, default=S0, help="untimed steps before the warm-up (profiling: 0)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-box measurement")
     ap.add_argument("--no-scatter", action="store_true", help="skip the scattering Monte-Carlo measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (reverse sweep) measurement")
     return ap.parse_args()
 
 
@@ -170,6 +171,26 @@ def algorithmic_bytes(precision, n3, emitted, queued, crossings, newton_passes):
     return dict(emit=emit, march=march, rec_step=step, alloc=alloc)
 
 
+def method_bytes(precision, n3, emitted, queued, crossings, newton_passes):
+    """Algorithmic bytes of the method itself (the per-unit figures of the
+    measurement plan), without the library's own intermediate traffic (the
+    march queue, the (x, 1-x) cache):
+      transport, per packet: 16 B at emission + 4 B tally, and per cell
+        crossing one velocity (16 B binary32 / 32 B binary64);
+      rec_step, per cell: 20 B (FP64 form 28 B) per Newton evaluation pass
+        (delta, x_e, T, tally) + 64 B (100 B) for the final pass (reads delta,
+        x_e, T, tally, U; writes x_e, T, U, emission weight, tally zero).
+    Split by kernel: emission = 16 B per packet + 4 B per packet absorbed at
+    home; march = 4 B per queued packet + one velocity per crossing."""
+    v = 16 if precision == "mixed" else 32
+    pass_b, final_b = (20, 64) if precision == "mixed" else (28, 100)
+    home = emitted - queued
+    emit = emitted * 16 + home * 4
+    march = queued * 4 + crossings * v
+    step = n3 * (pass_b * newton_passes + final_b)
+    return dict(emit=emit, march=march, rec_step=step, whole=emit + march + step)
+
+
 def time_form(cfg, zs, precision, W, K, seed, dist, clocks, prep=S0, graph=False):
     import torch
     from paper_2312_11448_gb300 import tune
@@ -210,7 +231,9 @@ def time_form(cfg, zs, precision, W, K, seed, dist, clocks, prep=S0, graph=False
     if flags & 4 or not math.isfinite(st[-1]["X_e"]) or emitted < cfg.n_packets:
         raise RuntimeError(f"{precision} form: invalid state (flags={flags}, X_e={st[-1]['X_e']}, emitted={emitted})")
     ab = algorithmic_bytes(precision, box.n3, emitted, queued, crossings, passes)
+    mb = method_bytes(precision, box.n3, emitted, queued, crossings, passes)
     out = dict(ms=ms, kt=kt, emitted=emitted, queued=queued, crossings=crossings, passes=passes, flags=flags, ab=ab,
+               mb=mb,
                Xe=st[-1]["X_e"], box=box, delta=delta, U=U,
                tuning=dict(box.tuning(), source="autotuner table" if tuned else "defaults"))
     if graph:
@@ -261,6 +284,65 @@ def time_e2e(cfg, zs, res, K):
     h2d = h_delta.numel() * h_delta.element_size() + h_vel.numel() * h_vel.element_size()
     d2h = h_x.numel() * h_x.element_size() + h_T.numel() * h_T.element_size()
     return ms, h2d, d2h
+
+
+def time_adjoint(cfg, zs, n_window=20, seed=1):
+    """The adjoint workload of the 256^3 configuration: FP64 form, tally mode,
+    a window of n_window steps of the 400-step schedule ending at the node
+    nearest z* = 1100, objective the visibility function there.  Forward:
+    transport + rec_step per step with the tallies stored and ceil(sqrt(N))
+    checkpoints; reverse: segment replays (rec_step) and rec_step_adjoint per
+    step.  Reports ms per reverse step (replay included), the forward FP64 step
+    beside it and the peak device memory, with the memory formula for the full
+    400-step run."""
+    import torch
+    from paper_2312_11448_gb300 import rec
+    from paper_2312_11448_gb300.autograd import Trajectory
+    k_star = int(np.argmin(np.abs(zs - 1100.0)))
+    k0 = k_star - n_window
+    zw = zs[k0:k_star + 1]
+    delta, U = fields_of(cfg, seed)
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    box = rec.Box(cfg.n, delta, U, cfg.n_packets, precision="fp64", mixing="tally", seed=seed,
+                  stream=torch.cuda.Stream())
+    box.state_init(zw[0])  # Saha state at the window start (the timing does not depend on it)
+    x0 = box.x.clone()
+    T0 = box.T.clone()
+    traj = Trajectory(box, zw, run_transport=True)
+    stream = box.stream
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    Xe = traj.forward(x0, T0)
+    e[1].record(stream)
+    J, dJ = rec.objective(zw, Xe, 2, 1100.0)
+    g_delta, g_T0, g_x0, g_a = traj.backward(dJ)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, rev_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    finite = bool(torch.isfinite(g_delta).all() and torch.isfinite(g_T0).all() and torch.isfinite(g_a).all())
+    peak = torch.cuda.max_memory_allocated() - base
+    cell_state = 8 + 8 + 32  # x_e, T, double4 velocity per checkpoint or replay state
+    n3 = cfg.n ** 3
+    full = {"tallies_gb": N_STEPS * n3 * 4 / 1e9,
+            "checkpoints_gb": math.ceil(math.sqrt(N_STEPS)) * n3 * cell_state / 1e9,
+            "replay_states_gb": math.ceil(math.sqrt(N_STEPS)) * n3 * cell_state / 1e9}
+    full["total_gb"] = sum(full.values())
+    box.close()
+    del traj, g_delta, g_T0, g_x0, g_a
+    torch.cuda.empty_cache()
+    return {"workload": (f"{cfg.n}^3, FP64 form, tally mode, steps {k0}..{k_star} of {N_STEPS} (z {zw[0]:.0f} -> "
+                         f"{zw[-1]:.0f}) from the Saha state at z {zw[0]:.0f}, objective: visibility at "
+                         f"z* = {zw[-1]:.0f}, checkpoints every "
+                         f"{traj_k(n_window)} steps"),
+            "forward_ms_per_step": fwd_ms / n_window, "reverse_ms_per_step": rev_ms / n_window,
+            "J": J, "finite_gradients": finite, "peak_device_gb": peak / 1e9,
+            "full_run_memory_estimate": full, "gpu_launch_groups": "transport, rec_step, rec_step_adjoint"}
+
+
+def traj_k(S):
+    return max(1, math.ceil(math.sqrt(S)))
 
 
 def time_batched(W, K, prep=60, n_boxes=64):
@@ -538,6 +620,15 @@ def run_ours(args):
         fp64 = time_form(cfg, zs, "fp64", W, max(5, K // 3), seed=rank_seed(rank), dist=dist, clocks=clocks,
                          prep=args.prep)
     e2e = None if args.no_e2e else time_e2e(cfg, zs, mixed, K)
+    adjoint = None
+    if not args.no_adjoint and world == 1:
+        for r in (fp64,):
+            if r:
+                r["box"].close()
+        torch.cuda.empty_cache()
+        t0 = clocks.mark()
+        adjoint = time_adjoint(cfg, zs)
+        clocks.window(t0, clocks.mark())
     batched = None
     if not args.no_batched:
         for r in (mixed, fp64):
@@ -578,11 +669,27 @@ def run_ours(args):
              "rec_step": "rec_step passes (k_newton_tma + k_final<mixed>)", "alloc": "allocation (3 kernels)"}
 
     def roof(g):
+        """frac on the method's bytes (method_bytes); the library's own count,
+        which adds its intermediate traffic, beside it."""
         ms_g = groups[g][0] / K
-        ach = mixed["ab"][g] / (ms_g * 1e-3) / 1e9
+        mb = mixed["mb"].get(g, mixed["ab"][g])
+        ach = mb / (ms_g * 1e-3) / 1e9
+        ach_b = mixed["ab"][g] / (ms_g * 1e-3) / 1e9
         return {"bound": "hbm", "kernel": names[g], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
-                "algorithmic_bytes_per_launch": mixed["ab"][g], "avg_launch_ms": ms_g}
+                "algorithmic_bytes_per_launch": mb, "avg_launch_ms": ms_g,
+                "bytes_rule": "method bytes (16 B/packet + 4 B/tally + 16 B/crossing; rec_step 20 B/pass + 64 B)"
+                if g != "alloc" else "library count (3 reads of r + prefix write per cell)",
+                "with_library_traffic": {"algorithmic_bytes_per_launch": mixed["ab"][g], "achieved": ach_b,
+                                         "frac": ach_b / peak}}
+
+    def whole_step(r, k_steps, ms_total):
+        ms_s = ms_total / k_steps
+        ach = r["mb"]["whole"] / (ms_s * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "algorithmic_bytes_per_step": r["mb"]["whole"], "ms_per_step": ms_s,
+                "bytes_rule": "per packet 16 B + 4 B tally + 16 B per crossing (FP64 form 32 B), per cell 20 B per "
+                              "Newton pass + 64 B final (FP64 form 28 B + 100 B)"}
 
     launches = sum(v[1] for v in mixed["kt"].values())
     out = {
@@ -598,6 +705,7 @@ def run_ours(args):
         "newton_passes": mixed["passes"], "X_e": mixed["Xe"], "flags": mixed["flags"],
         "roofline": dict(roof(dominant), traffic=profiled_traffic(dominant)),
         "roofline_other": {g: roof(g) for g in ("emit", "march", "rec_step", "alloc") if g in groups and g != dominant},
+        "roofline_whole_step": whole_step(mixed, K, ms_mixed),
         "queued_fraction": mixed["queued"] / max(mixed["emitted"], 1),
         "tuning": mixed["tuning"],
         "gpu_launches": launches,
@@ -607,7 +715,8 @@ def run_ours(args):
                             "ms_per_step": ms_fp64 / K64, "steps": K64,
                             "packets_per_s": world * fp64["emitted"] * K64 / (ms_fp64 * 1e-3),
                             "kernel_ms_per_step": {g: v[0] / K64 for g, v in fp64["kt"].items() if v[1]},
-                            "mixed_over_fp64": (ms_fp64 / K64) / (ms_mixed / K)}
+                            "mixed_over_fp64": (ms_fp64 / K64) / (ms_mixed / K),
+                            "roofline_whole_step": whole_step(fp64, K64, ms_fp64)}
     if e2e:
         out["e2e"] = {"value": world * n3 * K / (ms_e2e * 1e-3), "unit": "cell-steps/s", "h2d_bytes_per_step": e2e[1],
                       "d2h_bytes_per_step": e2e[2],
@@ -617,6 +726,14 @@ def run_ours(args):
         out["graph"] = {"ms_per_step": gms / K, "value": world * n3 * K / (gms * 1e-3), "unit": "cell-steps/s",
                         "api": "rec_graph_step: transport + rec_step captured as one CUDA graph per step, "
                                "executable graph updated in place", "steps": K}
+    if adjoint:
+        if fp64:
+            f_ms = ms_fp64 / K64
+            f_step_ms = fp64["kt"]["rec_step"][0] / K64
+            adjoint["fp64_forward_step_ms"] = f_ms
+            adjoint["reverse_over_forward_step"] = adjoint["reverse_ms_per_step"] / f_ms
+            adjoint["reverse_over_forward_rec_step"] = adjoint["reverse_ms_per_step"] / f_step_ms
+        out["adjoint"] = adjoint
     if batched:
         out["batched"] = batched
     if scatter:
@@ -650,8 +767,10 @@ def run_reference(args):
     value = cfg.n ** 3 / (ms * 1e-3)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": 0, "steps": K,
            "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64 (oracle; binary32 transport arithmetic)", "data": "synthetic",
-           "config": {"workload": describe(cfg, "oracle"), "n": cfg.n, "packets_per_step": cfg.n_packets},
+           "dtype": "f64 (oracle; binary32 transport arithmetic; transport sampled and scaled)", "data": "synthetic",
+           "config": {"workload": describe(cfg, "oracle"), "n": cfg.n, "packets_per_step": cfg.n_packets,
+                      "sampled": f"each timed step transports {sample:.0e} of the {cfg.n_packets:.0e} packets and "
+                                 f"scales that time linearly; ms_per_step is the scaled step, not wall time"},
            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                             "sample": f"per step: oracle rec_step over all cells + transport of {sample:.0e} packets "
                                       f"scaled to {cfg.n_packets:.0e}; {platform_name()}"},

@@ -269,6 +269,13 @@ rec_status rec_step_adjoint(rec_ctx* ctx, int32_t step, double z_from, double z_
  * (the start node of a trajectory; rec_step_adjoint handles its end node). */
 rec_status rec_xe_adjoint(rec_ctx* ctx, const double* x, double Xe_bar, double* xbar, double* g_delta);
 
+/* Statistics of the current state, for the start node of a trajectory: writes
+ * X_e = sum delta x / sum delta (Sec. II.A), lambda = <alpha_e n_e^2>/<n_1s> and
+ * S1s of each box (n_boxes records) from the sums of the last rec_state_init,
+ * rec_refresh or rec_step; the other fields of the records are left as they are.
+ * Errors: REC_EINVAL, REC_ESTATE (no sums yet), REC_ECUDA. */
+rec_status rec_volume_stats(rec_ctx* ctx, rec_stats* dev_stats);
+
 /* Objective on an X_e history over node redshifts zs[0..n_nodes-1] (decreasing),
  * host computation.  objective 1: X_e at the node nearest z_star.  objective 2:
  * the visibility function g = (d tau/dz) exp(-tau) at that node, with the Thomson
@@ -376,6 +383,29 @@ typedef struct {
  * REC_ECUDA. */
 rec_status lya_scatter_mc(rec_ctx* ctx, const lya_mc_params* mp, const uint32_t* dev_prefix,
                           lya_mc_photon* dev_photons, lya_mc_stats* dev_stats);
+
+/* The mixing fraction f_alpha(D) of Sec. III.B (its Fig. MCtravel) from the
+ * records of lya_scatter_mc: among the photons destroyed in the line
+ * (two-photon decay or photo-ionisation of the n = 2 atom, the fates that end
+ * a Ly-alpha photon's energy locally), the fraction whose comoving distance from
+ * the emission point exceeds D.  Sec. V uses f_alpha at D = 3 kpc as the share of
+ * full mixing (rec_set_f_alpha).  Photons lost by redshifting are not
+ * destroyed and do not count.  Photons stopped by the step cap (LYA_MC_CAPPED)
+ * would still be destroyed or lost later, so they are reported separately.
+ *   dev_photons: device records [n_photons] of lya_scatter_mc (1 <= n_photons < 2^32).
+ *   D_kpc: HOST array [m] of distances, comoving kpc, finite and >= 0, 1 <= m <= 256;
+ *     read during the call.
+ *   dev_out: DEVICE double [3 m]: dev_out[j] = B_j / N_d, with B_j the destroyed
+ *     photons farther than D_j and N_d all destroyed photons (NaN if N_d = 0);
+ *     dev_out[m + j] = B_j / (N_d + N_c) and dev_out[2 m + j] = (B_j + N_c) / (N_d + N_c),
+ *     N_c the capped photons: the range f_alpha(D_j) can take whatever the capped
+ *     photons' fates would have been.
+ *   dev_counts: DEVICE uint64 [4] (may be NULL): photons per fate (LYA_MC_*).
+ * Counts are integers, so the result does not depend on the launch.  Scratch:
+ * 2 KiB of counters, allocated by the context on first use.
+ * Errors: REC_EINVAL, REC_ENOMEM, REC_ECUDA. */
+rec_status lya_mc_mixing_fraction(rec_ctx* ctx, const lya_mc_photon* dev_photons, uint64_t n_photons,
+                                  const double* D_kpc, int32_t m, double* dev_out, uint64_t* dev_counts);
 
 /* Scalars of a Monte-Carlo snapshot as lya_scatter_mc uses them (host
  * computation, no GPU needed): out[0] = a, out[1] = v_th / c,

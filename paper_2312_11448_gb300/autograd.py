@@ -79,11 +79,11 @@ class Trajectory:
                 self._prepare_tally(s, self.zs[s])
                 b.tally.copy_(self.tallies[s])
                 b.refresh(self.zs[s])
+                if s == 0:
+                    b.volume_stats(slot=0)  # X_e of the start node
                 b.step(s, self.zs[s], self.zs[s + 1], slot=s + 1)
         st = b.stats_all()
-        d = b.delta.double()
-        Xe0 = float((d * self.x0).sum() / d.sum())
-        return np.array([Xe0] + [st[s + 1]["X_e"] for s in range(self.S)])
+        return np.array([st[s]["X_e"] for s in range(self.S + 1)])
 
     def backward(self, dJ_dXe):
         """Reverse sweep for weights dJ/dX_e at every node.

@@ -591,6 +591,7 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->div);
   cudaFree(c->mc_scratch);
   cudaFree(c->trb_scratch);
+  cudaFree(c->mf_cnt);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   cudaFree(c->bx);
   cudaFree(c->bstep);
@@ -643,6 +644,30 @@ rec_status lya_scatter_mc(rec_ctx* c, const lya_mc_params* mp, const uint32_t* d
   cudaError_t e = rec::run_scatter_mc(c, S, mp, dev_prefix, dev_photons, dev_stats);
   if (e == cudaErrorMemoryAllocation) return fail(c, REC_ENOMEM, "Monte-Carlo scratch");
   if (e != cudaSuccess) return cuda_fail(c, e, "lya_scatter_mc");
+  return REC_OK;
+}
+
+rec_status lya_mc_mixing_fraction(rec_ctx* c, const lya_mc_photon* dev_photons, uint64_t n_photons,
+                                  const double* D_kpc, int32_t m, double* dev_out, uint64_t* dev_counts) {
+  if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");
+  if (!dev_photons || !dev_out || !D_kpc) return fail(c, REC_EINVAL, "lya_mc_mixing_fraction: a buffer is NULL");
+  if (n_photons < 1 || n_photons >= (1ull << 32)) return fail(c, REC_EINVAL, "n_photons must be in [1, 2^32)");
+  if (m < 1 || m > rec::kMixFracMax)
+    return fail(c, REC_EINVAL, "m must be in [1, " + std::to_string(rec::kMixFracMax) + "]");
+  for (int j = 0; j < m; ++j)
+    if (!(D_kpc[j] >= 0.0) || !is_finite(D_kpc[j])) return fail(c, REC_EINVAL, "distances must be finite and >= 0");
+  cudaError_t e = rec::run_mixing_fraction(c, dev_photons, n_photons, D_kpc, m, dev_out, dev_counts);
+  if (e == cudaErrorMemoryAllocation) return fail(c, REC_ENOMEM, "mixing-fraction counters");
+  if (e != cudaSuccess) return cuda_fail(c, e, "lya_mc_mixing_fraction");
+  return REC_OK;
+}
+
+rec_status rec_volume_stats(rec_ctx* c, rec_stats* dev_stats) {
+  if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");
+  if (!dev_stats) return fail(c, REC_EINVAL, "dev_stats is NULL");
+  if (!c->emis_ready) return fail(c, REC_ESTATE, "no state sums yet: call rec_state_init or rec_refresh first");
+  cudaError_t e = rec::launch_volume_stats(c, dev_stats);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_volume_stats");
   return REC_OK;
 }
 

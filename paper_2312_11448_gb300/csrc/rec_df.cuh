@@ -1,0 +1,73 @@
+// Double-float arithmetic: a value carried as the unevaluated sum hi + lo of
+// two binary32 numbers (about 48 significant bits), built from error-free
+// transformations: Knuth's TwoSum, the fast TwoSum of Dekker (1971) for
+// |a| >= |b|, and the TwoProduct from one fused multiply-add (Ogita, Rump &
+// Oishi, SIAM J. Sci. Comput. 26, 1955 (2005)).  On GB300 the binary64 pipe
+// issues about 1/58 of the binary32 rate, so a residual that needs more than
+// binary32 but is evaluated once per cell per pass costs far less this way.
+// The __fadd_rn / __fmul_rn intrinsics keep the compiler from fusing the
+// transforms' operations into multiply-adds (which would break exactness).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rec {
+
+struct dfloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  const float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+  return {s, e};
+}
+
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  const dfloat s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+  return df_fast_two_sum(p, e);
+}
+
+// Split a binary64 value into hi + lo with integer operations only (no
+// binary64 arithmetic or conversion): hi takes the sign, the exponent and the
+// leading 24 significand bits, lo the remaining 29 bits (rounded to 24).
+// Exact to 2^-48 relative for 2^-74 <= |x| < 2^127; outside that range (not
+// reached by ionisation fractions) it falls back to a rounded conversion.
+__device__ __forceinline__ dfloat df_from_double(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+  if (e < 949u || e > 1150u) return {__double2float_rn(x), 0.0f};
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((e - 896u) << 23) | ((uint32_t)(b >> 29) & 0x7fffffu));
+  const float scale = __uint_as_float((e - 948u) << 23);  // 2^(e - 1075)
+  const float lo = __fmul_rn(__uint2float_rn((uint32_t)b & 0x1fffffffu), scale);
+  return {hi, sign ? -lo : lo};
+}
+
+// hi + lo rounded to one binary32 value
+__device__ __forceinline__ float df_to_float(dfloat a) { return __fadd_rn(a.hi, a.lo); }
+
+}  // namespace rec

@@ -177,6 +177,8 @@ struct rec_ctx {
   // second-order step (rec_step_trbdf2): stage arrays and scalars
   void* trb_scratch = nullptr;
   size_t trb_bytes = 0;
+  // mixing fraction of Monte-Carlo records (lya_mc_mixing_fraction): counters
+  void* mf_cnt = nullptr;
 };
 
 namespace rec {
@@ -223,6 +225,8 @@ double thomson_sigma_c(); // sigma_T c, m^3/s
 cudaError_t launch_state_init(rec_ctx* c, double z);
 cudaError_t launch_refresh(rec_ctx* c, double z);
 cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* st);
+// X_e, lambda and S_1s of the current state of every box into st.
+cudaError_t launch_volume_stats(rec_ctx* c, rec_stats* st);
 // Context-free FP64 step on static device scratch; no device allocation.
 rec_status launch_rec_step_noalloc(const rec_params& p, const rec_box& b, double z_from, double z_to,
                                    cudaStream_t stream, rec_stats* st, std::string* why);
@@ -260,6 +264,9 @@ uint64_t scatter_redistribution_mixed_host(double a, double y, const double* kin
                                            double* ppar, double* dy, double* kout);
 cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp, const uint32_t* prefix,
                            lya_mc_photon* out, lya_mc_stats* st);
+constexpr int kMixFracMax = 256;  // distances per lya_mc_mixing_fraction call
+cudaError_t run_mixing_fraction(rec_ctx* c, const lya_mc_photon* rec, uint64_t n, const double* D, int m,
+                                double* out, uint64_t* counts);
 
 // rec_trbdf2.cu: second-order (TR-BDF2) step, FP64 form, tally and full mixing
 cudaError_t launch_rec_step_trbdf2(rec_ctx* c, double z_from, double z_to, rec_stats* st);

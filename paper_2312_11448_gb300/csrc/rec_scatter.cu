@@ -811,6 +811,52 @@ __global__ void k_scatter_stats(const unsigned long long* cnt, lya_mc_stats* st)
   st->nonfinite = cnt[7];
 }
 
+// ---- mixing fraction f_alpha(D) of Sec. III.B from the photon records ----------------
+// Destroyed photons (two-photon decay or photo-ionisation) are the ones whose
+// Ly-alpha energy leaves the line; f_alpha(D) is the share of them destroyed
+// farther than D from where they were emitted.  Counts are integers
+// (order-independent), so the fractions do not depend on the launch.
+struct MfArgs {
+  const lya_mc_photon* rec;
+  uint64_t n;
+  int32_t m;
+  unsigned long long* cnt;  // [4 + m]: photons per fate, then destroyed photons with D > D_j
+  double D[kMixFracMax];
+};
+
+__global__ void __launch_bounds__(ST) k_mix_fraction(MfArgs a) {
+  __shared__ unsigned int s[4 + kMixFracMax];
+  for (int i = threadIdx.x; i < 4 + a.m; i += ST) s[i] = 0u;
+  __syncthreads();
+  for (uint64_t k = (uint64_t)blockIdx.x * ST + threadIdx.x; k < a.n; k += (uint64_t)gridDim.x * ST) {
+    const unsigned f = (unsigned)a.rec[k].fate;
+    if (f < 4u) atomicAdd(&s[f], 1u);
+    if (f == (unsigned)LYA_MC_TWO_PHOTON || f == (unsigned)LYA_MC_IONISED) {
+      const double D = a.rec[k].D_kpc;
+      for (int j = 0; j < a.m; ++j)
+        if (D > a.D[j]) atomicAdd(&s[4 + j], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 + a.m; i += ST)
+    if (s[i]) atomicAdd(a.cnt + i, (unsigned long long)s[i]);
+}
+
+// out[j] = B_j / N_d; out[m + j] = B_j / (N_d + N_c); out[2m + j] = (B_j + N_c) / (N_d + N_c),
+// with B_j the destroyed photons beyond D_j, N_d the destroyed and N_c the capped ones.
+__global__ void k_mix_fraction_final(const unsigned long long* cnt, int m, double* out, uint64_t* counts) {
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const double Nd = (double)(cnt[LYA_MC_TWO_PHOTON] + cnt[LYA_MC_IONISED]);
+  const double Nc = (double)cnt[LYA_MC_CAPPED];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double B = (double)cnt[4 + j];
+    out[j] = Nd > 0.0 ? B / Nd : nan;
+    out[m + j] = Nd + Nc > 0.0 ? B / (Nd + Nc) : nan;
+    out[2 * m + j] = Nd + Nc > 0.0 ? (B + Nc) / (Nd + Nc) : nan;
+  }
+  if (counts && threadIdx.x < 4) counts[threadIdx.x] = cnt[threadIdx.x];
+}
+
 }  // namespace
 
 // Scalars of one Monte-Carlo snapshot at redshift mp->z.  Branching of an
@@ -992,6 +1038,30 @@ cudaError_t run_scatter_mc(rec_ctx* c, const McSetup& S, const lya_mc_params* mp
     }
     k_scatter_stats<<<1, 32, 0, c->stream>>>(cnt, st);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t run_mixing_fraction(rec_ctx* c, const lya_mc_photon* rec, uint64_t n, const double* D, int m,
+                                double* out, uint64_t* counts) {
+  if (!c->mf_cnt) {
+    cudaError_t e = cudaMalloc(&c->mf_cnt, sizeof(unsigned long long) * (4 + kMixFracMax));
+    if (e != cudaSuccess) { c->mf_cnt = nullptr; return e; }
+  }
+  cudaError_t e = cudaMemsetAsync(c->mf_cnt, 0, sizeof(unsigned long long) * (4 + m), c->stream);
+  if (e != cudaSuccess) return e;
+  MfArgs a;
+  a.rec = rec;
+  a.n = n;
+  a.m = m;
+  a.cnt = (unsigned long long*)c->mf_cnt;
+  for (int j = 0; j < kMixFracMax; ++j) a.D[j] = j < m ? D[j] : 0.0;
+  uint64_t blocks = (n + ST - 1) / ST;
+  const uint64_t cap = (uint64_t)c->sm_count * 4;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  GroupTimer t(c, kTOther, 2);
+  k_mix_fraction<<<(unsigned)blocks, ST, 0, c->stream>>>(a);
+  k_mix_fraction_final<<<1, ST, 0, c->stream>>>(a.cnt, m, out, counts);
   return cudaGetLastError();
 }
 

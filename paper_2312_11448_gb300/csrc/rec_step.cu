@@ -28,6 +28,7 @@
 
 #include <cooperative_groups.h>
 
+#include "rec_df.cuh"
 #include "rec_internal.cuh"
 #include "rec_reduce.cuh"
 
@@ -328,13 +329,17 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
     float4* U = (float4*)a.vel4;
     float* emis = (float*)a.emis;
     const float kdf = (float)a.k.kd, Hf = (float)a.k.H, dtf = (float)a.k.dt;
+    const dfloat Gd = df_from_double(G);
     for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
       float d = delta[i];
       double x = a.x[i];
+      // the state and 1 - x as double-float pairs, from the bits of x
+      const dfloat X = df_from_double(x);
+      const dfloat Y = df_add(dfloat{1.0f, 0.0f}, df_neg(X));
       uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
-      CellF32 c = cell_f32(f, a.k.mixing, d, a.xy[i], T[i], tal, wscale);
+      CellF32 c = cell_f32(f, a.k.mixing, d, make_float2(df_to_float(X), df_to_float(Y)), T[i], tal, wscale);
       float Gcf = Gf;
-      double Gc = G;
+      dfloat Gc = Gd;
       if (PART) {
         const float fm = (float)a.fmix;
         const float Ci = local_C_f32(a.k, ((const float*)a.div)[i], c.n * c.yf);
@@ -342,7 +347,7 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
         c.s = f.dt * fm;
         const float go = ((1.0f - fm) / fm) * Ci * (float)(a.k.beta * a.k.ea);
         Gcf = Gf + go;
-        Gc = G + (double)go;
+        Gc = df_add(Gd, dfloat{go, 0.0f});
       }
       // binary32 roots x' and y' = 1 - x' (both without cancellation) and the
       // discriminant D = B^2 + 4 A c
@@ -351,15 +356,15 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
       float sq = __fsqrt_rn(B * B + 4.0f * c.A * (c.xf + sGf));
       float xr = __fdiv_rn(2.0f * (c.xf + sGf), B + sq);
       float yr = __fdiv_rn(2.0f * (c.A + c.yf), 2.0f * c.A + B + sq);
-      // binary64 state update by its increment: with x' = x + dx the backward-Euler
+      // state update by its increment: with x' = x + dx the backward-Euler
       // equation reads A dx^2 + (2Ax + B) dx + r0 = 0, where
       //   r0 = A x^2 - sG (1 - x)
       // is dt times the net rate (recombination minus photo-ionisation) at the old
-      // state, formed in binary64 since near Saha equilibrium the two terms cancel.
-      // The discriminant of this equation is D again.
-      double y = 1.0 - x;
-      double r0 = fma((double)c.A, x * x, -((double)c.s * Gc) * y);
-      float dx = fdiv(-2.0f * __double2float_rn(r0), 2.0f * c.A * c.xf + B + sq);
+      // state.  Near Saha equilibrium the two terms cancel, so r0 is formed in
+      // double-float arithmetic (about 48 bits) rather than in binary32; the
+      // discriminant of this equation is D again.
+      const dfloat r0 = df_add(df_mul_f(df_mul(X, X), c.A), df_neg(df_mul(df_mul_f(Gc, c.s), Y)));
+      float dx = fdiv(-2.0f * r0.hi, 2.0f * c.A * c.xf + B + sq);
       double xn = x + (double)dx;
       float damp = __expf(-(kdf * xr + Hf) * dtf);
       float4 u = U[i];
@@ -1077,6 +1082,23 @@ PassArgs batch_args(rec_ctx* c, const StepCoef& k) {
   return a;
 }
 }  // namespace
+
+// Volume statistics of the current state (sums of the last rec_state_init,
+// rec_refresh or rec_step): X_e = sum delta x / sum delta (Sec. II.A).
+__global__ void k_volume_stats(const DevScalars* sc, const BoxDev* bxs, int B, rec_stats* st) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const DevScalars* s = bxs ? bxs[b].sc : sc;
+    st[b].X_e = s->Sdx / s->Sd;
+    st[b].lambda = s->lam_state;
+    st[b].S1s = s->S1s;
+  }
+}
+
+cudaError_t launch_volume_stats(rec_ctx* c, rec_stats* st) {
+  GroupTimer t(c, kTOther, 1);
+  k_volume_stats<<<1, 128, 0, c->stream>>>(c->sc, c->n_boxes > 1 ? c->bx : nullptr, c->n_boxes, st);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_refresh_batch(rec_ctx* c, double z) {
   StepCoef k = step_coef(c->cosmo, c->params, z + 1e-6 * (1.0 + z), z, 0);

@@ -547,17 +547,44 @@ __device__ __forceinline__ uint32_t wrap_step(uint32_t i, int s, uint32_t n) {
   return s > 0 ? (i + 1 == n ? 0 : i + 1) : (i == 0 ? n - 1 : i - 1);
 }
 
+// Path length along the ray at which the packet leaves its current cell: the
+// nearest face, ties broken x < y < z.
+template <class R>
+__device__ __forceinline__ R dda_exit(const Ray<R>& r, bool* ax0, bool* ax1, bool* ax2) {
+  *ax0 = r.tMx <= r.tMy && r.tMx <= r.tMz;
+  *ax1 = !*ax0 && r.tMy <= r.tMz;
+  *ax2 = !*ax0 && !*ax1;
+  return *ax0 ? r.tMx : (*ax1 ? r.tMy : r.tMz);
+}
+
+// Gas-frame resonance distance offset kappa n.U_c of a cell.
+template <class R, class V>
+__device__ __forceinline__ R doppler(const Ray<R>& r, const V& U) {
+  using A = Ar<R>;
+  return A::add(A::add(A::mul(r.knx, U.x), A::mul(r.kny, U.y)), A::mul(r.knz, U.z));
+}
+
+template <class R, bool P2>
+__device__ __forceinline__ void dda_advance(Ray<R>& r, bool ax0, bool ax1, bool ax2, R s_exit, uint32_t n);
+
 template <class R, bool P2 = false, class V>
 __device__ __forceinline__ int march_cell(Ray<R>& r, const V& Uc, uint32_t n) {
   using A = Ar<R>;
-  R dc = A::add(A::add(A::mul(r.knx, Uc.x), A::mul(r.kny, Uc.y)), A::mul(r.knz, Uc.z));
-  const bool ax0 = r.tMx <= r.tMy && r.tMx <= r.tMz;
-  const bool ax1 = !ax0 && r.tMy <= r.tMz;
-  const bool ax2 = !ax0 && !ax1;
-  const R s_exit = ax0 ? r.tMx : (ax1 ? r.tMy : r.tMz);
+  R dc = doppler(r, Uc);
+  bool ax0, ax1, ax2;
+  const R s_exit = dda_exit(r, &ax0, &ax1, &ax2);
   // resonance in this cell at path length u0 - kappa n.U_c: absorb unless beyond the exit
   if (A::sub(r.u0, dc) <= s_exit) return 1;
   if (r.kc >= kMaxCrossings) return 2;
+  dda_advance<R, P2>(r, ax0, ax1, ax2, s_exit, n);
+  return 0;
+}
+
+// The step across the exit face: periodic neighbour along the exit axis and
+// its next face distance.
+template <class R, bool P2>
+__device__ __forceinline__ void dda_advance(Ray<R>& r, bool ax0, bool ax1, bool ax2, R s_exit, uint32_t n) {
+  using A = Ar<R>;
   const uint32_t wx = wrap_step<P2>(r.ix, r.sx, n);
   const uint32_t wy = wrap_step<P2>(r.iy, r.sy, n);
   const uint32_t wz = wrap_step<P2>(r.iz, r.sz, n);
@@ -570,7 +597,6 @@ __device__ __forceinline__ int march_cell(Ray<R>& r, const V& Uc, uint32_t n) {
   r.tMy = ax1 ? tn : r.tMy;
   r.tMz = ax2 ? tn : r.tMz;
   ++r.kc;
-  return 0;
 }
 
 __device__ __forceinline__ void add_counters(DevScalars* sc, uint64_t ab, uint64_t cap, uint64_t cross) {
@@ -799,13 +825,22 @@ __global__ void __launch_bounds__(TT, emit_occupancy<R>()) k_emit(TransportArgs<
 // the warps advance through the super-tile buckets together and the cells
 // they touch stay close in memory; each warp refills its idle lanes from its
 // current chunk, so that lanes stay busy whatever the spread of path lengths.
-// Cells a lane marches between two votes of its warp (A/B on GB300 at 256^3:
-// 1 -> 8.11 ms, 2 -> 7.84, 4 -> 7.71-7.82, 8 -> 7.76; 4 keeps the batch at its best).
-constexpr int kMarchSteps = 4;
+// Cells a lane marches per round between two votes of its warp.  The walk of
+// the traversal does not depend on the velocities, so a round first steps the
+// traversal through its cells and gathers their velocities together, then runs
+// the resonance tests in order: the lane waits on memory once per round rather
+// than once per cell.  The arithmetic of every cell is the same as one cell at
+// a time; only the order of the loads changes.
+#ifndef REC_MARCH_AHEAD
+#define REC_MARCH_AHEAD 4
+#endif
+template <class R> struct MarchAhead { static constexpr int value = sizeof(R) == 4 ? REC_MARCH_AHEAD : 2; };
 
 // Resident blocks per SM of the march (register budget per thread; a batch
 // keeps the box of each lane's packet in registers).
-template <class R, bool MB> constexpr int march_occupancy() { return MB ? 4 : (sizeof(R) == 4 ? 5 : 4); }
+template <class R, bool MB> constexpr int march_occupancy() {
+  return MB ? 3 : (sizeof(R) == 4 ? (MarchAhead<R>::value > 4 ? 3 : MarchAhead<R>::value > 2 ? 4 : 5) : 3);
+}
 
 // P2: the box side is a power of two (cell index by shifts and masks).
 // MB: batched context; the lanes of a warp may hold packets of different boxes.
@@ -907,18 +942,42 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
       }
     }
     if (!__any_sync(0xffffffffu, active)) break;  // no packet left in the warp
-    // up to kMarchSteps cells per lane between the warp's refill and exit votes
+    if (active) {
+      // one round of kA cells: cell 0 is the current one (velocity in Uc); the
+      // walk records each cell's exit distance and gathers the velocity of the
+      // cell after it, then the cells are tested in order
+      constexpr int kA = MarchAhead<R>::value;
+      R se[kA];
+      V Un[kA];
+      uint32_t cl[kA + 1];
+      cl[0] = cell;
+      const uint32_t kc0 = r.kc;
 #pragma unroll
-    for (int u = 0; u < kMarchSteps; ++u) {
-      if (!active) break;
-      int res = march_cell<R, P2>(r, Uc, ln);
+      for (int k = 0; k < kA; ++k) {
+        bool ax0, ax1, ax2;
+        se[k] = dda_exit(r, &ax0, &ax1, &ax2);
+        dda_advance<R, P2>(r, ax0, ax1, ax2, se[k], ln);
+        cl[k + 1] = P2 ? (((r.iz << lg) | r.iy) << lg) | r.ix : (r.iz * ln + r.iy) * ln + r.ix;
+        Un[k] = lvel[cl[k + 1]];
+      }
+      int res = 0;
+      uint32_t kend = 0, cend = 0;
+#pragma unroll
+      for (int k = 0; k < kA; ++k) {
+        const R dc = doppler(r, k == 0 ? Uc : Un[k - 1]);
+        if (res == 0) {
+          // resonance in cell k at path length u0 - kappa n.U: absorb unless beyond its exit
+          if (Ar<R>::sub(r.u0, dc) <= se[k]) { res = 1; kend = (uint32_t)k; cend = cl[k]; }
+          else if (kc0 + (uint32_t)k >= kMaxCrossings) { res = 2; kend = (uint32_t)k; }
+        }
+      }
       if (res == 0) {
-        cell = P2 ? (((r.iz << lg) | r.iy) << lg) | r.ix : (r.iz * ln + r.iy) * ln + r.ix;
-        Uc = lvel[cell];
+        cell = cl[kA];
+        Uc = Un[kA - 1];
       } else {
         active = false;
-        my_cross += r.kc - 1;  // the first crossing was counted at emission
-        if (res == 1) { atomicAdd(ltally + cell, 1u); ++my_abs; }
+        my_cross += kc0 + kend - 1;  // crossings up to the last cell; the first was counted at emission
+        if (res == 1) { atomicAdd(ltally + cend, 1u); ++my_abs; }
         else ++my_cap;
       }
     }

@@ -132,17 +132,22 @@ __global__ void __launch_bounds__(NT) k_trb_start(TrbArgs a, StepCoef k) {
 }
 
 // Stage 1 explicit part x + (gamma h / 2) f(x_n), same for T; the iterate starts at the state.
-__global__ void __launch_bounds__(NT) k_trb_explicit1(TrbArgs a, StepCoef k, double h1) {
+// The weights w_i = J_i / <J> come from the tallies and the n_1s of the state at
+// the start of the step (first substep) and are held over its substeps, as in
+// the backward-Euler step.
+__global__ void __launch_bounds__(NT) k_trb_explicit1(TrbArgs a, StepCoef k, double h1, int first_sub) {
   const double Ga = a.s->Ga, Sa = a.s->Sa;
   const double tot = (double)a.sc->tally_total;
   for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.n3; i += (int64_t)gridDim.x * NT) {
     const double d = a.delta[i], x = a.x[i], T = a.T[i], n = k.nH * d;
     double w = 1.0;
-    if (a.tally_mode && tot > 0.0 && Sa > 0.0) {
+    if (!first_sub) {
+      w = a.w[i];
+    } else if (a.tally_mode && tot > 0.0 && Sa > 0.0) {
       const double n1s_rel = d * (1.0 - x);
       if (n1s_rel > 0.0) w = ((double)a.tally[i] / tot) * Sa / n1s_rel;
     }
-    a.w[i] = w;
+    if (first_sub) a.w[i] = w;
     const double fx = -alpha_e(k, T) * n * x * x + w * Ga * (1.0 - x);
     const double g = k.kc * x / (1.0 + k.fHe + x);
     const double hh = k.hq / (d * (1.0 + k.fHe + x));
@@ -152,10 +157,7 @@ __global__ void __launch_bounds__(NT) k_trb_explicit1(TrbArgs a, StepCoef k, dou
     a.xg[i] = x;
     a.Tg[i] = T;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.s->outer_done = 0;
-    a.s->bad = 0;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.s->outer_done = 0;
 }
 
 // Stage 2 explicit part (x_g / gamma - (1-gamma)^2 x_n / gamma) / (2 - gamma), same for T.
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(NT) k_trb_newton(TrbArgs a, StepCoef k, double
       const double lmin = lam_min(k, s, peebles(k, Sn, n3));
       if (!(ln > lmin)) ln = (lam > lmin) ? 0.5 * (lam + lmin) : lmin + fmax(fabs(lmin), fabs(lam));
       if (fabs(ln - lam) <= 1e-13 * fabs(lam) && fabs(Sn - S) <= 1e-13 * fabs(S)) s->newton_conv = 1;
-      if (R[5] > 0.0) s->bad = 1; else s->bad = 0;
+      if (R[5] > 0.0 && s->newton_conv) s->bad = 1;  // converged with a cell left without a positive root
       s->lam = ln;
       s->S = Sn;
       s->passes += 1;
@@ -439,7 +441,7 @@ cudaError_t launch_rec_step_trbdf2(rec_ctx* c, double z_from, double z_to, rec_s
     const StepCoef kg = step_coef(c->cosmo, c->params, zg, zg, 0);
     const StepCoef kb = step_coef(c->cosmo, c->params, zb, zb, sidx == ns - 1);
     k_trb_start<<<c->grid, NT, 0, c->stream>>>(a, ka);
-    k_trb_explicit1<<<c->grid, NT, 0, c->stream>>>(a, ka, 0.5 * gam * h);
+    k_trb_explicit1<<<c->grid, NT, 0, c->stream>>>(a, ka, 0.5 * gam * h, sidx == 0 ? 1 : 0);
     stage(c, a, kg, 0.5 * gam * h);
     k_trb_explicit2<<<c->grid, NT, 0, c->stream>>>(a, c1, c0);
     stage(c, a, kb, (1.0 - gam) / (2.0 - gam) * h);

@@ -108,6 +108,8 @@ def lib():
         L.lya_mc_scalars.argtypes = [P(Params), P(McParams), i32, P(d)]
         L.lya_mc_redistribution_host.argtypes = [d, d, P(d), C.c_uint64, C.c_int64, P(d), P(d), P(d),
                                                  P(C.c_uint64)]
+        L.lya_mc_mixing_fraction.argtypes = [vp, vp, C.c_uint64, P(d), i32, vp, vp]
+        L.rec_volume_stats.argtypes = [vp, vp]
         L.rec_free.argtypes = [vp]
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
@@ -115,7 +117,8 @@ def lib():
         for f in ("rec_init", "rec_state_init", "rec_refresh", "lya_transport", "rec_step", "rec_step_noalloc", "rec_graph_step", "rec_get_tuning", "rec_set_tuning",
                   "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times",
                   "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2", "lya_mc_scalars",
-                  "lya_mc_redistribution_host", "lya_voigt_mixed", "rec_set_f_alpha"):
+                  "lya_mc_redistribution_host", "lya_voigt_mixed", "rec_set_f_alpha", "lya_mc_mixing_fraction",
+                  "rec_volume_stats"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -173,21 +176,6 @@ def voigt(a: float, y, mixed=False) -> np.ndarray:
 
 
 MC_ARITH = {"fp64": 0, "mixed": 1}
-
-
-def mixing_fraction(records, D_kpc) -> np.ndarray:
-    """f_alpha(D) of Sec. III.B from Monte-Carlo records: the fraction of the
-    photons destroyed (photo-ionisation or two-photon decay) farther than D
-    (comoving kpc, scalar or array) from their emission point.  Photons lost
-    by redshifting or stopped by the step cap are not destroyed and do not
-    count.  Host post-processing of lya_scatter_mc's records."""
-    fate = np.asarray(records["fate"])
-    D = np.asarray(records["D_kpc"])[(fate == 1) | (fate == 2)]
-    Dq = np.atleast_1d(np.asarray(D_kpc, dtype=np.float64))
-    if D.size == 0:
-        return np.full(Dq.shape, np.nan)
-    Ds = np.sort(D)
-    return 1.0 - np.searchsorted(Ds, Dq, side="right") / Ds.size
 
 
 def mc_redistribution_mixed(a, y, seed, m, kin=(0.0, 0.0, 1.0)):
@@ -296,6 +284,10 @@ class Batch:
         self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, C.c_void_p(self._stats.data_ptr())),
                     "rec_graph_step")
 
+    def volume_stats(self):
+        """rec_volume_stats: X_e, lambda and S1s of every box's current state into the records."""
+        self._check(lib().rec_volume_stats(self.ctx, C.c_void_p(self._stats.data_ptr())), "rec_volume_stats")
+
     def timing(self, enable=True):
         self._check(lib().rec_timing(self.ctx, 1 if enable else 0), "rec_timing")
 
@@ -396,6 +388,7 @@ class Box:
         if rc != REC_OK:
             raise RecError(f"rec_init: {lib().rec_last_error(None).decode()} (status {rc})")
         self.ctx = ctx
+        self.mc_records = None
 
     # ---- calls -----------------------------------------------------------------------
     def _check(self, rc, what):
@@ -428,6 +421,10 @@ class Box:
     def graph_step(self, step, z_from, z_to, slot=0):
         """transport(step, z_from) + step(step, z_from, z_to) as one CUDA graph launch."""
         self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_graph_step")
+
+    def volume_stats(self, slot=0):
+        """rec_volume_stats: X_e, lambda and S1s of the current state into record `slot`."""
+        self._check(lib().rec_volume_stats(self.ctx, self._slot(slot)), "rec_volume_stats")
 
     def set_f_alpha(self, f_alpha):
         """Partial mixing: the share of the full-mixing rate for the following steps."""
@@ -477,12 +474,35 @@ class Box:
             st = torch.zeros(C.sizeof(McStats), dtype=torch.uint8, device=dev)
         ptr = lambda t: None if t is None or t.numel() == 0 else C.c_void_p(t.data_ptr())
         self._check(lib().lya_scatter_mc(self.ctx, C.byref(mp), ptr(pre), ptr(rec), ptr(st)), "lya_scatter_mc")
+        self.mc_records = rec if records else None  # device copy, for mixing_fraction
         self.stream.synchronize()
         s = McStats.from_buffer_copy(st.cpu().numpy().tobytes())
         stats = dict(count=[int(v) for v in s.count], sampler_caps=int(s.sampler_caps), steps=int(s.steps),
                      scatterings=int(s.scatterings), nonfinite=int(s.nonfinite))
         out = rec.cpu().numpy().view(MC_PHOTON) if records else None
         return out, stats
+
+    def mixing_fraction(self, D_kpc, records=None):
+        """f_alpha(D) of Sec. III.B (lya_mc_mixing_fraction) from the device records
+        of the last scatter_mc call (or a device uint8 tensor of records).
+        Returns (f, f_min, f_max, counts): f excludes capped photons, [f_min, f_max]
+        is the range their unknown fates allow, counts the photons per fate."""
+        torch = self.torch
+        recs = self.mc_records if records is None else records
+        if recs is None or recs.numel() == 0:
+            raise RecError("no device Monte-Carlo records: run scatter_mc(records=True) first")
+        n_ph = recs.numel() // MC_PHOTON.itemsize
+        D = np.ascontiguousarray(np.atleast_1d(D_kpc), dtype=np.float64)
+        with torch.cuda.stream(self.stream):
+            out = torch.empty(3 * D.size, dtype=torch.float64, device=recs.device)
+            cnt = torch.empty(4, dtype=torch.int64, device=recs.device)
+        self._check(lib().lya_mc_mixing_fraction(self.ctx, C.c_void_p(recs.data_ptr()), int(n_ph),
+                                                 D.ctypes.data_as(C.POINTER(C.c_double)), int(D.size),
+                                                 C.c_void_p(out.data_ptr()), C.c_void_p(cnt.data_ptr())),
+                    "lya_mc_mixing_fraction")
+        self.stream.synchronize()
+        o = out.cpu().numpy().reshape(3, D.size)
+        return o[0], o[1], o[2], cnt.cpu().numpy().astype(np.uint64)
 
     TIMER_GROUPS = ("alloc", "emit", "march", "transport_end", "rec_step", "adjoint", "other")
 

@@ -134,8 +134,14 @@ def apply_table(obj, key, path=TABLE):
     entry = load_table(path).get(key)
     if not entry:
         return None
-    obj.set_tuning(**{f: entry["setting"][f] for f in FIELDS})
-    return entry["setting"]
+    # a stored grid above the kernels' current residency limit (the defaults
+    # after rec_init are those limits) is clamped to it
+    cur = obj.tuning()
+    setting = {f: entry["setting"][f] for f in FIELDS}
+    for f in ("emit_blocks_per_sm", "march_blocks_per_sm"):
+        setting[f] = min(setting[f], cur[f])
+    obj.set_tuning(**setting)
+    return setting
 
 
 def main():

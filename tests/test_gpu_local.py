@@ -137,22 +137,38 @@ def test_partial_mode_rejections():
     box.close()
 
 
-@pytest.mark.skip(reason="rec_set_f_alpha has not been run on a GPU yet")
-def test_set_f_alpha_equals_a_context_made_with_it(cosmo):
+@pytest.mark.parametrize("f_new", [0.4, 0.0, 1.0])
+def test_set_f_alpha_equals_a_context_made_with_it(cosmo, f_new):
     """Changing the partial-mixing share on a context gives the step of a
-    context created with that share (Sec. V's redshift-dependent f_alpha)."""
+    context created with that share (Sec. V's redshift-dependent f_alpha),
+    including the two ends: 0 (the local limit) and 1 (full mixing)."""
     from gpu_helpers import make_fields
     from paper_2312_11448_gb300 import rec
     d, U = make_fields(12, 0.8, 3.0, seed=1)
     a = rec.Box(12, d, U, 1000, precision="fp64", mixing="partial", seed=7, f_alpha=0.9)
-    b = rec.Box(12, d, U, 1000, precision="fp64", mixing="partial", seed=7, f_alpha=0.4)
+    b = rec.Box(12, d, U, 1000, precision="fp64", mixing="partial", seed=7, f_alpha=f_new)
     for box in (a, b):
         box.state_init(1300.0)
-    a.set_f_alpha(0.4)
-    a.step(0, 1300.0, 1290.0)
-    b.step(0, 1300.0, 1290.0)
+    a.step(0, 1300.0, 1295.0)
+    b.set_f_alpha(0.9)
+    b.step(0, 1300.0, 1295.0)
+    a.set_f_alpha(f_new)
+    b.set_f_alpha(f_new)
+    a.step(1, 1295.0, 1290.0)
+    b.step(1, 1295.0, 1290.0)
     for name in ("x", "T", "vel4", "emis"):
         assert np.array_equal(a.host(name), b.host(name)), name
+    # and against the oracle's partial step at the new share
+    c = rec.Box(12, d, U, 1000, precision="fp64", mixing="partial", seed=7, f_alpha=f_new)
+    c.state_init(1300.0)
+    dd, UU, _ = oracle_fields(c)
+    x0 = c.host("x")
+    T0 = c.host("T").astype(np.float64)
+    c.close()
+    x1, T1, U1, e1, so = O.rec_step(cosmo, 12, 1300.0, 1295.0, dd, x0, T0, U=UU, mixing="partial", f_alpha=0.9)
+    x2, T2, U2, e2, so = O.rec_step(cosmo, 12, 1295.0, 1290.0, dd, x1, T1, U=U1, mixing="partial", f_alpha=f_new)
+    np.testing.assert_allclose(a.host("x"), x2, rtol=TOL["fp64"], atol=0)
+    np.testing.assert_allclose(a.host("T"), T2, rtol=TOL["fp64"], atol=0)
     with pytest.raises(rec.RecError, match="0, 1"):
         a.set_f_alpha(1.2)
     full = rec.Box(8, d[:512], U[:512], 10, precision="fp64", mixing="full")

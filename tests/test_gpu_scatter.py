@@ -175,10 +175,8 @@ def test_rejected_arguments():
 
 
 # ---- mixed-arithmetic form (statistical parity) ---------------------------------
-_NOT_YET_RUN = pytest.mark.skip(reason="the mixed-arithmetic kernel has not been run on a GPU yet")
 
 
-@_NOT_YET_RUN
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_mixed_arith_statistics_match_oracle(cosmo, precision):
     """Fate fractions (binomial) and the distributions of scattering counts,
@@ -203,8 +201,15 @@ def test_mixed_arith_statistics_match_oracle(cosmo, precision):
     box.close()
 
 
-@_NOT_YET_RUN
 def test_mixed_arith_peebles_factor(cosmo):
+    """Fig. Cfact with the mixed-arithmetic kernel: C = p_alpha f_z from 32768
+    photons per expansion rate (a) equals the binary64 kernel's C on
+    independent photons (two-sample binomial test, 5 sigma) and (b) follows
+    R / (beta + R) of Eq. Cfactor within 4 sigma plus 3 % of C.  At this sample
+    size both arithmetic forms resolve a deficit of about 2 % below that
+    Sobolev-limit formula at zeta >= 1e4 (the same in both forms, at eps = 0.1
+    and 0.03, up to zeta = 1e5), so the allowance is a property of the
+    Monte Carlo, not of the arithmetic."""
     n, z, xe = 4, 1700.0, 0.5
     box = _box(n, "mixed", np.ones(n ** 3), np.zeros((n ** 3, 3)))
     set_state(box, np.full(n ** 3, xe), np.full(n ** 3, 4000.0))
@@ -212,12 +217,20 @@ def test_mixed_arith_peebles_factor(cosmo):
     n1s = bg["nH"] * (1 - xe)
     beta = O.rates(cosmo, z, bg["Tg"])["beta"]
     A = O.A_2P1S
+    Np = 32768
     for zeta in (3e3, 1e4, 3e4):
-        _, st = box.scatter_mc(z, 32768, records=False, zeta=zeta, lambda2g=0.0, arith="mixed",
-                               x_lost=50 * _x50(cosmo, z, zeta, n1s), max_steps=2_000_000)
-        N = 32768 - st["count"][3]
+        kw = dict(records=False, zeta=zeta, lambda2g=0.0, x_lost=50 * _x50(cosmo, z, zeta, n1s),
+                  max_steps=2_000_000)
+        C = {}
+        for arith, step in (("mixed", 0), ("fp64", 1)):
+            _, st = box.scatter_mc(z, Np, arith=arith, step=step, **kw)
+            N = Np - st["count"][3]
+            assert st["count"][3] <= 8 and st["count"][1] == 0 and st["nonfinite"] == 0
+            C[arith] = (3 * A / (beta + 3 * A) * st["count"][0] / N, N)
         R = 8 * np.pi * zeta * bg["H"] / (LAMBDA_A ** 3 * n1s)
         C_th = R / (beta + R)
-        C_mc = 3 * A / (beta + 3 * A) * st["count"][0] / N
-        assert C_mc == pytest.approx(C_th, abs=4 * np.sqrt(C_th * (1 - C_th) / N)), zeta
+        (cm, Nm), (cf, Nf) = C["mixed"], C["fp64"]
+        p = 0.5 * (cm + cf)
+        assert abs(cm - cf) < 5 * np.sqrt(p * (1 - p) * (1 / Nm + 1 / Nf)), zeta
+        assert cm == pytest.approx(C_th, abs=4 * np.sqrt(C_th * (1 - C_th) / Nm) + 0.03 * C_th), zeta
     box.close()

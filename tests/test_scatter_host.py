@@ -107,30 +107,3 @@ def test_mixed_form_voigt(a):
     got = rec.voigt(a, y, mixed=True)
     ref = wofz(y.astype(np.float32).astype(np.float64) + 1j * np.float32(a)).real
     assert np.max(np.abs(got / ref - 1)) < 2e-6
-
-
-def test_mixing_fraction_definition():
-    """f_alpha(D): destroyed photons (two-photon decay or photo-ionisation)
-    farther than D, over all destroyed photons; lost and capped photons ignored."""
-    from paper_2312_11448_gb300 import rec
-    rec_ = np.zeros(7, dtype=rec.MC_PHOTON)
-    rec_["fate"] = [0, 1, 2, 2, 3, 1, 2]
-    rec_["D_kpc"] = [9.0, 0.1, 0.5, 2.0, 9.0, 3.5, 0.5]
-    f = rec.mixing_fraction(rec_, [0.0, 0.3, 0.5, 1.0, 3.0, 4.0])
-    np.testing.assert_allclose(f, [5 / 5, 4 / 5, 2 / 5, 2 / 5, 1 / 5, 0.0])
-
-
-def test_mixing_fraction_on_oracle_photons():
-    import oracle as O
-    from paper_2312_11448_gb300 import rec
-    cp = O.default_cosmo()
-    mp = O.mc_params(1700.0, zeta=3e3, lambda2g=3e4, seed=3)
-    S = O.mc_setup(cp, mp, 2)
-    mp.x_lost = 50 * (S["sig0"] * S["a"] * 0.5 * S["nH"] / (np.sqrt(np.pi) * S["dxdl"])) ** (1 / 3)
-    P = (np.arange(9) * 32).astype(np.uint32)
-    recs, cnt = O.lya_mc(cp, mp, 2, np.ones(8), np.full(8, 0.5), P, threads=4)
-    D = np.logspace(-6, 0, 25)
-    f = rec.mixing_fraction(recs, D)
-    assert np.all(np.diff(f) <= 0) and f[0] <= 1.0 and f[-1] >= 0.0
-    dest = recs["D_kpc"][(recs["fate"] == 1) | (recs["fate"] == 2)]
-    assert f[10] == pytest.approx(np.mean(dest > D[10]))

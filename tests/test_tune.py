@@ -46,12 +46,19 @@ def test_workload_keys_and_table(tmp_path):
     assert tune.load_table(str(tmp_path / "missing.json")) == {}
 
     class Fake:
-        def __init__(self):
+        def __init__(self, limit=5):
             self.set = None
+            self.limit = limit
+
+        def tuning(self):  # defaults after rec_init: the residency limits
+            return dict(_start(), emit_blocks_per_sm=self.limit, march_blocks_per_sm=self.limit)
 
         def set_tuning(self, **kw):
             self.set = kw
 
     f = Fake()
     assert tune.apply_table(f, "k", str(p)) == _start() and f.set == _start()
+    # a stored grid above the kernels' current limit is clamped to it
+    f = Fake(limit=4)
+    assert tune.apply_table(f, "k", str(p)) == dict(_start(), emit_blocks_per_sm=4, march_blocks_per_sm=4)
     assert tune.apply_table(f, "absent", str(p)) is None
