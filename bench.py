@@ -154,7 +154,7 @@ def algorithmic_bytes(precision, n3, emitted, queued, crossings, newton_passes):
            T, tally; final pass reads delta, x_e (+ cache), T, tally, velocity and
            writes x_e (+ cache), T, velocity, emission, tally."""
     if precision == "mixed":
-        v, t, d, e, qe = 16, 4, 4, 4, 48
+        v, t, d, e, qe = 16, 4, 4, 4, 32
     else:
         v, t, d, e, qe = 32, 8, 8, 8, 96
     home = emitted - queued
@@ -348,8 +348,11 @@ def traj_k(S):
 def time_batched(W, K, prep=60, n_boxes=64):
     """The batched workload: 64 boxes with sides uniform in {32,48,64,96,128},
     sigma_lnrho uniform in [0.1, 1.5], 1e6 packets per 32^3 scaled by volume,
-    mixed form, tally mixing, z 1600 -> 700 in 200 steps; one context, one
-    launch per phase for all boxes.  Timed after `prep` + W untimed steps."""
+    mixed form, tally mixing, z 1600 -> 700 in 200 steps; one context: a step
+    is three launches for all boxes (persistent allocation + emission, march,
+    persistent rec_step).  Timed after `prep` + W untimed steps, K steps with
+    kernel timing (per-group times), then K steps as captured CUDA graphs
+    (rec_graph_step), the line's value."""
     import torch
     from paper_2312_11448_gb300 import rec
     from paper_2312_11448_gb300.inputs import batched_configs, make_box as fields, z_schedule
@@ -359,7 +362,7 @@ def time_batched(W, K, prep=60, n_boxes=64):
         d, U = fields(c, seed=100 + i)
         boxes.append((c.n, d, U, c.n_packets))
     zs = z_schedule(cfgs[0].z_start, cfgs[0].z_end, cfgs[0].n_steps)
-    batch = rec.Batch(boxes, precision="mixed", mixing="tally", seed=7)
+    batch = rec.Batch(boxes, precision="mixed", mixing="tally", seed=7, stream=torch.cuda.Stream())
     del boxes
     from paper_2312_11448_gb300 import tune
     tuned = tune.apply_table(batch, tune.batch_key(n_boxes, "mixed"))
@@ -379,8 +382,21 @@ def time_batched(W, K, prep=60, n_boxes=64):
         batch.step(s, zs[s], zs[s + 1])
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms_direct = e0.elapsed_time(e1)
     kt = batch.kernel_times()
+    batch.timing(False)
+    # the same steps as one captured graph per step (executable graph updated in place)
+    s0 = prep + W + K
+    batch.graph_step(s0, zs[s0], zs[s0 + 1])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(K):
+        s = s0 + 1 + k
+        batch.graph_step(s, zs[s], zs[s + 1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    batch.sync()  # raises if a bounded device-side wait expired
     st = batch.stats()
     emitted = sum(r["emitted"] for r in st)
     flags = 0
@@ -397,6 +413,8 @@ def time_batched(W, K, prep=60, n_boxes=64):
                          f"per 32^3 scaled by volume, mixed form, tally mixing, steps {prep + W}+ of 200 "
                          f"(z 1600->700), one context"),
             "value": cells * K / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / K, "steps": K,
+            "api": "rec_graph_step: one CUDA graph per step (3 kernels), executable graph updated in place",
+            "direct_ms_per_step": ms_direct / K,
             "warmup": W, "cells": cells, "packets_per_step": emitted,
             "packets_per_s": emitted * K / (ms * 1e-3),
             "kernel_ms_per_step": {g: v[0] / K for g, v in kt.items() if v[1]},

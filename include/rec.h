@@ -141,9 +141,13 @@ typedef struct {
 
 /* Create a context for n_boxes independent boxes (1 <= n_boxes <= 128), each
  * with its own side, fields and packet count; all share params (cosmology,
- * precision form, mixing mode, seed).  With n_boxes > 1 every phase of a call
- * (allocation, emission, march, each rec_step pass) is one launch over all
- * boxes; box b draws its random numbers with box index b in the Philox counter
+ * precision form, mixing mode, seed).  With n_boxes > 1 the work of all boxes
+ * is done together: lya_transport is one persistent cooperative launch for the
+ * allocation and the emission (its phases separated by grid barriers whose
+ * waits are bounded, see rec_set_wait_limit) followed by the march, and
+ * rec_step is one persistent cooperative launch per substep (the Newton
+ * evaluations and the final pass as its phases), so a step is three launches;
+ * box b draws its random numbers with box index b in the Philox counter
  * (box 0 therefore reproduces a single-box context bit for bit), keeps its own
  * sums, lambda and Newton state, and the dev_stats arguments of lya_transport
  * and rec_step point to n_boxes records, one per box.  The adjoint entry points
@@ -275,6 +279,27 @@ rec_status rec_xe_adjoint(rec_ctx* ctx, const double* x, double Xe_bar, double* 
  * rec_refresh or rec_step; the other fields of the records are left as they are.
  * Errors: REC_EINVAL, REC_ESTATE (no sums yet), REC_ECUDA. */
 rec_status rec_volume_stats(rec_ctx* ctx, rec_stats* dev_stats);
+
+/* Bound of the device-side waits (no counterpart in the paper).  Every wait
+ * inside a kernel is bounded: a bulk-copy stage of the per-cell passes is
+ * looked at once without blocking, then polled at most `polls` times (default
+ * 2^22, about a second); past that the block records the expiry (rec_stats
+ * flags bit 3) and returns without finishing its share of the pass.  The wait
+ * for its copies still in flight before such a return keeps the default bound.
+ * The grid barriers between the phases of the persistent batched launches
+ * (see rec_init) poll at most `polls` times as well.  0 makes every such wait
+ * give up at once, which is how the error path is tested.  Host-side only: takes effect from the next call
+ * enqueued.  Errors: REC_EINVAL (NULL context). */
+rec_status rec_set_wait_limit(rec_ctx* ctx, uint32_t polls);
+
+/* Waits for the context stream and reports the device-side failures of the
+ * calls enqueued since the last rec_sync: REC_ETIMEOUT if a bounded wait
+ * expired (see rec_set_wait_limit).  The state those calls left is then
+ * incomplete: re-initialise it (zero the tallies; rec_state_init, or write x_e
+ * and T and call rec_refresh) before stepping again; rec_sync clears the expiry and the
+ * device counters a pass that gave up may have left part-way, so the context
+ * stays usable.  Errors: REC_ETIMEOUT, REC_ECUDA. */
+rec_status rec_sync(rec_ctx* ctx);
 
 /* Objective on an X_e history over node redshifts zs[0..n_nodes-1] (decreasing),
  * host computation.  objective 1: X_e at the node nearest z_star.  objective 2:

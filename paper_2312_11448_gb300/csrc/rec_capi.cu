@@ -165,7 +165,7 @@ rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_
   c->alloc_blocks = c->tot_ablk;
   const size_t qbytes = (size_t)params->n_quantiles * (mixed ? 4 : 8);
   const size_t part_n = std::max<size_t>(2 * (size_t)rec::kMaxSums * c->tot_pblk, (size_t)rec::kMaxSums * c->tot_ablk);
-  const size_t qentry = mixed ? 48 : 96;
+  const size_t qentry = mixed ? 32 : 96;  // two float4 | three double4 per queued packet
   e = cudaMalloc(&c->sc, sizeof(rec::DevScalars) * n_boxes);
   if (e == cudaSuccess) e = cudaMalloc(&c->gsc, sizeof(rec::DevScalars));
   if (e == cudaSuccess) e = cudaMalloc(&c->sc_adj, sizeof(rec::DevScalars));
@@ -276,7 +276,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   size_t qbytes = (size_t)params->n_quantiles * (params->precision == REC_PREC_MIXED ? 4 : 8);
   e = cudaMalloc(&c->sc, sizeof(rec::DevScalars));
   if (e == cudaSuccess) e = cudaMalloc(&c->sc_adj, sizeof(rec::DevScalars));
-  // block partials, double-buffered for the cooperative substep
+  // block partials (two per block: the TMA-staged passes run more blocks than the grid)
   if (e == cudaSuccess) e = cudaMalloc(&c->part, 2 * sizeof(double) * rec::kMaxSums * (size_t)c->grid);
   if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(uint32_t) * (size_t)(c->n3 + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->partQ, sizeof(unsigned long long) * (size_t)c->alloc_blocks);
@@ -293,8 +293,8 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
     if (e == cudaSuccess) e = cudaMalloc(&c->cpre, sizeof(unsigned long long) * (nb + 1));
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->quant, qbytes);
-  // march queue: three float4 (mixed) or double4_32a (FP64) per packet, worst case all packets
-  size_t qentry = params->precision == REC_PREC_MIXED ? 48 : 96;
+  // march queue: two float4 (mixed) or three double4_32a (FP64) per packet, worst case all packets
+  size_t qentry = params->precision == REC_PREC_MIXED ? 32 : 96;
   if (e == cudaSuccess) e = cudaMalloc(&c->queue, qentry * (size_t)std::max<uint64_t>(b.n_packets, 1));
   if (e != cudaSuccess) {
     rec_status r = (e == cudaErrorMemoryAllocation) ? fail(nullptr, REC_ENOMEM, "device allocation failed")
@@ -403,10 +403,6 @@ rec_status rec_graph_step(rec_ctx* c, int32_t step, double z_from, double z_to, 
   cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamIsCapturing");
   if (cs != cudaStreamCaptureStatusNone) return fail(c, REC_EINVAL, "the context stream is already being captured");
-  if (c->coop_grid == 0) {  // resolve the substep launch mode outside the capture
-    const char* sel = std::getenv("REC_SUBSTEP");
-    if (!(sel && std::strcmp(sel, "coop") == 0)) c->coop_grid = -1;
-  }
   e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
   c->capturing = true;
@@ -659,6 +655,23 @@ rec_status lya_mc_mixing_fraction(rec_ctx* c, const lya_mc_photon* dev_photons, 
   cudaError_t e = rec::run_mixing_fraction(c, dev_photons, n_photons, D_kpc, m, dev_out, dev_counts);
   if (e == cudaErrorMemoryAllocation) return fail(c, REC_ENOMEM, "mixing-fraction counters");
   if (e != cudaSuccess) return cuda_fail(c, e, "lya_mc_mixing_fraction");
+  return REC_OK;
+}
+
+rec_status rec_set_wait_limit(rec_ctx* c, uint32_t polls) {
+  if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");
+  c->wait_limit = polls;
+  return REC_OK;
+}
+
+rec_status rec_sync(rec_ctx* c) {
+  if (!c) return fail(nullptr, REC_EINVAL, "context is NULL");
+  int timed_out = 0;
+  cudaError_t e = rec::launch_check_waits(c, &timed_out);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rec_sync");
+  if (timed_out)
+    return fail(c, REC_ETIMEOUT,
+                "a bounded device-side wait expired: the state of the calls since the last rec_sync is incomplete");
   return REC_OK;
 }
 

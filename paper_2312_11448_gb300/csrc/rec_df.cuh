@@ -52,19 +52,35 @@ __device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
 }
 
 // Split a binary64 value into hi + lo with integer operations only (no
-// binary64 arithmetic or conversion): hi takes the sign, the exponent and the
-// leading 24 significand bits, lo the remaining 29 bits (rounded to 24).
-// Exact to 2^-48 relative for 2^-74 <= |x| < 2^127; outside that range (not
-// reached by ionisation fractions) it falls back to a rounded conversion.
+// binary64 arithmetic or conversion, which issue on the slow binary64 pipe):
+// hi takes the sign, the exponent and the leading 24 significand bits, lo the
+// remaining 29 bits (rounded to 24).  Exact to 2^-48 relative for
+// 2^-74 <= |x| < 2^127.  Below that range the result is 0 (ionisation
+// fractions never get there); above it, infinities and NaN give a NaN.
 __device__ __forceinline__ dfloat df_from_double(double x) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
-  if (e < 949u || e > 1150u) return {__double2float_rn(x), 0.0f};
   const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-  const float hi = __uint_as_float(sign | ((e - 896u) << 23) | ((uint32_t)(b >> 29) & 0x7fffffu));
-  const float scale = __uint_as_float((e - 948u) << 23);  // 2^(e - 1075)
-  const float lo = __fmul_rn(__uint2float_rn((uint32_t)b & 0x1fffffffu), scale);
-  return {hi, sign ? -lo : lo};
+  const uint32_t ec = e < 949u ? 949u : (e > 1150u ? 1150u : e);
+  float hi = __uint_as_float(sign | ((ec - 896u) << 23) | ((uint32_t)(b >> 29) & 0x7fffffu));
+  const float scale = __uint_as_float((ec - 948u) << 23);  // 2^(e - 1075)
+  float lo = __fmul_rn(__uint2float_rn((uint32_t)b & 0x1fffffffu), scale);
+  lo = sign ? -lo : lo;
+  if (e < 949u) { hi = 0.0f; lo = 0.0f; }
+  if (e > 1150u) { hi = __uint_as_float(0x7fc00000u); lo = 0.0f; }
+  return {hi, lo};
+}
+
+// A binary32 value as binary64, exactly, with integer operations only (zero
+// and subnormal inputs give zero; infinities and NaN keep their class).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint64_t mant = (uint64_t)(u & 0x7fffffu) << 29;
+  const uint64_t ed = e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u);
+  const uint64_t bits = e == 0u ? sign : (sign | (ed << 52) | mant);
+  return __longlong_as_double((long long)bits);
 }
 
 // hi + lo rounded to one binary32 value

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "rec.h"
+#include "rec_grid.cuh"
 
 namespace rec {
 
@@ -26,6 +27,8 @@ constexpr int kAllocItems = 16;        // consecutive cells per thread in the al
 // bucket arrays are sized for it; the side in use is a tuning parameter).
 constexpr uint32_t kMinTile = 8;
 constexpr int kAllocChunk = kAllocThreads * kAllocItems;
+// Polls of a bounded device-side wait before it gives up (about a second).
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;
 
 // Device-resident scalars of one box.  Everything data-dependent stays on the
 // device so that calls never synchronise with the host.
@@ -56,6 +59,7 @@ struct DevScalars {
   unsigned long long march_next;   // next queue chunk handed to a march warp
   uint32_t alloc_counter;
   int32_t emis_valid;
+  GridBarrier bar;  // grid barrier of the persistent batched launches (batch-wide record)
 };
 
 // Batched contexts (several boxes in one context, one launch per phase for
@@ -144,9 +148,10 @@ struct rec_ctx {
   void* quant;               // emission-profile table (float or double) [n_quantiles]
   int grid;                  // blocks of the streaming passes
   int alloc_blocks;
-  int coop_grid = 0;         // blocks of the cooperative substep kernel (0: not yet queried, -1: unavailable)
   int newton_tma = 0;        // TMA-staged Newton pass usable (0: not yet queried, 1 / -1)
-  void* queue;               // queued packets of the march (3 x 16|32 B each) [n_packets]
+  int batch_step_grid = 0;   // resident blocks of the persistent batched substep (0: not queried, -1: none)
+  int batch_front_grid = 0;  // resident blocks of the persistent batched transport front (same)
+  void* queue;               // queued packets of the march (2 x 16 B binary32, 3 x 32 B binary64) [n_packets]
   int sm_count;
   bool emis_ready;
   std::string err;
@@ -179,6 +184,8 @@ struct rec_ctx {
   size_t trb_bytes = 0;
   // mixing fraction of Monte-Carlo records (lya_mc_mixing_fraction): counters
   void* mf_cnt = nullptr;
+  // polls before a bounded device-side wait gives up (rec_set_wait_limit)
+  uint32_t wait_limit = rec::kDefaultWaitLimit;
 };
 
 namespace rec {
@@ -227,6 +234,9 @@ cudaError_t launch_refresh(rec_ctx* c, double z);
 cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* st);
 // X_e, lambda and S_1s of the current state of every box into st.
 cudaError_t launch_volume_stats(rec_ctx* c, rec_stats* st);
+// Synchronises the stream; *timed_out = 1 if a bounded device wait expired
+// since the last check (flags bit 3 of any box), clearing it and the counters.
+cudaError_t launch_check_waits(rec_ctx* c, int* timed_out);
 // Context-free FP64 step on static device scratch; no device allocation.
 rec_status launch_rec_step_noalloc(const rec_params& p, const rec_box& b, double z_from, double z_to,
                                    cudaStream_t stream, rec_stats* st, std::string* why);

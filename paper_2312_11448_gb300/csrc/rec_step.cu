@@ -26,13 +26,9 @@
 #include <cstring>
 #include <mutex>
 
-#include <cooperative_groups.h>
-
 #include "rec_df.cuh"
 #include "rec_internal.cuh"
 #include "rec_reduce.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace rec {
 namespace {
@@ -147,17 +143,23 @@ __device__ __forceinline__ CellF32 cell_f32(const CoefF32& f, int mixing, float 
 
 // Roots in both forms: x' = 2c/(B + sqrt(D)) and y' = 1 - x' = 2(A + y)/(2A + B + sqrt(D)),
 // D = B^2 + 4Ac; neither subtracts.  d x'/dG = s (1 - x') / (2 A x' + B) = s y' / sqrt(D).
-// These feed the Newton sums, whose difference F = S0 - lambda S1 cancels, so
-// they use correctly rounded division and square root.
+// They feed the Newton sums for lambda.  A few ulp of binary32 in each term
+// move the root lambda by a relative few 1e-7 (the form's tolerance is 1e-4),
+// so the square root and the three quotients use the hardware approximations
+// (reciprocal square root, reciprocal): the evaluation pass is bound by its
+// instruction count, and the correctly rounded forms cost about four times as
+// many instructions.
 __device__ __forceinline__ void root_f32(float A, float s, float G, float x, float y, float* xr, float* yr,
                                          float* dxdG) {
   float sG = s * G;
   float B = 1.0f + sG;
   float cc = x + sG;
-  float sq = __fsqrt_rn(B * B + 4.0f * A * cc);
-  *xr = __fdiv_rn(2.0f * cc, B + sq);
-  *yr = __fdiv_rn(2.0f * (A + y), 2.0f * A + B + sq);
-  if (dxdG) *dxdG = __fdiv_rn(s * (*yr), sq);
+  const float D = B * B + 4.0f * A * cc;
+  const float rs = rsqrtf(D);
+  const float sq = D * rs;
+  *xr = fdiv(2.0f * cc, B + sq);
+  *yr = fdiv(2.0f * (A + y), 2.0f * A + B + sq);
+  if (dxdG) *dxdG = s * (*yr) * rs;
 }
 
 // -------------------------------------------------------------- kernels
@@ -280,6 +282,80 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
   block_sum<3, NT>(v);
 }
 
+// Scalars of the mixed form's final pass at the converged lambda.
+struct FinalMixed {
+  CoefF32 f;
+  float Gf, wscale, kdf, Hf, dtf;
+  dfloat Gd;
+};
+__device__ __forceinline__ FinalMixed final_mixed_setup(const PassArgs& a, double G, double tot, double S1s) {
+  FinalMixed m;
+  m.f = coef_f32(a.k);
+  m.Gf = (float)G;
+  m.wscale = tot > 0.0 ? (float)(S1s / tot) : 0.0f;
+  m.kdf = (float)a.k.kd;
+  m.Hf = (float)a.k.H;
+  m.dtf = (float)a.k.dt;
+  m.Gd = df_from_double(G);
+  return m;
+}
+
+// One cell of the mixed form's final pass: x' (binary64 state by its
+// increment), its binary32 cache (x', 1 - x'), T', the drag-damped velocity,
+// the emission weight and the tally reset, from the cell's inputs d, x, T,
+// tally and velocity; adds the cell to the sums of the new state.
+template <bool PART>
+__device__ __forceinline__ void final_cell_mixed(const PassArgs& a, const FinalMixed& m, bool zero_tally, int64_t i,
+                                                 float d, double x, float Tin, uint32_t tal, float4 u, Kahan32& s0,
+                                                 Kahan32& s1, Kahan32& s2) {
+  const CoefF32& f = m.f;
+  // the state and 1 - x as double-float pairs, from the bits of x
+  const dfloat X = df_from_double(x);
+  const dfloat Y = df_add(dfloat{1.0f, 0.0f}, df_neg(X));
+  CellF32 c = cell_f32(f, a.k.mixing, d, make_float2(df_to_float(X), df_to_float(Y)), Tin,
+                       (a.k.mixing == REC_MIX_TALLY) ? tal : 0u, m.wscale);
+  float Gcf = m.Gf;
+  dfloat Gc = m.Gd;
+  if (PART) {
+    const float fm = (float)a.fmix;
+    const float Ci = local_C_f32(a.k, ((const float*)a.div)[i], c.n * c.yf);
+    c.A *= fm + (1.0f - fm) * Ci;
+    c.s = f.dt * fm;
+    const float go = ((1.0f - fm) / fm) * Ci * (float)(a.k.beta * a.k.ea);
+    Gcf = m.Gf + go;
+    Gc = df_add(m.Gd, dfloat{go, 0.0f});
+  }
+  // binary32 roots x' and y' = 1 - x' (both without cancellation) and the
+  // discriminant D = B^2 + 4 A c
+  float sGf = c.s * Gcf;
+  float B = 1.0f + sGf;
+  float sq = __fsqrt_rn(B * B + 4.0f * c.A * (c.xf + sGf));
+  float xr = __fdiv_rn(2.0f * (c.xf + sGf), B + sq);
+  float yr = __fdiv_rn(2.0f * (c.A + c.yf), 2.0f * c.A + B + sq);
+  // state update by its increment: with x' = x + dx the backward-Euler
+  // equation reads A dx^2 + (2Ax + B) dx + r0 = 0, where
+  //   r0 = A x^2 - sG (1 - x)
+  // is dt times the net rate (recombination minus photo-ionisation) at the old
+  // state.  Near Saha equilibrium the two terms cancel, so r0 is formed in
+  // double-float arithmetic (about 48 bits) rather than in binary32; the
+  // discriminant of this equation is D again.
+  const dfloat r0 = df_add(df_mul_f(df_mul(X, X), c.A), df_neg(df_mul(df_mul_f(Gc, c.s), Y)));
+  float dx = fdiv(-2.0f * r0.hi, 2.0f * c.A * c.xf + B + sq);
+  double xn = x + f2d_bits(dx);  // one binary64 addition, no conversion instruction
+  float damp = __expf(-(m.kdf * xr + m.Hf) * m.dtf);
+  u.x *= damp; u.y *= damp; u.z *= damp;
+  ((float4*)a.vel4)[i] = u;
+  a.x[i] = xn;
+  a.xy[i] = make_float2(xr, yr);
+  ((float*)a.T)[i] = c.Tn;
+  float ne = c.n * xr;
+  ((float*)a.emis)[i] = c.al * ne * ne;
+  if (zero_tally) a.tally[i] = 0u;
+  s0.add(d * yr);
+  s1.add(d * xr);
+  s2.add(d);
+}
+
 // Per-block final update at the converged lambda: writes x, T, U, emission
 // weights (zeroes the tallies on the last substep); partial sums (thread 0):
 // v0 = sum delta (1 - x'), v1 = sum delta x', v2 = sum delta.
@@ -321,65 +397,13 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
     }
   } else {
     Kahan32 s0, s1, s2;
-    const CoefF32 f = coef_f32(a.k);
-    const float Gf = (float)G;
-    const float wscale = tot > 0.0 ? (float)(S1s / tot) : 0.0f;
+    const FinalMixed fm = final_mixed_setup(a, G, tot, S1s);
     const float* delta = (const float*)a.delta;
-    float* T = (float*)a.T;
-    float4* U = (float4*)a.vel4;
-    float* emis = (float*)a.emis;
-    const float kdf = (float)a.k.kd, Hf = (float)a.k.H, dtf = (float)a.k.dt;
-    const dfloat Gd = df_from_double(G);
+    const float* T = (const float*)a.T;
+    const float4* U = (const float4*)a.vel4;
     for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
-      float d = delta[i];
-      double x = a.x[i];
-      // the state and 1 - x as double-float pairs, from the bits of x
-      const dfloat X = df_from_double(x);
-      const dfloat Y = df_add(dfloat{1.0f, 0.0f}, df_neg(X));
-      uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
-      CellF32 c = cell_f32(f, a.k.mixing, d, make_float2(df_to_float(X), df_to_float(Y)), T[i], tal, wscale);
-      float Gcf = Gf;
-      dfloat Gc = Gd;
-      if (PART) {
-        const float fm = (float)a.fmix;
-        const float Ci = local_C_f32(a.k, ((const float*)a.div)[i], c.n * c.yf);
-        c.A *= fm + (1.0f - fm) * Ci;
-        c.s = f.dt * fm;
-        const float go = ((1.0f - fm) / fm) * Ci * (float)(a.k.beta * a.k.ea);
-        Gcf = Gf + go;
-        Gc = df_add(Gd, dfloat{go, 0.0f});
-      }
-      // binary32 roots x' and y' = 1 - x' (both without cancellation) and the
-      // discriminant D = B^2 + 4 A c
-      float sGf = c.s * Gcf;
-      float B = 1.0f + sGf;
-      float sq = __fsqrt_rn(B * B + 4.0f * c.A * (c.xf + sGf));
-      float xr = __fdiv_rn(2.0f * (c.xf + sGf), B + sq);
-      float yr = __fdiv_rn(2.0f * (c.A + c.yf), 2.0f * c.A + B + sq);
-      // state update by its increment: with x' = x + dx the backward-Euler
-      // equation reads A dx^2 + (2Ax + B) dx + r0 = 0, where
-      //   r0 = A x^2 - sG (1 - x)
-      // is dt times the net rate (recombination minus photo-ionisation) at the old
-      // state.  Near Saha equilibrium the two terms cancel, so r0 is formed in
-      // double-float arithmetic (about 48 bits) rather than in binary32; the
-      // discriminant of this equation is D again.
-      const dfloat r0 = df_add(df_mul_f(df_mul(X, X), c.A), df_neg(df_mul(df_mul_f(Gc, c.s), Y)));
-      float dx = fdiv(-2.0f * r0.hi, 2.0f * c.A * c.xf + B + sq);
-      double xn = x + (double)dx;
-      float damp = __expf(-(kdf * xr + Hf) * dtf);
-      float4 u = U[i];
-      u.x *= damp; u.y *= damp; u.z *= damp;
-      U[i] = u;
-      a.x[i] = xn;
-      a.xy[i] = make_float2(xr, yr);
-      T[i] = c.Tn;
-      float ne = c.n * xr;
-      float r = c.al * ne * ne;
-      emis[i] = r;
-      if (zero_tally) a.tally[i] = 0u;
-      s0.add(d * yr);
-      s1.add(d * xr);
-      s2.add(d);
+      const uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
+      final_cell_mixed<PART>(a, fm, zero_tally, i, delta[i], a.x[i], T[i], tal, U[i], s0, s1, s2);
     }
     v[0] = s0.value(); v[1] = s1.value(); v[2] = s2.value();
   }
@@ -410,11 +434,14 @@ __device__ __forceinline__ void finish_substep(DevScalars* sc, const StepCoef& k
 // Batched contexts (MB): the grid is the concatenation of every box's pass
 // blocks; a block works on its box's cells with the box's own block count, and
 // the last block of a box reduces that box's partials.  Single box: the whole grid.
-__device__ __forceinline__ void pass_view(PassArgs& a, const BoxDev* bxs, int B, int* blk, int* nblk, int* box) {
+// g: the block's index in the concatenated grid (blockIdx.x, or a virtual
+// block of a persistent launch).
+__device__ __forceinline__ void pass_view(PassArgs& a, const BoxDev* bxs, int B, int* blk, int* nblk, int* box,
+                                          uint32_t g) {
   int lo = 0, hi = B;
   while (hi - lo > 1) {
     int mid = (lo + hi) >> 1;
-    if (bxs[mid].pblk0 <= blockIdx.x) lo = mid;
+    if (bxs[mid].pblk0 <= g) lo = mid;
     else hi = mid;
   }
   const BoxDev& d = bxs[lo];
@@ -428,7 +455,7 @@ __device__ __forceinline__ void pass_view(PassArgs& a, const BoxDev* bxs, int B,
   a.emis = d.emis;
   a.sc = d.sc;
   a.part += (size_t)d.pblk0 * kMaxSums;
-  *blk = (int)(blockIdx.x - d.pblk0);
+  *blk = (int)(g - d.pblk0);
   *nblk = (int)d.pblk;
   *box = lo;
 }
@@ -436,7 +463,7 @@ __device__ __forceinline__ void pass_view(PassArgs& a, const BoxDev* bxs, int B,
 template <bool MIXED, bool MB>
 __global__ void __launch_bounds__(NT) k_newton(PassArgs a, const BoxDev* bxs, int B) {
   int blk = blockIdx.x, nblk = gridDim.x, box = 0;
-  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box, blockIdx.x);
   DevScalars* sc = a.sc;
   if (ld_flag(&sc->conv)) return;
   const double lam = sc->lam;
@@ -496,6 +523,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for a stage: a non-blocking look, then at most `limit` blocking polls.
+// limit 0 gives up without looking (the error path, for tests).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, uint32_t limit) {
+  if (limit == 0) return false;
+  if (mbar_test_wait(b, parity)) return true;
+  for (uint32_t polls = 0; polls < limit; ++polls)
+    if (mbar_try_wait(b, parity)) return true;
+  return false;
+}
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_addr(dst)),
@@ -503,7 +548,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-__global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a) {
+__global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a, uint32_t limit) {
   DevScalars* sc = a.sc;
   if (ld_flag(&sc->conv)) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -554,9 +599,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a) {
     }
     const int s = (int)(it % kTmaStages);
     const uint32_t parity = (uint32_t)((it / kTmaStages) & 1);
-    uint32_t polls = 0;
-    while (!mbar_try_wait(&full[s], parity))
-      if (++polls > kTmaWaitLimit) { timed_out = true; break; }
+    if (!mbar_wait_bounded(&full[s], parity, limit)) timed_out = true;
     if (!timed_out) {
       const TmaStage& t = stage[s];
       for (int k = threadIdx.x; k < kTmaTile; k += kTmaThreads) cell(t.delta[k], t.xy[k], t.T[k], t.tally[k]);
@@ -600,7 +643,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a) {
 template <bool MIXED, bool MB>
 __global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st, const BoxDev* bxs, int B) {
   int blk = blockIdx.x, nblk = gridDim.x, box = 0;
-  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box, blockIdx.x);
   DevScalars* sc = a.sc;
   const double lam = sc->lam;
   double v[3];
@@ -613,6 +656,169 @@ __global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st, const B
   double S[3];
   combine_partials<3, NT>(a.part, nblk, kMaxSums, S);
   if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st ? st + box : nullptr);
+}
+
+// ---- batched substep as one persistent launch ------------------------------------
+// A whole substep of a batched context in one cooperative launch: the Newton
+// prologue of every box, then Newton evaluations (each box's pass blocks run
+// as virtual blocks of the resident grid; the last virtual block of a box
+// takes its Newton step) separated by bounded grid barriers until every box
+// has converged, then the final pass.  Scalars that other blocks update within
+// the launch are read through L2 (ld.cg).  A barrier that gives up ends the
+// launch (flags bit 3 of the batch record; rec_sync reports it).
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) k_batch_substep(PassArgs a0, rec_stats* st, const BoxDev* bxs, int B, int nvb,
+                                                      DevScalars* gsc, uint32_t limit) {
+  if (blockIdx.x == 0)
+    for (int b = threadIdx.x; b < B; b += NT) substep_begin(bxs[b].sc, a0.k, (double)bxs[b].n3);
+  if (!grid_barrier(&gsc->bar, &gsc->flags, limit)) return;
+  for (int pass = 0; pass < kNewtonMaxPasses; ++pass) {
+    for (int g = blockIdx.x; g < nvb; g += gridDim.x) {
+      PassArgs a = a0;
+      int blk, nblk, box;
+      pass_view(a, bxs, B, &blk, &nblk, &box, (uint32_t)g);
+      DevScalars* sc = a.sc;
+      if (__ldcg(&sc->conv)) continue;  // the same for the whole block
+      const double lam = __ldcg(&sc->lam);
+      double v[3];
+      newton_block_sums<MIXED>(a, lam, __ldcg(&sc->omC) * lam + __ldcg(&sc->G0), (double)__ldcg(&sc->tally_total),
+                               __ldcg(&sc->S1s), blk, nblk, v);
+      if (threadIdx.x == 0) {
+        double* p = a.part + (size_t)blk * kMaxSums;
+        p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+      }
+      if (!last_block_done(&sc->counter, nblk)) continue;
+      double S[3];
+      combine_partials<3, NT>(a.part, nblk, kMaxSums, S);
+      if (threadIdx.x == 0) {
+        newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
+        sc->counter = 0;
+      }
+    }
+    if (!grid_barrier(&gsc->bar, &gsc->flags, limit)) return;
+    int open = 0;
+    for (int b = threadIdx.x; b < B; b += NT) open |= __ldcg(&bxs[b].sc->conv) == 0;
+    if (!__syncthreads_or(open)) break;
+  }
+  for (int g = blockIdx.x; g < nvb; g += gridDim.x) {
+    PassArgs a = a0;
+    int blk, nblk, box;
+    pass_view(a, bxs, B, &blk, &nblk, &box, (uint32_t)g);
+    DevScalars* sc = a.sc;
+    const double lam = __ldcg(&sc->lam);
+    double v[3];
+    final_block<MIXED>(a, __ldcg(&sc->omC) * lam + __ldcg(&sc->G0), (double)__ldcg(&sc->tally_total), __ldcg(&sc->S1s),
+                       blk, nblk, v);
+    if (threadIdx.x == 0) {
+      double* p = a.part + (size_t)blk * kMaxSums;
+      p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+    }
+    if (!last_block_done(&sc->counter, nblk)) continue;
+    double S[3];
+    combine_partials<3, NT>(a.part, nblk, kMaxSums, S);
+    if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st ? st + box : nullptr);
+  }
+}
+
+// ---- final pass of the mixed form with TMA-staged tiles ----------------------------
+// The final pass streams five inputs per cell (Delta, x, T, tallies, velocity;
+// 36 B) and writes six outputs.  As in the Newton evaluation, persistent CTAs
+// bring tiles of kTmaTile cells of the inputs into a ring of shared-memory
+// stages with bulk asynchronous copies, so that the loads are in flight while
+// the previous tile is computed; the outputs are stored directly.  Waits are
+// bounded as in k_newton_tma.
+constexpr int kFinStages = 2;
+constexpr int kFinCtasPerSm = 3;
+struct FinStage {
+  float delta[kTmaTile];
+  double x[kTmaTile];
+  float T[kTmaTile];
+  uint32_t tally[kTmaTile];
+  float4 U[kTmaTile];
+};
+constexpr size_t kFinSmem = sizeof(FinStage) * kFinStages + 8 * kFinStages;
+
+__global__ void __launch_bounds__(kTmaThreads, kFinCtasPerSm) k_final_tma(PassArgs a, rec_stats* st, uint32_t limit) {
+  DevScalars* sc = a.sc;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  FinStage* stage = reinterpret_cast<FinStage*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(FinStage) * kFinStages);
+  const double lam = sc->lam;
+  const FinalMixed fm = final_mixed_setup(a, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s);
+  const bool zero_tally = a.k.last != 0;
+  const bool tally_mode = a.k.mixing == REC_MIX_TALLY;
+  const uint32_t stage_bytes = kTmaTile * (4 + 8 + 4 + 16) + (tally_mode ? kTmaTile * 4 : 0);
+  const int64_t n_tiles = a.n3 / kTmaTile;
+  const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const float* delta = (const float*)a.delta;
+  const float* Tg = (const float*)a.T;
+  const float4* Ug = (const float4*)a.vel4;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFinStages; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t it) {  // thread 0: tile `it` of this CTA into its stage
+    const int s = (int)(it % kFinStages);
+    const int64_t c0 = ((int64_t)blockIdx.x + it * gridDim.x) * kTmaTile;
+    mbar_expect_tx(&full[s], stage_bytes);
+    bulk_load(stage[s].delta, delta + c0, kTmaTile * 4, &full[s]);
+    bulk_load(stage[s].x, a.x + c0, kTmaTile * 8, &full[s]);
+    bulk_load(stage[s].T, Tg + c0, kTmaTile * 4, &full[s]);
+    if (tally_mode) bulk_load(stage[s].tally, a.tally + c0, kTmaTile * 4, &full[s]);
+    bulk_load(stage[s].U, Ug + c0, kTmaTile * 16, &full[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int64_t it = 0; it < my_tiles && it < kFinStages - 1; ++it) issue(it);
+  Kahan32 s0, s1, s2;
+  bool timed_out = false;
+  int64_t it = 0;
+  for (; it < my_tiles; ++it) {
+    if (threadIdx.x == 0 && it + kFinStages - 1 < my_tiles) {
+      // the stage refilled here was read by every thread before the barrier that ended the last iteration
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(it + kFinStages - 1);
+    }
+    const int s = (int)(it % kFinStages);
+    const uint32_t parity = (uint32_t)((it / kFinStages) & 1);
+    if (!mbar_wait_bounded(&full[s], parity, limit)) timed_out = true;
+    if (!timed_out) {
+      const FinStage& t = stage[s];
+      const int64_t c0 = ((int64_t)blockIdx.x + it * gridDim.x) * kTmaTile;
+      for (int k = threadIdx.x; k < kTmaTile; k += kTmaThreads)
+        final_cell_mixed<false>(a, fm, zero_tally, c0 + k, t.delta[k], t.x[k], t.T[k], tally_mode ? t.tally[k] : 0u,
+                                t.U[k], s0, s1, s2);
+    }
+    if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+  }
+  if (timed_out) {
+    if (threadIdx.x == 0) {
+      atomicOr(&sc->flags, 8);
+      // the copies issued for the tiles it .. it + kFinStages - 2 may still be in flight
+      for (int64_t j = it; j < my_tiles && j < it + kFinStages - 1; ++j) {
+        uint32_t polls = 0;
+        while (!mbar_try_wait(&full[j % kFinStages], (uint32_t)((j / kFinStages) & 1)) && ++polls < kTmaWaitLimit) {
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  // cells after the last whole tile
+  for (int64_t i = n_tiles * kTmaTile + (int64_t)blockIdx.x * kTmaThreads + threadIdx.x; i < a.n3;
+       i += (int64_t)gridDim.x * kTmaThreads)
+    final_cell_mixed<false>(a, fm, zero_tally, i, delta[i], a.x[i], Tg[i], tally_mode ? a.tally[i] : 0u, Ug[i], s0,
+                            s1, s2);
+  double v[3] = {s0.value(), s1.value(), s2.value()};
+  block_sum<3, kTmaThreads>(v);
+  if (threadIdx.x == 0) {
+    double* p = a.part + (size_t)blockIdx.x * kMaxSums;
+    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+  }
+  if (!last_block_done(&sc->counter)) return;
+  double S[3];
+  combine_partials<3, kTmaThreads>(a.part, gridDim.x, kMaxSums, S);
+  if (threadIdx.x == 0) finish_substep(sc, a.k, S, lam, st);
 }
 
 // Newton evaluation and final pass of partial mixing (single-box contexts).
@@ -778,89 +984,12 @@ __global__ void __launch_bounds__(NT) k_local(PassArgs a, const void* div, rec_s
   }
 }
 
-// A whole substep in one cooperative launch: Newton evaluations separated by
-// grid barriers until converged, then the final pass.  Every block combines
-// the block partials itself, in the same fixed order, so all blocks take the
-// same Newton steps without another barrier; the partials are double-buffered
-// because a fast block may start the next evaluation while a slow one is
-// still reading the previous partials.
-template <bool MIXED>
-__global__ void __launch_bounds__(NT) k_substep_coop(PassArgs a, rec_stats* st, double n3d) {
-  cg::grid_group grid = cg::this_grid();
-  DevScalars* sc = a.sc;
-  const StepCoef& k = a.k;
-  __shared__ double s_lam, s_rel;
-  __shared__ int s_conv;
-  const double S1s = sc->S1s, tot = (double)sc->tally_total;
-  // R_alpha^mix from the substep-start <n_1s> (Eq. R-alpha), C from Eq. Cfactor
-  const double R = k.KR / (k.nH * S1s / n3d);
-  const double C = (k.L2g + R) / (k.beta + k.L2g + R);
-  const double omC = 1.0 - C, G0 = C * k.beta * k.ea;
-  const double tol = MIXED ? 1e-5 : 1e-8;
-  double lam = sc->lam_state;
-  if (sc->lam_prev > 0.0 && sc->lam_state > 0.0)
-    lam = sc->lam_state * fmin(2.0, fmax(0.5, sc->lam_state / sc->lam_prev));
-  if (!(lam > 0.0)) lam = 1e-30;
-  int passes = 0;
-  bool conv = false;
-  double prev_rel = HUGE_VAL;
-  while (passes < kNewtonMaxPasses && !conv) {
-    double v[3];
-    newton_block_sums<MIXED>(a, lam, omC * lam + G0, tot, S1s, blockIdx.x, gridDim.x, v);
-    double* part = a.part + (size_t)(passes & 1) * gridDim.x * kMaxSums;
-    if (threadIdx.x == 0) {
-      double* p = part + (size_t)blockIdx.x * kMaxSums;
-      p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
-    }
-    grid.sync();
-    double S[3];
-    combine_partials<3, NT>(part, gridDim.x, kMaxSums, S);
-    if (threadIdx.x == 0) {
-      double F = S[0] - lam * S[1];
-      double Fp = omC * S[2] - S[1];
-      double step = F / Fp;
-      double lnew = lam - step;
-      if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
-      double rel = fabs(step) / lam;
-      s_conv = (Fp < 0.0 && (rel <= tol || (rel <= 1e-3 && rel >= 0.5 * prev_rel))) ? 1 : 0;
-      s_lam = lnew;
-      s_rel = rel;
-    }
-    __syncthreads();
-    lam = s_lam;
-    conv = s_conv != 0;
-    prev_rel = s_rel;
-    ++passes;
-  }
-  double v[3];
-  final_block<MIXED>(a, omC * lam + G0, tot, S1s, blockIdx.x, gridDim.x, v);
-  double* part = a.part + (size_t)(passes & 1) * gridDim.x * kMaxSums;
-  if (threadIdx.x == 0) {
-    double* p = part + (size_t)blockIdx.x * kMaxSums;
-    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
-  }
-  grid.sync();
-  if (blockIdx.x != 0) return;
-  double S[3];
-  combine_partials<3, NT>(part, gridDim.x, kMaxSums, S);
-  if (threadIdx.x == 0) {
-    sc->C = C;
-    sc->omC = omC;
-    sc->G0 = G0;
-    sc->lam = lam;
-    sc->passes = passes;
-    sc->conv = conv ? 1 : 0;
-    if (!conv) sc->flags |= 1;
-    finish_substep(sc, k, S, lam, st);
-  }
-}
-
 // Emission weights and sums of the current state at redshift z (no update);
 // also recounts the tallies.
 template <bool MIXED, bool MB>
 __global__ void __launch_bounds__(NT) k_refresh(PassArgs a, const BoxDev* bxs, int B) {
   int blk = blockIdx.x, nblk = gridDim.x, box = 0;
-  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box, blockIdx.x);
   DevScalars* sc = a.sc;
   const int64_t stride = (int64_t)nblk * NT;
   double v[6];  // S1s, Sdx, Sd, sum alpha n^2 x^2, sum n(1-x), tally count
@@ -912,7 +1041,7 @@ __global__ void __launch_bounds__(NT) k_refresh(PassArgs a, const BoxDev* bxs, i
 template <bool MIXED, bool MB>
 __global__ void k_state_init(PassArgs a, double nH_over_S, double Tg, const BoxDev* bxs, int B) {
   int blk = blockIdx.x, nblk = gridDim.x, box = 0;
-  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box);
+  if (MB) pass_view(a, bxs, B, &blk, &nblk, &box, blockIdx.x);
   const int64_t stride = (int64_t)nblk * NT;
   for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
     double d = MIXED ? (double)((const float*)a.delta)[i] : ((const double*)a.delta)[i];
@@ -976,61 +1105,39 @@ cudaError_t launch_state_init(rec_ctx* c, double z) {
   return launch_refresh(c, z);
 }
 
-// The TMA-staged Newton pass needs 16-byte aligned streams (bulk copies) and
-// its shared-memory ring; REC_NEWTON=plain selects the grid-stride kernel.
+// The TMA-staged Newton and final passes need 16-byte aligned streams (bulk
+// copies) and their shared-memory rings; REC_NEWTON=plain selects the
+// grid-stride kernels.
 bool newton_tma_ok(rec_ctx* c, const PassArgs& a) {
   if (c->newton_tma == 0) {
     const char* sel = std::getenv("REC_NEWTON");
     bool ok = !(sel && std::strcmp(sel, "plain") == 0);
     ok = ok && cudaFuncSetAttribute(k_newton_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) ==
                    cudaSuccess;
-    ok = ok && kTmaCtasPerSm * c->sm_count <= 2 * c->grid;  // its blocks fit the partials (2 x grid entries)
+    ok = ok && cudaFuncSetAttribute(k_final_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFinSmem) ==
+                   cudaSuccess;
+    // their blocks fit the partials (2 x grid entries)
+    ok = ok && kTmaCtasPerSm * c->sm_count <= 2 * c->grid && kFinCtasPerSm * c->sm_count <= 2 * c->grid;
     c->newton_tma = ok ? 1 : -1;
     cudaGetLastError();
   }
   auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-  return c->newton_tma > 0 && al(a.delta) && al(a.xy) && al(a.T) && al(a.tally);
+  return c->newton_tma > 0 && al(a.delta) && al(a.xy) && al(a.T) && al(a.tally) && al(a.x) && al(a.vel4);
 }
 
 cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* st) {
   const int ns = c->params.n_sub;
   const bool mixed = c->params.precision == REC_PREC_MIXED;
   double ya = std::log1p(z_from), yb = std::log1p(z_to);
-  // grid of the cooperative substep: every block must be resident
-  if (c->coop_grid == 0) {
-    // tuning: one launch per Newton evaluation (default, faster on GB300 at the
-    // 256^3 workload) or REC_SUBSTEP=coop for one cooperative launch per substep
-    const char* sel = std::getenv("REC_SUBSTEP");
-    if (!(sel && std::strcmp(sel, "coop") == 0)) c->coop_grid = -1;
-  }
-  if (c->coop_grid == 0) {
-    int per_sm = 0;
-    cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_substep_coop<true>, NT, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_substep_coop<false>, NT, 0);
-    if (e != cudaSuccess) return e;
-    int attr = 0;
-    cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, 0);
-    c->coop_grid = (attr && per_sm > 0) ? std::min(c->grid, per_sm * c->sm_count) : -1;
-  }
   const bool local_modes = c->params.mixing == REC_MIX_LOCAL || c->params.mixing == REC_MIX_PARTIAL;
-  if (local_modes) c->coop_grid = -1;  // the cooperative substep covers tally and full mixing
   const bool one_pass = c->params.mixing == REC_MIX_LOCAL ||
                         (c->params.mixing == REC_MIX_PARTIAL && !(c->params.f_alpha > 0.0));
-  GroupTimer t(c, kTStep, one_pass ? 2 * ns
-                                   : (c->coop_grid > 0 ? ns : ns * (kNewtonMaxPasses + 2 + (local_modes ? 1 : 0))));
+  GroupTimer t(c, kTStep, one_pass ? 2 * ns : ns * (kNewtonMaxPasses + 2 + (local_modes ? 1 : 0)));
   for (int s = 0; s < ns; ++s) {
     double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
     double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
     StepCoef k = step_coef(c->cosmo, c->params, za, zb, s == ns - 1);
     PassArgs a = pass_args(c, k);
-    if (c->coop_grid > 0) {
-      double n3d = (double)c->n3;
-      void* args[] = {&a, &st, &n3d};
-      cudaError_t e = cudaLaunchCooperativeKernel(mixed ? (void*)k_substep_coop<true> : (void*)k_substep_coop<false>,
-                                                  c->coop_grid, NT, args, 0, c->stream);
-      if (e != cudaSuccess) return e;
-      continue;
-    }
     const bool part = c->params.mixing == REC_MIX_PARTIAL && c->params.f_alpha > 0.0;
     if (c->params.mixing == REC_MIX_LOCAL || (c->params.mixing == REC_MIX_PARTIAL && !part)) {
       const double fac = (1.0 + zb) * 1.0e3 / (2.0 * c->cosmo.L_m / c->box.n);
@@ -1059,11 +1166,12 @@ cudaError_t launch_rec_step(rec_ctx* c, double z_from, double z_to, rec_stats* s
     k_substep_begin<<<1, 32, 0, c->stream>>>(c->sc, k, (double)c->n3);
     const bool tma = mixed && newton_tma_ok(c, a);
     for (int it = 0; it < kNewtonMaxPasses; ++it) {
-      if (tma) k_newton_tma<<<c->sm_count * kTmaCtasPerSm, kTmaThreads, kTmaSmem, c->stream>>>(a);
+      if (tma) k_newton_tma<<<c->sm_count * kTmaCtasPerSm, kTmaThreads, kTmaSmem, c->stream>>>(a, c->wait_limit);
       else if (mixed) k_newton<true, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
       else k_newton<false, false><<<c->grid, NT, 0, c->stream>>>(a, nullptr, 1);
     }
-    if (mixed) k_final<true, false><<<c->grid, NT, 0, c->stream>>>(a, st, nullptr, 1);
+    if (tma) k_final_tma<<<c->sm_count * kFinCtasPerSm, kTmaThreads, kFinSmem, c->stream>>>(a, st, c->wait_limit);
+    else if (mixed) k_final<true, false><<<c->grid, NT, 0, c->stream>>>(a, st, nullptr, 1);
     else k_final<false, false><<<c->grid, NT, 0, c->stream>>>(a, st, nullptr, 1);
   }
   return cudaGetLastError();
@@ -1100,6 +1208,42 @@ cudaError_t launch_volume_stats(rec_ctx* c, rec_stats* st) {
   return cudaGetLastError();
 }
 
+// Expired bounded waits (flags bit 3) of every box: reported in *out and
+// cleared, with the counters a pass that gave up may have left part-way.
+__global__ void k_check_waits(DevScalars* sc, const BoxDev* bxs, int B, DevScalars* gsc, int* out) {
+  if (threadIdx.x != 0) return;
+  // a batch-wide expiry (a grid barrier gave up) may have left any box part-way
+  const bool all = gsc && (gsc->flags & 8);
+  int any = all ? 1 : 0;
+  for (int b = 0; b < B; ++b) {
+    DevScalars* s = bxs ? bxs[b].sc : sc;
+    if (all || (s->flags & 8)) {
+      any = 1;
+      s->flags &= ~8;
+      s->counter = 0;
+      s->alloc_counter = 0;
+    }
+  }
+  if (all) {
+    gsc->flags &= ~8;
+    gsc->counter = 0;
+    gsc->alloc_counter = 0;
+    gsc->bar.arrived = 0;
+  }
+  *out = any;
+}
+
+cudaError_t launch_check_waits(rec_ctx* c, int* timed_out) {
+  int* d = reinterpret_cast<int*>(c->part);  // scratch word: no pass is in flight after the sync
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  k_check_waits<<<1, 32, 0, c->stream>>>(c->sc, c->n_boxes > 1 ? c->bx : nullptr, c->n_boxes,
+                                         c->n_boxes > 1 ? c->gsc : nullptr, d);
+  e = cudaMemcpyAsync(timed_out, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
+
 cudaError_t launch_refresh_batch(rec_ctx* c, double z) {
   StepCoef k = step_coef(c->cosmo, c->params, z + 1e-6 * (1.0 + z), z, 0);
   PassArgs a = batch_args(c, k);
@@ -1124,10 +1268,43 @@ cudaError_t launch_state_init_batch(rec_ctx* c, double z) {
   return launch_refresh_batch(c, z);
 }
 
+// Resident blocks of the persistent batched substep (0: cooperative launch unavailable).
+int batch_substep_grid(rec_ctx* c, bool mixed) {
+  if (c->batch_step_grid == 0) {
+    int per_sm = 0, coop = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_substep<true>, NT, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_substep<false>, NT, 0);
+    cudaGetLastError();
+    c->batch_step_grid = (e == cudaSuccess && coop && per_sm > 0) ? per_sm * c->sm_count : -1;
+  }
+  return c->batch_step_grid;
+}
+
 cudaError_t launch_rec_step_batch(rec_ctx* c, double z_from, double z_to, rec_stats* st) {
   const int ns = c->params.n_sub;
   const bool mixed = c->params.precision == REC_PREC_MIXED;
   const double ya = std::log1p(z_from), yb = std::log1p(z_to);
+  const int pgrid = batch_substep_grid(c, mixed);
+  if (pgrid > 0) {  // one persistent launch per substep
+    GroupTimer t(c, kTStep, ns);
+    for (int s = 0; s < ns; ++s) {
+      double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);
+      double zb = (s == ns - 1) ? z_to : std::expm1(ya - (ya - yb) * (double)(s + 1) / ns);
+      StepCoef k = step_coef(c->cosmo, c->params, za, zb, s == ns - 1);
+      PassArgs a = batch_args(c, k);
+      const BoxDev* bxs = c->bx;
+      int B = c->n_boxes, nvb = c->tot_pblk;
+      DevScalars* gsc = c->gsc;
+      uint32_t limit = c->wait_limit;
+      void* args[] = {&a, &st, &bxs, &B, &nvb, &gsc, &limit};
+      cudaError_t e = cudaLaunchCooperativeKernel(mixed ? (void*)k_batch_substep<true> : (void*)k_batch_substep<false>,
+                                                  pgrid, NT, args, 0, c->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+  }
   GroupTimer t(c, kTStep, ns * (kNewtonMaxPasses + 2));
   for (int s = 0; s < ns; ++s) {
     double za = (s == 0) ? z_from : std::expm1(ya - (ya - yb) * (double)s / ns);

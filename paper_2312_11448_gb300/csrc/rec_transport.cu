@@ -145,17 +145,19 @@ template <> struct Draws<double> {
 };
 
 // ---- allocation -------------------------------------------------------------------
+// The maximum is taken in the working precision (exact for any precision), so
+// the binary32 form issues no binary64 instruction per cell.
 template <class R>
 __global__ void __launch_bounds__(kPassThreads) k_alloc_max(const R* emis, int64_t n3, DevScalars* sc, double* part) {
-  double m = 0.0;
+  R m = (R)0;
   int bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * kPassThreads + threadIdx.x; i < n3; i += (int64_t)gridDim.x * kPassThreads) {
-    double r = (double)emis[i];
-    if (!(r >= 0.0) || isinf(r)) bad = 1;
+    const R r = emis[i];
+    if (!(r >= (R)0) || isinf(r)) bad = 1;
     else m = fmax(m, r);
   }
   bad = __syncthreads_or(bad);
-  double bm = block_max<kPassThreads>(m);
+  double bm = block_max<kPassThreads>((double)m);
   if (threadIdx.x == 0) {
     part[(size_t)blockIdx.x * kMaxSums + 0] = bm;
     part[(size_t)blockIdx.x * kMaxSums + 1] = bad ? 1.0 : 0.0;
@@ -343,6 +345,19 @@ __device__ __forceinline__ uint32_t sys_floor(uint64_t N, uint64_t pre, uint64_t
   return (uint32_t)q;
 }
 
+// floor(t / S) and t mod S for t < 2^64, given m = floor((2^64 - 1) / S): the
+// multiply-high estimate is short by at most 2, then corrected exactly
+// (replaces a 64-bit division per cell).
+__device__ __forceinline__ uint64_t div_small(uint64_t t, uint64_t S, uint64_t m, uint64_t* r) {
+  uint64_t q = __umul64hi(t, m);
+  uint64_t rr = t - q * S;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (rr >= S) { ++q; rr -= S; }
+  *r = rr;
+  return q;
+}
+
 // Packet prefix P_i = floor((N prefixQ_i + u) / S) of the thread's consecutive
 // cells: one 128-bit division for the first, then exact 64-bit remainder
 // updates, (R + N Q_i) / S.  The same pass writes the coarse index first[w] =
@@ -376,12 +391,12 @@ __device__ __forceinline__ void alloc_prefix_block(const R* emis, int64_t n3, ui
     uint64_t rem;
     uint32_t pk = sys_floor(n_packets, pre_block + incl - acc, u, S, &rem);
     uint32_t bk = 0xffffffffu, bcount = 0;
+    const uint64_t minv = ~0ull / S;
 #pragma unroll
     for (int k = 0; k < kAllocItems; ++k) {
       out[k] = pk;
-      const uint64_t t = rem + n_packets * Q[k];
-      const uint64_t dq = t / S;
-      rem = t - dq * S;
+      const uint64_t t = rem + n_packets * Q[k];  // < S + 2^63 <= 2^64
+      const uint64_t dq = div_small(t, S, minv, &rem);
       const uint32_t p1 = pk + (uint32_t)dq;
       if (p1 > pk && c0 + k < n3) {
         for (uint32_t w = (pk + 31u) >> 5; 32ull * w < p1; ++w) first[w] = (uint32_t)(c0 + k);
@@ -418,45 +433,51 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix(const R* emis, int64_t n3, 
 }
 
 // One block: bucket capacities -> offsets (in place); fill counters cleared.
-__global__ void __launch_bounds__(1024) k_bucket_offsets(unsigned long long* bcap, unsigned long long* bfill, int nb) {
-  __shared__ unsigned long long part[1024];
-  const int per = (nb + 1023) / 1024;
+template <int NTH>
+__device__ __forceinline__ void bucket_offsets_block(unsigned long long* bcap, unsigned long long* bfill, int nb) {
+  __shared__ unsigned long long part[NTH];
+  const int per = (nb + NTH - 1) / NTH;
   unsigned long long s = 0;
-  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) s += bcap[b];
+  for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) s += __ldcg(&bcap[b]);
   part[threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long run = 0;
-    for (int t = 0; t < 1024; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; }
+    for (int t = 0; t < NTH; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; }
   }
   __syncthreads();
   unsigned long long run = part[threadIdx.x];
   for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
-    unsigned long long v = bcap[b];
+    unsigned long long v = __ldcg(&bcap[b]);
     bcap[b] = run;
     run += v;
     bfill[b] = 0;
   }
 }
+__global__ void __launch_bounds__(1024) k_bucket_offsets(unsigned long long* bcap, unsigned long long* bfill, int nb) {
+  bucket_offsets_block<1024>(bcap, bfill, nb);
+}
 
 // One block: the march works through the queue in chunks of `chunk` packets
 // that never straddle a bucket; cpre[b] = first chunk of bucket b, cpre[nb] =
 // all chunks.  Also the total queued.
-__global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* bfill, unsigned long long* cpre, int nb,
-                                                      DevScalars* sc, uint32_t chunk) {
-  __shared__ unsigned long long part[1024], qpart[1024];
-  const int per = (nb + 1023) / 1024;
+template <int NTH>
+__device__ __forceinline__ void bucket_scan_block(const unsigned long long* bfill, unsigned long long* cpre, int nb,
+                                                  DevScalars* sc, uint32_t chunk) {
+  __shared__ unsigned long long part[NTH], qpart[NTH];
+  const int per = (nb + NTH - 1) / NTH;
   unsigned long long s = 0, q = 0;
   for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
-    s += (bfill[b] + chunk - 1) / chunk;
-    q += bfill[b];
+    const unsigned long long f = __ldcg(&bfill[b]);
+    s += (f + chunk - 1) / chunk;
+    q += f;
   }
   part[threadIdx.x] = s;
   qpart[threadIdx.x] = q;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long run = 0, qt = 0;
-    for (int t = 0; t < 1024; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; qt += qpart[t]; }
+    for (int t = 0; t < NTH; ++t) { unsigned long long v = part[t]; part[t] = run; run += v; qt += qpart[t]; }
     cpre[nb] = run;
     sc->qtail = qt;
     sc->march_next = 0;
@@ -465,16 +486,24 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* 
   unsigned long long run = part[threadIdx.x];
   for (int b = threadIdx.x * per; b < min(nb, (threadIdx.x + 1) * per); ++b) {
     cpre[b] = run;
-    run += (bfill[b] + chunk - 1) / chunk;
+    run += (__ldcg(&bfill[b]) + chunk - 1) / chunk;
   }
+}
+__global__ void __launch_bounds__(1024) k_bucket_scan(const unsigned long long* bfill, unsigned long long* cpre, int nb,
+                                                      DevScalars* sc, uint32_t chunk) {
+  bucket_scan_block<1024>(bfill, cpre, nb, sc, chunk);
 }
 
 // ---- transport ----------------------------------------------------------------------
-// A queued packet: the march state right after it left its home cell,
-//   q0 = {cell bits, tMax_x, tMax_y, tMax_z}
-//   q1 = {tDelta_x, tDelta_y, tDelta_z (sign = step direction), u0}
-//   q2 = {kappa n_x, kappa n_y, kappa n_z, -}
-// so that the march continues bit for bit without recomputing anything.
+// A queued packet: the march state right after it left its home cell.
+// Binary32 form (two float4):
+//   q0 = {cell bits, tMax_x, tMax_y, tMax_z},  q1 = {n_x, n_y, n_z, u0};
+// the march recomputes tDelta = 1/|n| and kappa n with the same rounded
+// operations as the emission, so it continues bit for bit.
+// Binary64 form (three double4): q0 as above, q1 = {tDelta (sign = step
+// direction), u0}, q2 = {kappa n, -}: recomputing them would cost three
+// correctly rounded binary64 reciprocals per packet on the slow binary64 pipe.
+template <class R> struct QueueVecs { static constexpr int value = sizeof(R) == 4 ? 2 : 3; };
 template <class R>
 struct TransportArgs {
   const uint32_t* P;
@@ -499,11 +528,19 @@ struct TransportArgs {
   int refill;                      // idle lanes of a warp that trigger a refill
 };
 
+// Loads of the packet prefix and coarse index: the read-only path, or through
+// L2 (FRESH) when they were written earlier in the same launch.
+template <bool FRESH>
+__device__ __forceinline__ uint32_t ld_index(const uint32_t* p) {
+  return FRESH ? __ldcg(p) : __ldg(p);
+}
+
 // First index k in [lo, hi] with P[k] > key (P[hi] > key holds).
+template <bool FRESH = false>
 __device__ __forceinline__ uint32_t upper_bound(const uint32_t* P, uint32_t lo, uint32_t hi, uint32_t key) {
   while (lo < hi) {
     uint32_t mid = lo + ((hi - lo) >> 1);
-    if (__ldg(P + mid) > key) hi = mid;
+    if (ld_index<FRESH>(P + mid) > key) hi = mid;
     else lo = mid + 1;
   }
   return lo;
@@ -677,7 +714,7 @@ struct EmitBox {
 // Emission: one packet per thread.  Packets resonant in their home cell are
 // tallied here; the others take their first step and are queued.  One warp
 // emits the packets base .. base + 31 of one box (N packets).
-template <class R, bool P2>
+template <class R, bool P2, bool FRESH = false>
 __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitBox<R>& e, uint32_t base, uint32_t N,
                                           uint64_t& my_abs, uint64_t& my_cross) {
   using A = Ar<R>;
@@ -689,10 +726,10 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
   const bool act = p < N;
   // ---- cell of each packet: the coarse index gives the cell of the warp's
   // first packet, then a 32-cell window of P resolves the rest with ballots
-  const uint32_t c0 = __ldg(e.first + (base >> 5));
-  const uint32_t Pc0 = __ldg(e.P + c0);
+  const uint32_t c0 = ld_index<FRESH>(e.first + (base >> 5));
+  const uint32_t Pc0 = ld_index<FRESH>(e.P + c0);
   const uint32_t widx = c0 + 1u + lane;
-  const uint32_t wv = (widx <= n3) ? __ldg(e.P + widx) : 0xffffffffu;
+  const uint32_t wv = (widx <= n3) ? ld_index<FRESH>(e.P + widx) : 0xffffffffu;
   // off = number of window entries <= p (the window is sorted): binary search
   // over the 32 lane values with shuffles
   uint32_t off = 0;
@@ -706,8 +743,8 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
   const uint32_t prev = __shfl_sync(0xffffffffu, wv, (off > 0 ? off - 1u : 0u) & 31u);
   uint32_t cell = c0 + off, Pc = (off == 0) ? Pc0 : prev;
   if (act && off >= 32) {
-    cell = upper_bound(e.P, c0 + 32u, n3, p) - 1u;
-    Pc = __ldg(e.P + cell);
+    cell = upper_bound<FRESH>(e.P, c0 + 32u, n3, p) - 1u;
+    Pc = ld_index<FRESH>(e.P + cell);
   }
   bool home = false, queued = false;
   Ray<R> r;
@@ -793,14 +830,20 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
     if (queued) {
       uint64_t slot = a.boff[bk] + qb + __popc(gm & ((1u << lane) - 1u));
       uint32_t c1 = P2 ? (((r.iz << e.tl.lg) | r.iy) << e.tl.lg) | r.ix : (r.iz * n + r.iy) * n + r.ix;
-      V q0v, q1v, q2v;
+      constexpr int QV = QueueVecs<R>::value;
+      V q0v, q1v;
       q0v.x = bits_to<R>(c1); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
-      q1v.x = r.sx < 0 ? -r.tDx : r.tDx; q1v.y = r.sy < 0 ? -r.tDy : r.tDy; q1v.z = r.sz < 0 ? -r.tDz : r.tDz;
-      q1v.w = r.u0;
-      q2v.x = r.knx; q2v.y = r.kny; q2v.z = r.knz; q2v.w = zero;
-      a.queue[3 * slot] = q0v;
-      a.queue[3 * slot + 1] = q1v;
-      a.queue[3 * slot + 2] = q2v;
+      if (QV == 2) {
+        q1v.x = nx; q1v.y = ny; q1v.z = nz; q1v.w = r.u0;
+      } else {
+        q1v.x = r.sx < 0 ? -r.tDx : r.tDx; q1v.y = r.sy < 0 ? -r.tDy : r.tDy; q1v.z = r.sz < 0 ? -r.tDz : r.tDz;
+        q1v.w = r.u0;
+        V q2v;
+        q2v.x = r.knx; q2v.y = r.kny; q2v.z = r.knz; q2v.w = zero;
+        a.queue[QV * slot + 2] = q2v;
+      }
+      a.queue[QV * slot] = q0v;
+      a.queue[QV * slot + 1] = q1v;
     }
   }
 }
@@ -842,10 +885,14 @@ template <class R, bool MB> constexpr int march_occupancy() {
   return MB ? 3 : (sizeof(R) == 4 ? (MarchAhead<R>::value > 4 ? 3 : MarchAhead<R>::value > 2 ? 4 : 5) : 3);
 }
 
+__device__ __forceinline__ void transport_end_batch(const BoxDev* bxs, int B, const unsigned long long* bfill,
+                                                    rec_stats* st);
+
 // P2: the box side is a power of two (cell index by shifts and masks).
 // MB: batched context; the lanes of a warp may hold packets of different boxes.
 template <class R, bool P2, bool MB>
-__global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(TransportArgs<R> a, const BoxDev* bxs, int B) {
+__global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(TransportArgs<R> a, const BoxDev* bxs, int B,
+                                                                        const BoxStep* bst, rec_stats* st) {
   using V = typename Vec4<R>::T;
   const int lane = threadIdx.x & 31;
   const uint32_t n = (uint32_t)a.n;
@@ -856,10 +903,12 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
   const V* lvel = a.vel;
   uint32_t* ltally = a.tally;
   uint32_t ln = n;
+  R lkappa = a.kappa;
   int lbox = -1, cbox = 0;
   const V* cvel = a.vel;
   uint32_t* ctally = a.tally;
   uint32_t cn = n;
+  R ckappa = a.kappa;
   const uint64_t n_chunks = a.cpre[a.nb];
   uint64_t chunk = 0;
   uint64_t pos = 0, end = 0;  // queue slots [pos, end) left in the current chunk
@@ -899,13 +948,15 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
             cvel = (const V*)bxs[cbox].vel4;
             ctally = bxs[cbox].tally;
             cn = bxs[cbox].n;
+            ckappa = (R)bst[cbox].kappa;
           }
         }
         const uint32_t take = (uint32_t)min((uint64_t)__popc(idle), end - pos);
         const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
         if (((idle >> lane) & 1u) && rank < take) {
           const uint64_t slot = pos + rank;
-          V q0v = a.queue[3 * slot], q1v = a.queue[3 * slot + 1], q2v = a.queue[3 * slot + 2];
+          constexpr int QV = QueueVecs<R>::value;
+          const V q0v = a.queue[QV * slot], q1v = a.queue[QV * slot + 1];
           if (MB) {
             if (lbox != cbox) {  // counters of the previous box to shared memory
               if (lbox >= 0) box_counters_add(cnt, lbox, my_abs, my_cap, my_cross);
@@ -915,6 +966,7 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
             lvel = cvel;
             ltally = ctally;
             ln = cn;
+            lkappa = ckappa;
           }
           cell = to_bits<R>(q0v.x);
           if (P2) {
@@ -925,11 +977,19 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
             a.tl.template coords<false>(cell, &r.ix, &r.iy, &r.iz);
           }
           r.tMx = q0v.y; r.tMy = q0v.z; r.tMz = q0v.w;
-          r.sx = q1v.x < (R)0 ? -1 : 1; r.tDx = fabs(q1v.x);
-          r.sy = q1v.y < (R)0 ? -1 : 1; r.tDy = fabs(q1v.y);
-          r.sz = q1v.z < (R)0 ? -1 : 1; r.tDz = fabs(q1v.z);
           r.u0 = q1v.w;
-          r.knx = q2v.x; r.kny = q2v.y; r.knz = q2v.z;
+          if (QV == 2) {  // tDelta and kappa n exactly as the emission formed them
+            axis_setup<R>(q1v.x, &r.tDx, &r.sx);
+            axis_setup<R>(q1v.y, &r.tDy, &r.sy);
+            axis_setup<R>(q1v.z, &r.tDz, &r.sz);
+            r.knx = Ar<R>::mul(lkappa, q1v.x); r.kny = Ar<R>::mul(lkappa, q1v.y); r.knz = Ar<R>::mul(lkappa, q1v.z);
+          } else {
+            const V q2v = a.queue[QV * slot + 2];
+            r.sx = q1v.x < (R)0 ? -1 : 1; r.tDx = fabs(q1v.x);
+            r.sy = q1v.y < (R)0 ? -1 : 1; r.tDy = fabs(q1v.y);
+            r.sz = q1v.z < (R)0 ? -1 : 1; r.tDz = fabs(q1v.z);
+            r.knx = q2v.x; r.kny = q2v.y; r.knz = q2v.z;
+          }
           r.kc = 1;  // the step out of the home cell
           Uc = lvel[cell];
           active = true;
@@ -985,6 +1045,11 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
   if (MB) {
     if (lbox >= 0) box_counters_add(cnt, lbox, my_abs, my_cap, my_cross);
     box_counters_flush(cnt, bxs, B);
+    // the last block to finish closes the call: queued counts, tally totals, statistics
+    if (last_block_done(&a.sc->counter)) {
+      transport_end_batch(bxs, B, a.bfill, st);
+      if (threadIdx.x == 0) a.sc->counter = 0;
+    }
   } else {
     add_counters(a.sc, my_abs, my_cap, my_cross);
   }
@@ -1056,8 +1121,8 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   {
     GroupTimer t(c, kTMarch, 1);
     const int mb = c->sm_count * tu.march_blocks_per_sm;
-    if (p2) k_march<R, true, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1);
-    else k_march<R, false, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1);
+    if (p2) k_march<R, true, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1, nullptr, nullptr);
+    else k_march<R, false, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1, nullptr, nullptr);
   }
   {
     GroupTimer t(c, kTEnd, 1);
@@ -1074,34 +1139,37 @@ __device__ __forceinline__ int alloc_box(const BoxDev* bxs, int B, uint32_t g) {
   return last_le(B, g, [&](int i) { return bxs[i].ablk0; });
 }
 
+// Allocation phases of a batch as functions of the allocation block g of ng
+// (blockIdx.x of a per-phase launch, or a virtual block of the persistent one).
 template <class R>
-__global__ void __launch_bounds__(AT) k_alloc_max_batch(const BoxDev* bxs, int B, DevScalars* gsc, double* part) {
-  const int b = alloc_box(bxs, B, blockIdx.x);
+__device__ __forceinline__ void alloc_max_batch(const BoxDev* bxs, int B, DevScalars* gsc, double* part, uint32_t g,
+                                                uint32_t ng) {
+  const int b = alloc_box(bxs, B, g);
   const BoxDev& d = bxs[b];
-  const int64_t c0 = (int64_t)(blockIdx.x - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+  const int64_t c0 = (int64_t)(g - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
   R v[kAllocItems];
   load_items<R>((const R*)d.emis, c0, d.n3, v);
-  double m = 0.0;
+  R m = (R)0;
   int bad = 0;
 #pragma unroll
   for (int k = 0; k < kAllocItems; ++k) {
     if (c0 + k >= d.n3) continue;
-    double r = (double)v[k];
-    if (!(r >= 0.0) || isinf(r)) bad = 1;
+    const R r = v[k];
+    if (!(r >= (R)0) || isinf(r)) bad = 1;
     else m = fmax(m, r);
   }
   bad = __syncthreads_or(bad);
-  double bm = block_max<AT>(m);
+  double bm = block_max<AT>((double)m);
   if (threadIdx.x == 0) {
-    part[(size_t)blockIdx.x * kMaxSums + 0] = bm;
-    part[(size_t)blockIdx.x * kMaxSums + 1] = bad ? 1.0 : 0.0;
+    part[(size_t)g * kMaxSums + 0] = bm;
+    part[(size_t)g * kMaxSums + 1] = bad ? 1.0 : 0.0;
   }
-  if (!last_block_done(&gsc->counter)) return;
+  if (!last_block_done(&gsc->counter, ng)) return;
   // one warp per box: maximum over the box's blocks
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < B; i += AT / 32) {
     const uint32_t g0 = bxs[i].ablk0;
-    const uint32_t g1 = (i + 1 < B) ? bxs[i + 1].ablk0 : gridDim.x;
+    const uint32_t g1 = (i + 1 < B) ? bxs[i + 1].ablk0 : ng;
     double mx = 0.0, anybad = 0.0;
     for (uint32_t g = g0 + lane; g < g1; g += 32) {
       mx = fmax(mx, __ldcg(part + (size_t)g * kMaxSums));
@@ -1121,16 +1189,20 @@ __global__ void __launch_bounds__(AT) k_alloc_max_batch(const BoxDev* bxs, int B
   }
   if (threadIdx.x == 0) gsc->counter = 0;
 }
+template <class R>
+__global__ void __launch_bounds__(AT) k_alloc_max_batch(const BoxDev* bxs, int B, DevScalars* gsc, double* part) {
+  alloc_max_batch<R>(bxs, B, gsc, part, blockIdx.x, gridDim.x);
+}
 
 template <class R>
-__global__ void __launch_bounds__(AT) k_alloc_sum_batch(const BoxDev* bxs, int B, uint32_t k0, uint32_t k1,
-                                                        DevScalars* gsc, unsigned long long* partQ) {
-  const int b = alloc_box(bxs, B, blockIdx.x);
+__device__ __forceinline__ void alloc_sum_batch(const BoxDev* bxs, int B, uint32_t k0, uint32_t k1, DevScalars* gsc,
+                                                unsigned long long* partQ, uint32_t g, uint32_t ng) {
+  const int b = alloc_box(bxs, B, g);
   const BoxDev& d = bxs[b];
-  const R rmax = (R)d.sc->rmax;
+  const R rmax = (R)__ldcg(&d.sc->rmax);
   uint64_t acc = 0;
   if (rmax > (R)0) {
-    const int64_t c0 = (int64_t)(blockIdx.x - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+    const int64_t c0 = (int64_t)(g - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
     R v[kAllocItems];
     load_items<R>((const R*)d.emis, c0, d.n3, v);
 #pragma unroll
@@ -1138,15 +1210,15 @@ __global__ void __launch_bounds__(AT) k_alloc_sum_batch(const BoxDev* bxs, int B
   }
   uint64_t incl;
   uint64_t tot = block_scan_incl(acc, &incl);
-  if (threadIdx.x == 0) partQ[blockIdx.x] = tot;
-  if (!last_block_done(&gsc->alloc_counter)) return;
+  if (threadIdx.x == 0) partQ[g] = tot;
+  if (!last_block_done(&gsc->alloc_counter, ng)) return;
   // one warp per box: exclusive scan of its block sums (in place), the
   // systematic-sampling offset and the box's packet total
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < B; i += AT / 32) {
     const BoxDev& e = bxs[i];
     const uint32_t g0 = e.ablk0;
-    const uint32_t g1 = (i + 1 < B) ? bxs[i + 1].ablk0 : gridDim.x;
+    const uint32_t g1 = (i + 1 < B) ? bxs[i + 1].ablk0 : ng;
     uint64_t run = 0;
     for (uint32_t gb = g0; gb < g1; gb += 32) {
       const uint32_t g = gb + lane;
@@ -1178,23 +1250,34 @@ __global__ void __launch_bounds__(AT) k_alloc_sum_batch(const BoxDev* bxs, int B
   }
   if (threadIdx.x == 0) gsc->alloc_counter = 0;
 }
+template <class R>
+__global__ void __launch_bounds__(AT) k_alloc_sum_batch(const BoxDev* bxs, int B, uint32_t k0, uint32_t k1,
+                                                        DevScalars* gsc, unsigned long long* partQ) {
+  alloc_sum_batch<R>(bxs, B, k0, k1, gsc, partQ, blockIdx.x, gridDim.x);
+}
 
+template <class R>
+__device__ __forceinline__ void alloc_prefix_batch(const BoxDev* bxs, int B, const unsigned long long* partQ,
+                                                   unsigned long long* bcap, uint32_t g) {
+  const int b = alloc_box(bxs, B, g);
+  const BoxDev& d = bxs[b];
+  const DevScalars* sc = d.sc;
+  const int64_t c0 = (int64_t)(g - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
+  alloc_prefix_block<R>((const R*)d.emis, d.n3, d.npk, __ldcg(&sc->sumQ), __ldcg(&sc->alloc_u), (R)__ldcg(&sc->rmax),
+                        __ldcg(&partQ[g]), c0, d.P, d.first, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0, bcap);
+}
 template <class R>
 __global__ void __launch_bounds__(AT) k_alloc_prefix_batch(const BoxDev* bxs, int B, const unsigned long long* partQ,
                                                            unsigned long long* bcap) {
-  const int b = alloc_box(bxs, B, blockIdx.x);
-  const BoxDev& d = bxs[b];
-  const DevScalars* sc = d.sc;
-  const int64_t c0 = (int64_t)(blockIdx.x - d.ablk0) * kAllocChunk + (int64_t)threadIdx.x * kAllocItems;
-  alloc_prefix_block<R>((const R*)d.emis, d.n3, d.npk, sc->sumQ, sc->alloc_u, (R)sc->rmax, partQ[blockIdx.x], c0,
-                        d.P, d.first, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0, bcap);
+  alloc_prefix_batch<R>(bxs, B, partQ, bcap, blockIdx.x);
 }
 
 // Emission over the batch packet space (each box padded to a multiple of 32,
-// so a warp's 32 packets belong to one box).
-template <class R>
-__global__ void __launch_bounds__(TT, 4) k_emit_batch(TransportArgs<R> a, const BoxDev* bxs, const BoxStep* bst,
-                                                      int B, uint64_t tot_pk) {
+// so a warp's 32 packets belong to one box).  FRESH: the packet prefixes and
+// box scalars were written earlier in the same launch (read through L2).
+template <class R, bool FRESH>
+__device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const BoxDev* bxs, const BoxStep* bst, int B,
+                                                uint64_t tot_pk) {
   using V = typename Vec4<R>::T;
   __shared__ BoxCounters cnt;
   box_counters_clear(cnt, B);
@@ -1212,20 +1295,25 @@ __global__ void __launch_bounds__(TT, 4) k_emit_batch(TransportArgs<R> a, const 
       cur = b;
       lo_pk = bxs[b].pk0;
       hi_pk = (b + 1 < B) ? bxs[b + 1].pk0 : tot_pk;
-      N = __ldg(bxs[b].P + bxs[b].n3);  // packets actually allocated to this box
+      N = ld_index<FRESH>(bxs[b].P + bxs[b].n3);  // packets actually allocated to this box
     }
     const uint64_t base = gbase - lo_pk;
     if (base >= N) continue;  // padding of the packet space
     const BoxDev& d = bxs[cur];
     const EmitBox<R> e{d.P, d.first, (uint32_t)d.n3, d.n, (const V*)d.vel4, (const R*)d.T, d.tally,
-                       (R)bst[cur].kappa, (R)bst[cur].cth, Stream{a.strm.k0, a.strm.k1, (uint32_t)cur},
-                       Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0};
+                       (R)__ldcg(&bst[cur].kappa), (R)__ldcg(&bst[cur].cth),
+                       Stream{a.strm.k0, a.strm.k1, (uint32_t)cur}, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0};
     // one code path for all sides (the power-of-two specialisation would double
     // the inlined body and spill registers)
-    emit_warp<R, false>(a, e, (uint32_t)base, N, my_abs, my_cross);
+    emit_warp<R, false, FRESH>(a, e, (uint32_t)base, N, my_abs, my_cross);
   }
   if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
   box_counters_flush(cnt, bxs, B);
+}
+template <class R>
+__global__ void __launch_bounds__(TT, 4) k_emit_batch(TransportArgs<R> a, const BoxDev* bxs, const BoxStep* bst,
+                                                      int B, uint64_t tot_pk) {
+  emit_batch_body<R, false>(a, bxs, bst, B, tot_pk);
 }
 
 struct BoxStepArgs {
@@ -1235,25 +1323,61 @@ __global__ void k_set_box_step(BoxStepArgs p, BoxStep* out, int B) {
   for (int b = threadIdx.x; b < B; b += blockDim.x) out[b] = p.s[b];
 }
 
-__global__ void k_transport_end_batch(const BoxDev* bxs, int B, const unsigned long long* bfill, rec_stats* st) {
+__device__ __forceinline__ void transport_end_batch(const BoxDev* bxs, int B, const unsigned long long* bfill,
+                                                    rec_stats* st) {
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const BoxDev& d = bxs[b];
     DevScalars* sc = d.sc;
     unsigned long long q = 0;
     const uint32_t nb = d.nt * d.nt * d.nt;
-    for (uint32_t k = 0; k < nb; ++k) q += bfill[d.bk0 + k];
+    for (uint32_t k = 0; k < nb; ++k) q += __ldcg(&bfill[d.bk0 + k]);
+    // the counters were added by other blocks' atomics: read them through L2
+    const unsigned long long absorbed = __ldcg(&sc->absorbed), capped = __ldcg(&sc->capped);
     sc->qtail = q;
-    sc->tally_total += sc->absorbed;
-    if (sc->capped) sc->flags |= 2;
+    sc->tally_total = __ldcg(&sc->tally_total) + absorbed;
+    if (capped) atomicOr(&sc->flags, 2);
     if (st) {
-      st[b].emitted = sc->emitted;
-      st[b].absorbed = sc->absorbed;
-      st[b].capped = sc->capped;
-      st[b].crossings = sc->crossings;
+      st[b].emitted = __ldcg(&sc->emitted);
+      st[b].absorbed = absorbed;
+      st[b].capped = capped;
+      st[b].crossings = __ldcg(&sc->crossings);
       st[b].queued = q;
-      st[b].flags = sc->flags;
+      st[b].flags = __ldcg(&sc->flags);
     }
   }
+}
+__global__ void k_transport_end_batch(const BoxDev* bxs, int B, const unsigned long long* bfill, rec_stats* st) {
+  transport_end_batch(bxs, B, bfill, st);
+}
+
+// The allocation and the emission of a batched transport call as phases of
+// one persistent cooperative launch, separated by bounded grid barriers: box
+// transport scalars, bucket capacities cleared and the allocation maxima;
+// quantised sums and their scans; packet prefixes; bucket offsets; emission;
+// march chunk prefix.  The allocation phases run the allocation blocks of the
+// per-phase kernels as virtual blocks.  A barrier that gives up ends the launch
+// (flags bit 3 of the batch record) and the march that follows finds no work.
+template <class R>
+__global__ void __launch_bounds__(AT, 4) k_batch_front(TransportArgs<R> a, const BoxDev* bxs, BoxStep* bst,
+                                                       BoxStepArgs bs, int B, uint32_t k0, uint32_t k1,
+                                                       DevScalars* gsc, double* part, unsigned long long* partQ,
+                                                       unsigned long long* cpre, uint32_t n_ablk, uint64_t tot_pk,
+                                                       uint32_t limit) {
+  if (blockIdx.x == 0)
+    for (int b = threadIdx.x; b < B; b += AT) bst[b] = bs.s[b];
+  for (int i = blockIdx.x * AT + threadIdx.x; i < a.nb; i += gridDim.x * AT) a.boff[i] = 0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) gsc->march_next = ~0ull >> 1;  // no march work until the chunks exist
+  for (uint32_t g = blockIdx.x; g < n_ablk; g += gridDim.x) alloc_max_batch<R>(bxs, B, gsc, part, g, n_ablk);
+  if (!grid_barrier(&gsc->bar, &gsc->flags, limit)) return;
+  for (uint32_t g = blockIdx.x; g < n_ablk; g += gridDim.x) alloc_sum_batch<R>(bxs, B, k0, k1, gsc, partQ, g, n_ablk);
+  if (!grid_barrier(&gsc->bar, &gsc->flags, limit)) return;
+  for (uint32_t g = blockIdx.x; g < n_ablk; g += gridDim.x) alloc_prefix_batch<R>(bxs, B, partQ, a.boff, g);
+  if (!grid_barrier(&gsc->bar, &gsc->flags, limit)) return;
+  if (blockIdx.x == 0) bucket_offsets_block<AT>(a.boff, a.bfill, a.nb);
+  if (!grid_barrier(&gsc->bar, &gsc->flags, limit)) return;
+  emit_batch_body<R, true>(a, bxs, bst, B, tot_pk);
+  if (!grid_barrier(&gsc->bar, &gsc->flags, limit)) return;
+  if (blockIdx.x == 0) bucket_scan_block<AT>(a.bfill, cpre, a.nb, gsc, a.chunk);
 }
 
 template <class R>
@@ -1261,17 +1385,8 @@ cudaError_t run_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
   const int B = c->n_boxes;
   const uint32_t k0 = (uint32_t)c->params.seed, k1 = (uint32_t)(c->params.seed >> 32) ^ (uint32_t)step;
   const int nb = c->tot_buckets;
-  {
-    GroupTimer t(c, kTAlloc, 5);
-    BoxStepArgs bs;
-    for (int b = 0; b < B; ++b) transport_scalars(c->cosmo, (int)c->hbx[b].n, z, &bs.s[b].kappa, &bs.s[b].cth);
-    k_set_box_step<<<1, kMaxBoxes, 0, c->stream>>>(bs, c->bstep, B);
-    k_alloc_max_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, c->gsc, c->part);
-    k_alloc_sum_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, k0, k1, c->gsc, c->partQ);
-    cudaMemsetAsync(c->bcap, 0, sizeof(unsigned long long) * nb, c->stream);
-    k_alloc_prefix_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, c->partQ, c->bcap);
-    k_bucket_offsets<<<1, 1024, 0, c->stream>>>(c->bcap, c->bfill, nb);
-  }
+  BoxStepArgs bs;
+  for (int b = 0; b < B; ++b) transport_scalars(c->cosmo, (int)c->hbx[b].n, z, &bs.s[b].kappa, &bs.s[b].cth);
   TransportArgs<R> a;
   std::memset(&a, 0, sizeof(a));
   a.quant = (const R*)c->quant;
@@ -1285,18 +1400,52 @@ cudaError_t run_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
   a.cpre = c->cpre;
   a.chunk = (uint32_t)c->tune.march_chunk;
   a.refill = c->tune.march_refill;
-  {
-    GroupTimer t(c, kTEmit, 2);
-    k_emit_batch<R><<<c->sm_count * c->tune.emit_blocks_per_sm, TT, 0, c->stream>>>(a, c->bx, c->bstep, B, c->tot_pk);
-    k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->gsc, a.chunk);
+  if (c->batch_front_grid == 0) {  // resident blocks of the persistent front (cooperative launch)
+    int per_sm = 0, coop = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front<R>, AT, 0);
+    cudaGetLastError();
+    c->batch_front_grid = (e == cudaSuccess && coop && per_sm > 0) ? per_sm * c->sm_count : -1;
+  }
+  if (c->batch_front_grid > 0) {
+    // allocation + emission in one persistent launch, then the march (which closes the call)
+    GroupTimer t(c, kTEmit, 1);
+    const BoxDev* bxs = c->bx;
+    BoxStep* bst = c->bstep;
+    DevScalars* gsc = c->gsc;
+    double* part = c->part;
+    unsigned long long* partQ = c->partQ;
+    unsigned long long* cpre = c->cpre;
+    uint32_t n_ablk = (uint32_t)c->tot_ablk;
+    uint64_t tot_pk = c->tot_pk;
+    uint32_t limit = c->wait_limit;
+    int Bv = B;
+    uint32_t k0v = k0, k1v = k1;
+    void* args[] = {&a, &bxs, &bst, &bs, &Bv, &k0v, &k1v, &gsc, &part, &partQ, &cpre, &n_ablk, &tot_pk, &limit};
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_batch_front<R>, c->batch_front_grid, AT, args, 0, c->stream);
+    if (e != cudaSuccess) return e;
+  } else {
+    {
+      GroupTimer t(c, kTAlloc, 5);
+      k_set_box_step<<<1, kMaxBoxes, 0, c->stream>>>(bs, c->bstep, B);
+      k_alloc_max_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, c->gsc, c->part);
+      k_alloc_sum_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, k0, k1, c->gsc, c->partQ);
+      cudaMemsetAsync(c->bcap, 0, sizeof(unsigned long long) * nb, c->stream);
+      k_alloc_prefix_batch<R><<<c->tot_ablk, AT, 0, c->stream>>>(c->bx, B, c->partQ, c->bcap);
+      k_bucket_offsets<<<1, 1024, 0, c->stream>>>(c->bcap, c->bfill, nb);
+    }
+    {
+      GroupTimer t(c, kTEmit, 2);
+      k_emit_batch<R><<<c->sm_count * c->tune.emit_blocks_per_sm, TT, 0, c->stream>>>(a, c->bx, c->bstep, B,
+                                                                                      c->tot_pk);
+      k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->gsc, a.chunk);
+    }
   }
   {
     GroupTimer t(c, kTMarch, 1);
-    k_march<R, false, true><<<c->sm_count * c->tune.march_blocks_per_sm, TT, 0, c->stream>>>(a, c->bx, B);
-  }
-  {
-    GroupTimer t(c, kTEnd, 1);
-    k_transport_end_batch<<<1, kMaxBoxes, 0, c->stream>>>(c->bx, B, c->bfill, st);
+    k_march<R, false, true><<<c->sm_count * c->tune.march_blocks_per_sm, TT, 0, c->stream>>>(a, c->bx, B, c->bstep,
+                                                                                             st);
   }
   return cudaGetLastError();
 }

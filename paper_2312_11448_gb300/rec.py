@@ -75,7 +75,11 @@ A_2P1S = 6.2649e8  # 2p -> 1s decay rate, 1/s
 
 
 class RecError(RuntimeError):
-    pass
+    """A failed call; .status is the rec_status it returned (None for binding-side checks)."""
+
+    def __init__(self, msg, status=None):
+        super().__init__(msg)
+        self.status = status
 
 
 def lib():
@@ -110,6 +114,8 @@ def lib():
                                                  P(C.c_uint64)]
         L.lya_mc_mixing_fraction.argtypes = [vp, vp, C.c_uint64, P(d), i32, vp, vp]
         L.rec_volume_stats.argtypes = [vp, vp]
+        L.rec_set_wait_limit.argtypes = [vp, u32]
+        L.rec_sync.argtypes = [vp]
         L.rec_free.argtypes = [vp]
         L.rec_free.restype = None
         L.rec_last_error.argtypes = [vp]
@@ -118,7 +124,7 @@ def lib():
                   "rec_step_adjoint", "rec_xe_adjoint", "rec_transport_params", "rec_objective", "rec_timing", "rec_kernel_times",
                   "lya_scatter_mc", "lya_voigt", "rec_step_trbdf2", "lya_mc_scalars",
                   "lya_mc_redistribution_host", "lya_voigt_mixed", "rec_set_f_alpha", "lya_mc_mixing_fraction",
-                  "rec_volume_stats"):
+                  "rec_volume_stats", "rec_set_wait_limit", "rec_sync"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -266,7 +272,7 @@ class Batch:
 
     def _check(self, rc, what):
         if rc != REC_OK:
-            raise RecError(f"{what}: {lib().rec_last_error(self.ctx).decode()} (status {rc})")
+            raise RecError(f"{what}: {lib().rec_last_error(self.ctx).decode()} (status {rc})", rc)
 
     def state_init(self, z):
         self._check(lib().rec_state_init(self.ctx, z), "rec_state_init")
@@ -283,6 +289,12 @@ class Batch:
     def graph_step(self, step, z_from, z_to):
         self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, C.c_void_p(self._stats.data_ptr())),
                     "rec_graph_step")
+
+    def set_wait_limit(self, polls):
+        self._check(lib().rec_set_wait_limit(self.ctx, int(polls)), "rec_set_wait_limit")
+
+    def sync(self):
+        self._check(lib().rec_sync(self.ctx), "rec_sync")
 
     def volume_stats(self):
         """rec_volume_stats: X_e, lambda and S1s of every box's current state into the records."""
@@ -393,7 +405,7 @@ class Box:
     # ---- calls -----------------------------------------------------------------------
     def _check(self, rc, what):
         if rc != REC_OK:
-            raise RecError(f"{what}: {lib().rec_last_error(self.ctx).decode()} (status {rc})")
+            raise RecError(f"{what}: {lib().rec_last_error(self.ctx).decode()} (status {rc})", rc)
 
     def state_init(self, z):
         self._check(lib().rec_state_init(self.ctx, z), "rec_state_init")
@@ -421,6 +433,15 @@ class Box:
     def graph_step(self, step, z_from, z_to, slot=0):
         """transport(step, z_from) + step(step, z_from, z_to) as one CUDA graph launch."""
         self._check(lib().rec_graph_step(self.ctx, int(step), z_from, z_to, self._slot(slot)), "rec_graph_step")
+
+    def set_wait_limit(self, polls):
+        """rec_set_wait_limit: polls before a bounded device-side wait gives up."""
+        self._check(lib().rec_set_wait_limit(self.ctx, int(polls)), "rec_set_wait_limit")
+
+    def sync(self):
+        """rec_sync: wait for the stream; raises RecError (status REC_ETIMEOUT) if a
+        bounded device-side wait expired since the last sync."""
+        self._check(lib().rec_sync(self.ctx), "rec_sync")
 
     def volume_stats(self, slot=0):
         """rec_volume_stats: X_e, lambda and S1s of the current state into record `slot`."""
