@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-box measurement")
     ap.add_argument("--no-scatter", action="store_true", help="skip the scattering Monte-Carlo measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (reverse sweep) measurement")
+    ap.add_argument("--no-512", action="store_true", help="skip the 512^3 / 1e9-packet measurement")
     return ap.parse_args()
 
 
@@ -341,6 +342,57 @@ def time_adjoint(cfg, zs, n_window=20, seed=1):
             "full_run_memory_estimate": full, "gpu_launch_groups": "transport, rec_step, rec_step_adjoint"}
 
 
+def time_512(W=2, K=3):
+    """The 512^3 configuration (sigma_lnrho 1.2, sigma_v 2 km/s, 1e9 packets per
+    step, 600 steps z 1800 -> 500), mixed form, from the Saha state at the node
+    nearest z = 1140 (the 256^3 line's redshift; advancing there step by step
+    would take minutes), W untimed and K timed steps."""
+    import torch
+    from paper_2312_11448_gb300.inputs import CONFIGS, z_schedule
+    cfg = CONFIGS["box512_mixed"]
+    zs = z_schedule(cfg.z_start, cfg.z_end, cfg.n_steps)
+    k0 = int(np.argmin(np.abs(zs - 1140.0)))
+    box, delta, U = make_box(cfg, "mixed", 1)
+    box.state_init(zs[k0])
+    advance(box, zs, k0, k0 + W)
+    box.ensure_stats(K)
+    box.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(box.stream)
+    for k in range(K):
+        s = k0 + W + k
+        box.transport(s, zs[s], slot=k)
+        box.step(s, zs[s], zs[s + 1], slot=k)
+    e1.record(box.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = box.kernel_times()
+    st = box.stats_all()[:K]
+    box.close()
+    del delta, U
+    _FIELDS.pop((cfg, 1), None)  # 2 GB of host fields
+    torch.cuda.empty_cache()
+    emitted = sum(r["emitted"] for r in st) / K
+    queued = sum(r["queued"] for r in st) / K
+    crossings = sum(r["crossings"] for r in st) / K
+    passes = sum(r["newton_passes"] for r in st) / K
+    n3 = cfg.n ** 3
+    mb = method_bytes("mixed", n3, emitted, queued, crossings, passes)
+    peak, kind = measured_peaks()
+    march_ms = kt["march"][0] / K
+    return {"workload": (f"512^3 periodic box (24 kpc), sigma_lnrho 1.2, sigma_v 2 km/s, {cfg.n_packets:.0e} Lya "
+                         f"packets/step, tally mixing, mixed form, steps {k0 + W}+ of {cfg.n_steps} (z "
+                         f"{zs[k0]:.0f}) from the Saha state at step {k0}"),
+            "value": n3 * K / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / K, "steps": K, "warmup": W,
+            "packets_per_s": emitted * K / (ms * 1e-3), "crossings_per_packet": crossings / max(emitted, 1),
+            "kernel_ms_per_step": {g: v[0] / K for g, v in kt.items() if v[1]},
+            "march_roofline": {"bound": "hbm", "achieved": mb["march"] / (march_ms * 1e-3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": mb["march"] / (march_ms * 1e-3) / 1e9 / peak,
+                               "peak_source": f"{kind} hbm_gbs"},
+            "whole_step_frac": mb["whole"] / (ms / K * 1e-3) / 1e9 / peak}
+
+
 def traj_k(S):
     return max(1, math.ceil(math.sqrt(S)))
 
@@ -426,8 +478,24 @@ def time_batched(W, K, prep=60, n_boxes=64):
 # GB300 FP64 peak from its nominal 1.25 TFLOP/s: 0.625e12 fused multiply-adds per
 # second; a separate multiply or add issues at the same rate, so the peak counts
 # FP64 instructions.
-FP64_INSTR_PER_S = 0.625e12
-MC_OPS_PER_STEP, MC_OPS_PER_SCATTER = 70, 400  # FP64 instructions, counted from the kernel source
+# Roofline of the Monte-Carlo kernels (profiles/k_scatter_mc_z1700.md): ncu
+# counts on one launch of the bench workload (8192 photons capped at 2e4 steps,
+# 1.57e8 photon steps, one scattering per 10.5 steps), amortised per photon
+# step.  The binary64 kernel is bound by its binary64 pipe (127.8 SM-cycles of
+# that pipe per step: sm__pipe_fp64_cycles_active x sm__cycles_active / steps);
+# the mixed kernel by instruction issue (24.7 warp instructions per step:
+# smsp__inst_executed / steps).  Peaks: every SM's binary64 pipe busy every
+# cycle, and one warp instruction per cycle per SM sub-partition, at the
+# 2070 MHz maximum SM clock of the 152 SMs.
+_SM_CYCLES_PER_S = 152 * 2.070e9
+MC_PROFILE = {
+    "fp64": {"bound": "fp64-pipe", "kernel": "k_scatter (binary64)", "per_step": 127.8, "per_scatter": 0.0,
+             "peak": _SM_CYCLES_PER_S, "unit": "G SM-cycles/s of the binary64 pipe",
+             "note": "127.8 binary64-pipe SM-cycles per photon step (ncu), peak = every SM's pipe every cycle"},
+    "mixed": {"bound": "issue", "kernel": "k_scatter_mixed (binary32 + double-float)", "per_step": 24.7,
+              "per_scatter": 0.0, "peak": 4 * _SM_CYCLES_PER_S, "unit": "G warp instructions/s",
+              "note": "24.7 warp instructions per photon step (ncu), peak = one per cycle per SM sub-partition"},
+}
 
 
 def scatter_workload():
@@ -436,42 +504,46 @@ def scatter_workload():
     return n, z, density_field(n, 0.8, 11).ravel(), velocity_field(n, 1.0, 11)
 
 
-def time_scatter(cpu=True):
-    """Appendix A Monte Carlo (lya_scatter_mc, FP64 arithmetic): one photon per
-    resident lane in a 32^3 box (sigma_lnrho 0.8, sigma_v 1 km/s, Saha x_e) at
-    z = 1700 with the true expansion rate; photons end by photo-ionisation after
-    ~2e4 scatterings.  Throughput over the whole launch, tail included."""
+def time_scatter(cpu=True, arith="fp64", photons_per_lane=1):
+    """Appendix A Monte Carlo (lya_scatter_mc) in a 32^3 box (sigma_lnrho 0.8,
+    sigma_v 1 km/s, Saha x_e) at z = 1700 with the true expansion rate; photons
+    end by photo-ionisation after ~2e4 scatterings.  Throughput over the whole
+    launch, tail included.  arith: "fp64" (binary64, the oracle's operation
+    order) or "mixed" (binary32 with double-float position and frequency);
+    photons_per_lane photons per resident lane (lanes refill from a counter,
+    so more photons than lanes shorten the relative tail)."""
     import torch
     from paper_2312_11448_gb300 import rec
     n, z, d, U = scatter_workload()
     box = rec.Box(n, d, U, 1000, precision="mixed", mixing="full", seed=11)
     box.state_init(z)
     lanes = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 2 * 256
-    kw = dict(x_lost=2000.0, max_steps=1_000_000)
+    n_ph = lanes * photons_per_lane
+    kw = dict(x_lost=2000.0, max_steps=1_000_000, arith=arith)
     box.scatter_mc(z, 2048, records=False, **kw)  # warm-up (module load, Voigt nodes)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(box.stream)
-    _, st = box.scatter_mc(z, lanes, records=False, step=1, **kw)
+    _, st = box.scatter_mc(z, n_ph, records=False, step=1, **kw)
     e1.record(box.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     steps_s = st["steps"] / (ms * 1e-3)
     scat_s = st["scatterings"] / (ms * 1e-3)
-    ach = MC_OPS_PER_STEP * steps_s + MC_OPS_PER_SCATTER * scat_s
     out = {"workload": f"Appendix A Monte Carlo, {n}^3 box (24 kpc, sigma_lnrho 0.8, sigma_v 1 km/s), Saha x_e, "
-                       f"z = {z:.0f}, zeta = 1, eps = 0.1, {lanes} photons (one per resident lane), FP64 arithmetic",
-           "photons_per_s": lanes / (ms * 1e-3), "steps_per_s": steps_s, "scatterings_per_s": scat_s, "ms": ms,
-           "photons": lanes, "fates": dict(zip(rec.MC_FATES, st["count"])), "sampler_caps": st["sampler_caps"],
-           "steps_per_photon": st["steps"] / lanes,
-           "roofline": {"bound": "alu", "kernel": "k_scatter (FP64 pipe)", "achieved": ach / 1e9,
-                        "peak": FP64_INSTR_PER_S / 1e9, "unit": "G FP64 instructions/s", "frac": ach / FP64_INSTR_PER_S,
-                        "traffic": None,
-                        "note": f"{MC_OPS_PER_STEP} FP64 instructions per step and {MC_OPS_PER_SCATTER} per scattering "
-                                "counted from the source; peak = nominal FP64 rate 1.25 TFLOP/s as instructions"},
-           "gpu_launches": 2}
+                       f"z = {z:.0f}, zeta = 1, eps = 0.1, {n_ph} photons ({photons_per_lane} per resident lane), "
+                       f"{'binary64' if arith == 'fp64' else 'mixed (binary32 + double-float)'} arithmetic",
+           "arith": arith, "photons_per_s": n_ph / (ms * 1e-3), "steps_per_s": steps_s, "scatterings_per_s": scat_s,
+           "ms": ms, "photons": n_ph, "fates": dict(zip(rec.MC_FATES, st["count"])),
+           "sampler_caps": st["sampler_caps"], "steps_per_photon": st["steps"] / n_ph, "gpu_launches": 2}
+    prof = MC_PROFILE.get(arith)
+    if prof:  # instruction counts per step and per scattering from the committed ncu summary
+        ach = prof["per_step"] * steps_s + prof["per_scatter"] * scat_s
+        out["roofline"] = {"bound": prof["bound"], "kernel": prof["kernel"], "achieved": ach / 1e9,
+                           "peak": prof["peak"] / 1e9, "unit": prof["unit"], "frac": ach / prof["peak"],
+                           "traffic": None, "note": prof["note"]}
     if cpu:
-        out["cpu_baseline"] = scatter_cpu_baseline(box, n, z, lanes, kw)
+        out["cpu_baseline"] = scatter_cpu_baseline(box, n, z, n_ph, kw)
     box.close()
     return out
 
@@ -638,6 +710,15 @@ def run_ours(args):
         fp64 = time_form(cfg, zs, "fp64", W, max(5, K // 3), seed=rank_seed(rank), dist=dist, clocks=clocks,
                          prep=args.prep)
     e2e = None if args.no_e2e else time_e2e(cfg, zs, mixed, K)
+    big = None
+    if not args.no_512 and world == 1:
+        for r in (fp64,):
+            if r:
+                r["box"].close()
+        torch.cuda.empty_cache()
+        t0 = clocks.mark()
+        big = time_512()
+        clocks.window(t0, clocks.mark())
     adjoint = None
     if not args.no_adjoint and world == 1:
         for r in (fp64,):
@@ -661,6 +742,9 @@ def run_ours(args):
         t0 = clocks.mark()
         try:
             scatter = time_scatter(cpu=not args.no_cpu)
+            scatter["mixed_arith"] = time_scatter(cpu=False, arith="mixed", photons_per_lane=4)
+            scatter["mixed_arith"]["photons_per_s_over_fp64"] = (scatter["mixed_arith"]["photons_per_s"] /
+                                                                 scatter["photons_per_s"])
         except Exception as exc:  # a secondary line: report, keep the main measurement
             scatter = {"error": f"{type(exc).__name__}: {exc}"}
         clocks.window(t0, clocks.mark())
@@ -744,6 +828,8 @@ def run_ours(args):
         out["graph"] = {"ms_per_step": gms / K, "value": world * n3 * K / (gms * 1e-3), "unit": "cell-steps/s",
                         "api": "rec_graph_step: transport + rec_step captured as one CUDA graph per step, "
                                "executable graph updated in place", "steps": K}
+    if big:
+        out["box512"] = big
     if adjoint:
         if fp64:
             f_ms = ms_fp64 / K64

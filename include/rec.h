@@ -215,7 +215,11 @@ rec_status rec_step_trbdf2(rec_ctx* ctx, int32_t step, double z_from, double z_t
  * contexts) for the following rec_step and rec_graph_step calls.  Sec. V takes
  * the share from the Monte-Carlo mixing fraction f_alpha(D) of Sec. III.B (the
  * fraction of Ly-alpha photons destroyed farther than D from where they were
- * emitted), which changes with redshift; lya_scatter_mc gives it.  Host-side
+ * emitted), which changes with redshift; lya_scatter_mc and
+ * lya_mc_mixing_fraction give it.  f_alpha = 0 runs the local (no-mixing) limit
+ * of REC_MIX_LOCAL and f_alpha = 1 full mixing.  The kernels a step launches
+ * differ between f_alpha = 0 and f_alpha > 0, so the next rec_graph_step after
+ * the share crosses zero re-instantiates its executable graph.  Host-side
  * only: takes effect from the next call enqueued.
  * Errors: REC_EINVAL (not a partial-mixing context, f_alpha outside [0, 1]). */
 rec_status rec_set_f_alpha(rec_ctx* ctx, double f_alpha);
@@ -250,7 +254,9 @@ rec_status rec_set_tuning(rec_ctx* ctx, const rec_tuning* tuning);
  * the array's device address, which may load the module), so make it before
  * any stream capture.  Each call clears the scalar record on the stream first.
  * Calls that overlap in time on one device (several streams or host threads)
- * share the array and race: serialise them.
+ * share the array and race: serialise them.  The array's device address is
+ * looked up once per device and kept for the process: do not use this entry
+ * point after a cudaDeviceReset of that device.
  * Errors: REC_EINVAL, REC_ECUDA; rec_last_error(NULL) gives the cause. */
 rec_status rec_step_noalloc(const rec_params* params, const rec_box* box, double z_from, double z_to,
                             void* cuda_stream, rec_stats* dev_stats);

@@ -83,6 +83,49 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)bits);
 }
 
+// x + d as a binary64 value for the increment d of a backward-Euler state,
+// with integer operations in the common case |d| < x/4: d is aligned to x's
+// last place 2^(ex - 1075) and added to x's significand, carrying or borrowing
+// at most one binade.  The result is x + d rounded to 53 bits (the bits of d
+// beyond x's last place rounded to nearest, ties away).  Larger increments,
+// special values and x outside the normal range take one binary64 addition,
+// which on this chip issues on the slow binary64 pipe.
+// The rare case of add_small, kept out of line so that the compiler branches to
+// it instead of predicating a binary64 addition for every cell.
+static __device__ __noinline__ double add_wide(double x, float d) { return x + f2d_bits(d); }
+
+__device__ __forceinline__ double add_small(double x, float d) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t ud = __float_as_uint(d);
+  const uint32_t ed = (ud >> 23) & 0xffu;
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  // d's significand sd = 1.m (24 bits) at 2^(ed - 150); right shift into x's last place
+  const int sh = (ex - 1075) - ((int)ed - 150);
+  if ((ed != 0u && sh < -26) || ed == 0xffu || ex == 0 || ex >= 0x7fe) return add_wide(x, d);
+  const uint64_t sd = (uint64_t)((ud & 0x7fffffu) | 0x800000u);
+  uint64_t add;
+  if (ed == 0u || sh >= 25) {
+    add = 0;  // zero, subnormal or below half a last place of x
+  } else if (sh > 0) {
+    add = (sd >> sh) + ((sd >> (sh - 1)) & 1u);
+  } else {
+    add = sd << (-sh);  // d within 2^29 of x's last place: exact
+  }
+  // x's significand with the implicit bit, signed addition of d
+  int64_t S = (int64_t)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  S = (ud & 0x80000000u) ? S - (int64_t)add : S + (int64_t)add;
+  int e = ex;
+  if (S >= (int64_t)0x20000000000000ll) {  // carried into the next binade: round the dropped bit
+    S = (S >> 1) + (S & 1);
+    ++e;
+  } else if (S < (int64_t)0x10000000000000ll) {  // borrowed from the binade below (one bit suffices)
+    S <<= 1;
+    --e;
+  }
+  const uint64_t out = (b & 0x8000000000000000ull) | ((uint64_t)e << 52) | ((uint64_t)S & 0xfffffffffffffull);
+  return __longlong_as_double((long long)out);
+}
+
 // hi + lo rounded to one binary32 value
 __device__ __forceinline__ float df_to_float(dfloat a) { return __fadd_rn(a.hi, a.lo); }
 

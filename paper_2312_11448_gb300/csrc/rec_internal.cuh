@@ -60,6 +60,12 @@ struct DevScalars {
   uint32_t alloc_counter;
   int32_t emis_valid;
   GridBarrier bar;  // grid barrier of the persistent batched launches (batch-wide record)
+  // binary32 copies of the current iterate for the mixed form's passes (set
+  // with lam, so that no pass converts binary64 scalars per thread)
+  float lamf;        // lambda
+  float Gf;          // G = (1 - C) lambda + C beta e_alpha
+  float Ghi, Glo;    // G as a double-float pair
+  float wscale;      // S1s / tally_total (0 without tallies)
 };
 
 // Batched contexts (several boxes in one context, one launch per phase for

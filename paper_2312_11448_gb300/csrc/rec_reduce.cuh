@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rec_df.cuh"
+
 namespace rec {
 
 // Sum K values over the block (fixed shuffle tree, then warps in order).
@@ -34,6 +36,13 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
       v[k] = s;
     }
   }
+}
+
+// The first K entries of a longer array.
+template <int K, int NT, int N>
+__device__ __forceinline__ void block_sum_first(double (&v)[N]) {
+  static_assert(K <= N, "block_sum_first: K exceeds the array");
+  block_sum<K, NT>(*reinterpret_cast<double(*)[K]>(&v[0]));
 }
 
 template <int NT>
@@ -68,6 +77,17 @@ __device__ __forceinline__ bool last_block_done(uint32_t* counter) { return last
 // In the last block: combine K partial sums of nblk blocks (layout
 // part[b*stride + k]) in a fixed order.  Result valid in thread 0.
 template <int K, int NT>
+__device__ __forceinline__ void combine_partials(const double* part, int nblk, int stride, double (&out)[K]);
+// Combined into the first K entries of a longer array (the rest set to zero).
+template <int K, int NT, int N>
+__device__ __forceinline__ void combine_partials_first(const double* part, int nblk, int stride, double (&out)[N]) {
+  static_assert(K <= N, "combine_partials_first: K exceeds the array");
+#pragma unroll
+  for (int k = K; k < N; ++k) out[k] = 0.0;
+  combine_partials<K, NT>(part, nblk, stride, *reinterpret_cast<double(*)[K]>(&out[0]));
+}
+
+template <int K, int NT>
 __device__ __forceinline__ void combine_partials(const double* part, int nblk, int stride, double (&out)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) out[k] = 0.0;
@@ -97,5 +117,49 @@ struct Kahan32 {
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
+
+// Block sum of K compensated binary32 accumulators into binary64 (result in
+// thread 0).  The warp tree adds the (s, -c) pairs in double-float arithmetic
+// (binary32 operations only); lane 0 of each warp widens its pair once, and
+// thread 0 adds the warps in order in binary64.  On GB300 the binary64 pipe
+// is slow, so this keeps the per-thread reduction off it.
+template <int K, int NT, int N>
+__device__ __forceinline__ void block_sum_kahan(const Kahan32 (&acc)[K], double (&out)[N]) {
+  static_assert(K <= N, "block_sum_kahan: K exceeds the output");
+  __shared__ double sm[NT / 32][K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float hi[K], lo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const dfloat p = df_fast_two_sum(acc[k].s, -acc[k].c);
+    hi[k] = p.hi;
+    lo[k] = p.lo;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float h2 = __shfl_down_sync(0xffffffffu, hi[k], off);
+      const float l2 = __shfl_down_sync(0xffffffffu, lo[k], off);
+      const dfloat r = df_add(dfloat{hi[k], lo[k]}, dfloat{h2, l2});
+      hi[k] = r.hi;
+      lo[k] = r.lo;
+    }
+  }
+  __syncthreads();  // sm may still be read by a previous call
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[warp][k] = (double)hi[k] + (double)lo[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = sm[0][k];
+      for (int w = 1; w < NT / 32; ++w) t += sm[w][k];
+      out[k] = t;
+    }
+  }
+}
 
 }  // namespace rec

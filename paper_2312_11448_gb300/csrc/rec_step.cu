@@ -35,6 +35,20 @@ namespace {
 
 constexpr int NT = kPassThreads;
 
+struct CoefF32 {
+  float dt, H2, nH, Tg, kc, opf, hq, fa, pb, pc, pd;
+  float kd, H;  // drag coefficient per unit x and H, for the final pass
+};
+// Binary32 coefficients of a substep, formed once on the host.
+__host__ __device__ inline CoefF32 coef_f32(const StepCoef& k) {
+  CoefF32 f;
+  f.dt = (float)k.dt; f.H2 = (float)(2.0 * k.H); f.nH = (float)k.nH; f.Tg = (float)k.Tg; f.kc = (float)k.kc;
+  f.opf = (float)(1.0 + k.fHe); f.hq = (float)k.hq; f.fa = (float)k.fa; f.pb = (float)k.pb; f.pc = (float)k.pc;
+  f.pd = (float)k.pd;
+  f.kd = (float)k.kd; f.H = (float)k.H;
+  return f;
+}
+
 struct PassArgs {
   int64_t n3;
   const void* delta;
@@ -47,6 +61,7 @@ struct PassArgs {
   DevScalars* sc;
   double* part;
   StepCoef k;
+  CoefF32 kf;       // k in binary32 (mixed form)
   const void* div;  // partial mixing: velocity divergence per cell (working precision)
   double fmix;      // partial mixing: share f of the full-mixing rate (0 < f <= 1)
 };
@@ -91,16 +106,6 @@ __device__ __forceinline__ double root_f64(double A, double s, double G, double 
 }
 
 // --------------------------------------------------------------- MIXED cell
-struct CoefF32 {
-  float dt, H2, nH, Tg, kc, opf, hq, fa, pb, pc, pd;
-};
-__device__ __forceinline__ CoefF32 coef_f32(const StepCoef& k) {
-  CoefF32 f;
-  f.dt = (float)k.dt; f.H2 = (float)(2.0 * k.H); f.nH = (float)k.nH; f.Tg = (float)k.Tg; f.kc = (float)k.kc;
-  f.opf = (float)(1.0 + k.fHe); f.hq = (float)k.hq; f.fa = (float)k.fa; f.pb = (float)k.pb; f.pc = (float)k.pc;
-  f.pd = (float)k.pd;
-  return f;
-}
 
 struct CellF32 {
   float Tn, al, n, A, s, xf, yf;
@@ -143,26 +148,54 @@ __device__ __forceinline__ CellF32 cell_f32(const CoefF32& f, int mixing, float 
 
 // Roots in both forms: x' = 2c/(B + sqrt(D)) and y' = 1 - x' = 2(A + y)/(2A + B + sqrt(D)),
 // D = B^2 + 4Ac; neither subtracts.  d x'/dG = s (1 - x') / (2 A x' + B) = s y' / sqrt(D).
-// They feed the Newton sums for lambda.  A few ulp of binary32 in each term
-// move the root lambda by a relative few 1e-7 (the form's tolerance is 1e-4),
-// so the square root and the three quotients use the hardware approximations
-// (reciprocal square root, reciprocal): the evaluation pass is bound by its
-// instruction count, and the correctly rounded forms cost about four times as
-// many instructions.
+// They feed the sums whose difference F = S0 - lambda S1 is the lambda
+// equation; in stiff cells (2 A x' + s lambda >> 1, early in recombination)
+// its derivative (1 - C) S2 - S1 cancels to a small fraction of S1, so the
+// square root and the quotients are correctly rounded.  With d2xdG2:
+// d^2 x'/dG^2 = -2 x'_G (A x'_G + s) / sqrt(D) (the quadratic differentiated
+// twice), for the Halley step of the mixed form.
 __device__ __forceinline__ void root_f32(float A, float s, float G, float x, float y, float* xr, float* yr,
-                                         float* dxdG) {
+                                         float* dxdG, float* d2xdG2 = nullptr) {
   float sG = s * G;
   float B = 1.0f + sG;
   float cc = x + sG;
-  const float D = B * B + 4.0f * A * cc;
-  const float rs = rsqrtf(D);
-  const float sq = D * rs;
-  *xr = fdiv(2.0f * cc, B + sq);
-  *yr = fdiv(2.0f * (A + y), 2.0f * A + B + sq);
-  if (dxdG) *dxdG = s * (*yr) * rs;
+  float sq = __fsqrt_rn(B * B + 4.0f * A * cc);
+  *xr = __fdiv_rn(2.0f * cc, B + sq);
+  *yr = __fdiv_rn(2.0f * (A + y), 2.0f * A + B + sq);
+  if (dxdG) *dxdG = __fdiv_rn(s * (*yr), sq);
+  if (d2xdG2) *d2xdG2 = __fdiv_rn(-2.0f * (*dxdG) * (A * (*dxdG) + s), sq);
 }
 
 // -------------------------------------------------------------- kernels
+// Binary32 copies of the iterate for the mixed form's passes (one thread).
+__device__ __forceinline__ void set_mixed_scal(DevScalars* sc) {
+  const double G = sc->omC * sc->lam + sc->G0;
+  const dfloat Gd = df_from_double(G);
+  sc->lamf = (float)sc->lam;
+  sc->Gf = (float)G;
+  sc->Ghi = Gd.hi;
+  sc->Glo = Gd.lo;
+  sc->wscale = sc->tally_total > 0 ? (float)(sc->S1s / (double)sc->tally_total) : 0.0f;
+}
+
+// The same as the mixed form's passes read them: through L2 when other blocks
+// of the same launch may have written them.
+struct MixedScal {
+  float lamf, Gf, wscale;
+  dfloat Gd;
+};
+__device__ __forceinline__ MixedScal mixed_scal(const DevScalars* sc, bool via_l2) {
+  MixedScal m;
+  if (via_l2) {
+    m.lamf = __ldcg(&sc->lamf); m.Gf = __ldcg(&sc->Gf); m.wscale = __ldcg(&sc->wscale);
+    m.Gd = dfloat{__ldcg(&sc->Ghi), __ldcg(&sc->Glo)};
+  } else {
+    m.lamf = sc->lamf; m.Gf = sc->Gf; m.wscale = sc->wscale;
+    m.Gd = dfloat{sc->Ghi, sc->Glo};
+  }
+  return m;
+}
+
 // Substep prologue: C from the device sum S1s, Newton start.
 __device__ void substep_begin(DevScalars* sc, const StepCoef& k, double n3) {
   double n1s_mean = k.nH * sc->S1s / n3;
@@ -176,6 +209,7 @@ __device__ void substep_begin(DevScalars* sc, const StepCoef& k, double n3) {
     guess = sc->lam_state * fmin(2.0, fmax(0.5, sc->lam_state / sc->lam_prev));
   if (!(guess > 0.0)) guess = 1e-30;
   sc->lam = guess;
+  set_mixed_scal(sc);
   sc->conv = 0;
   sc->passes = 0;
   sc->counter = 0;
@@ -199,12 +233,48 @@ __device__ void newton_update(DevScalars* sc, double S0, double S1, double S2, d
   double rel = fabs(step) / lam;
   const double prev = sc->passes > 0 ? sc->last_step : HUGE_VAL;
   sc->lam = lnew;
+  set_mixed_scal(sc);
   sc->passes += 1;
   sc->last_step = rel;
   // quadratic convergence: a step below tol leaves an error of order tol^2 in lnew;
   // a small step that no longer shrinks is the rounding floor of F
   if (Fp < 0.0 && (rel <= tol || (rel <= 1e-3 && rel >= 0.5 * prev))) sc->conv = 1;
   else if (sc->passes >= kNewtonMaxPasses) sc->flags |= 1;
+}
+
+// Halley step for the mixed form (last block, thread 0): with
+// F = S0 - lambda S1, F' = (1 - C) S2 - S1 and F'' = (1 - C)^2 S3 + 2 (1 - C) S4,
+// lambda' = lambda - 2 F F' / (2 F'^2 - F F'').  The error after a Halley step
+// is of order the cube of the error before it, so a step below 2e-3 of lambda
+// leaves an error of order 1e-8, far inside the form's 1e-4 tolerance: one
+// evaluation pass usually suffices where the Newton step needs two.
+__device__ void halley_update(DevScalars* sc, double S0, double S1, double S2, double S3, double S4) {
+  const double lam = sc->lam, om = sc->omC;
+  const double F = S0 - lam * S1;
+  const double Fp = om * S2 - S1;
+  const double Fpp = om * om * S3 + 2.0 * om * S4;
+  const double den = 2.0 * Fp * Fp - F * Fpp;
+  const double step = (den > 0.0) ? 2.0 * F * Fp / den : F / Fp;
+  double lnew = lam - step;
+  if (!(Fp < 0.0) || !(lnew > 0.0)) lnew = lam * (F > 0.0 ? 2.0 : 0.5);
+  const double rel = fabs(step) / lam;
+  sc->lam = lnew;
+  set_mixed_scal(sc);
+  sc->passes += 1;
+  sc->last_step = rel;
+  if (Fp < 0.0 && rel <= 2e-3) sc->conv = 1;
+  else if (sc->passes >= kNewtonMaxPasses) sc->flags |= 1;
+}
+
+// Sums per Newton evaluation: three for the FP64 form (Newton), five for the
+// mixed form (Halley).
+template <bool MIXED> struct NSums { static constexpr int value = MIXED ? 5 : 3; };
+
+// The update of either form from the combined sums.
+template <bool MIXED>
+__device__ __forceinline__ void lambda_update(DevScalars* sc, const double (&S)[5]) {
+  if (MIXED) halley_update(sc, S[0], S[1], S[2], S[3], S[4]);
+  else newton_update(sc, S[0], S[1], S[2], 1e-8);
 }
 
 // Local Peebles factor from the substep-start n_1s and H + div v / 3 (no
@@ -223,13 +293,16 @@ __device__ __forceinline__ float local_C_f32(const StepCoef& k, float div, float
 }
 
 // Per-block partial sums of one Newton evaluation at lambda (result in thread 0):
-// v0 = sum alpha n^2 x'^2, v1 = sum n (1 - x'), v2 = sum (2 alpha n^2 x' + lambda n) dx'/dG.
+// v0 = sum alpha n^2 x'^2, v1 = sum n (1 - x'), v2 = sum (2 alpha n^2 x' + lambda n) dx'/dG;
+// mixed form also v3 = sum [2 alpha n^2 (dx'/dG)^2 + (2 alpha n^2 x' + lambda n) d2x'/dG2],
+// v4 = sum n dx'/dG (the second derivative of F for the Halley step).
 // PART: partial mixing — per cell, A scaled by f + (1 - f) C_i, s = dt f and G
 // offset by (1 - f)/f C_i beta e_alpha (C_i the local Peebles factor).
 template <bool MIXED, bool PART = false>
 __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam, double G, double tot, double S1s,
-                                                  int blk, int nblk, double (&v)[3]) {
+                                                  const MixedScal& ms, int blk, int nblk, double (&v)[5]) {
   const int64_t stride = (int64_t)nblk * NT;
+  v[3] = v[4] = 0.0;
   if (!MIXED) {
     v[0] = v[1] = v[2] = 0.0;
     const double* delta = (const double*)a.delta;
@@ -253,10 +326,9 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
       v[2] += (2.0 * an2 * xr + lam * c.n) * dxdG;
     }
   } else {
-    Kahan32 s0, s1, s2;
-    const CoefF32 f = coef_f32(a.k);
-    const float Gf = (float)G, lamf = (float)lam;
-    const float wscale = tot > 0.0 ? (float)(S1s / tot) : 0.0f;
+    Kahan32 acc[5];
+    const CoefF32& f = a.kf;
+    const float Gf = ms.Gf, lamf = ms.lamf, wscale = ms.wscale;
     const float* delta = (const float*)a.delta;
     const float* T = (const float*)a.T;
     for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
@@ -270,16 +342,20 @@ __device__ __forceinline__ void newton_block_sums(const PassArgs& a, double lam,
         c.s = f.dt * fm;
         Gc = Gf + ((1.0f - fm) / fm) * Ci * (float)(a.k.beta * a.k.ea);
       }
-      float xr, yr, dxdG;
-      root_f32(c.A, c.s, Gc, c.xf, c.yf, &xr, &yr, &dxdG);
+      float xr, yr, dxdG, d2;
+      root_f32(c.A, c.s, Gc, c.xf, c.yf, &xr, &yr, &dxdG, &d2);
       float an2 = c.al * c.n * c.n;
-      s0.add(an2 * xr * xr);
-      s1.add(c.n * yr);
-      s2.add((2.0f * an2 * xr + lamf * c.n) * dxdG);
+      const float q = 2.0f * an2 * xr + lamf * c.n;
+      acc[0].add(an2 * xr * xr);
+      acc[1].add(c.n * yr);
+      acc[2].add(q * dxdG);
+      acc[3].add(2.0f * an2 * dxdG * dxdG + q * d2);
+      acc[4].add(c.n * dxdG);
     }
-    v[0] = s0.value(); v[1] = s1.value(); v[2] = s2.value();
+    block_sum_kahan<5, NT>(acc, v);
+    return;
   }
-  block_sum<3, NT>(v);
+  block_sum_first<NSums<MIXED>::value, NT>(v);
 }
 
 // Scalars of the mixed form's final pass at the converged lambda.
@@ -288,15 +364,15 @@ struct FinalMixed {
   float Gf, wscale, kdf, Hf, dtf;
   dfloat Gd;
 };
-__device__ __forceinline__ FinalMixed final_mixed_setup(const PassArgs& a, double G, double tot, double S1s) {
+__device__ __forceinline__ FinalMixed final_mixed_setup(const PassArgs& a, const MixedScal& ms) {
   FinalMixed m;
-  m.f = coef_f32(a.k);
-  m.Gf = (float)G;
-  m.wscale = tot > 0.0 ? (float)(S1s / tot) : 0.0f;
-  m.kdf = (float)a.k.kd;
-  m.Hf = (float)a.k.H;
-  m.dtf = (float)a.k.dt;
-  m.Gd = df_from_double(G);
+  m.f = a.kf;
+  m.Gf = ms.Gf;
+  m.wscale = ms.wscale;
+  m.kdf = a.kf.kd;
+  m.Hf = a.kf.H;
+  m.dtf = a.kf.dt;
+  m.Gd = ms.Gd;
   return m;
 }
 
@@ -306,8 +382,8 @@ __device__ __forceinline__ FinalMixed final_mixed_setup(const PassArgs& a, doubl
 // tally and velocity; adds the cell to the sums of the new state.
 template <bool PART>
 __device__ __forceinline__ void final_cell_mixed(const PassArgs& a, const FinalMixed& m, bool zero_tally, int64_t i,
-                                                 float d, double x, float Tin, uint32_t tal, float4 u, Kahan32& s0,
-                                                 Kahan32& s1, Kahan32& s2) {
+                                                 float d, double x, float Tin, uint32_t tal, float4 u,
+                                                 Kahan32 (&acc)[3]) {
   const CoefF32& f = m.f;
   // the state and 1 - x as double-float pairs, from the bits of x
   const dfloat X = df_from_double(x);
@@ -341,7 +417,7 @@ __device__ __forceinline__ void final_cell_mixed(const PassArgs& a, const FinalM
   // discriminant of this equation is D again.
   const dfloat r0 = df_add(df_mul_f(df_mul(X, X), c.A), df_neg(df_mul(df_mul_f(Gc, c.s), Y)));
   float dx = fdiv(-2.0f * r0.hi, 2.0f * c.A * c.xf + B + sq);
-  double xn = x + f2d_bits(dx);  // one binary64 addition, no conversion instruction
+  double xn = add_small(x, dx);  // integer operations unless |dx| > x/4
   float damp = __expf(-(m.kdf * xr + m.Hf) * m.dtf);
   u.x *= damp; u.y *= damp; u.z *= damp;
   ((float4*)a.vel4)[i] = u;
@@ -351,17 +427,17 @@ __device__ __forceinline__ void final_cell_mixed(const PassArgs& a, const FinalM
   float ne = c.n * xr;
   ((float*)a.emis)[i] = c.al * ne * ne;
   if (zero_tally) a.tally[i] = 0u;
-  s0.add(d * yr);
-  s1.add(d * xr);
-  s2.add(d);
+  acc[0].add(d * yr);
+  acc[1].add(d * xr);
+  acc[2].add(d);
 }
 
 // Per-block final update at the converged lambda: writes x, T, U, emission
 // weights (zeroes the tallies on the last substep); partial sums (thread 0):
 // v0 = sum delta (1 - x'), v1 = sum delta x', v2 = sum delta.
 template <bool MIXED, bool PART = false>
-__device__ __forceinline__ void final_block(const PassArgs& a, double G, double tot, double S1s, int blk, int nblk,
-                                            double (&v)[3]) {
+__device__ __forceinline__ void final_block(const PassArgs& a, double G, double tot, double S1s, const MixedScal& ms,
+                                            int blk, int nblk, double (&v)[3]) {
   const int64_t stride = (int64_t)nblk * NT;
   const bool zero_tally = a.k.last != 0;
   if (!MIXED) {
@@ -396,16 +472,17 @@ __device__ __forceinline__ void final_block(const PassArgs& a, double G, double 
       v[2] += d;
     }
   } else {
-    Kahan32 s0, s1, s2;
-    const FinalMixed fm = final_mixed_setup(a, G, tot, S1s);
+    Kahan32 acc[3];
+    const FinalMixed fm = final_mixed_setup(a, ms);
     const float* delta = (const float*)a.delta;
     const float* T = (const float*)a.T;
     const float4* U = (const float4*)a.vel4;
     for (int64_t i = (int64_t)blk * NT + threadIdx.x; i < a.n3; i += stride) {
       const uint32_t tal = (a.k.mixing == REC_MIX_TALLY) ? a.tally[i] : 0u;
-      final_cell_mixed<PART>(a, fm, zero_tally, i, delta[i], a.x[i], T[i], tal, U[i], s0, s1, s2);
+      final_cell_mixed<PART>(a, fm, zero_tally, i, delta[i], a.x[i], T[i], tal, U[i], acc);
     }
-    v[0] = s0.value(); v[1] = s1.value(); v[2] = s2.value();
+    block_sum_kahan<3, NT>(acc, v);
+    return;
   }
   block_sum<3, NT>(v);
 }
@@ -467,17 +544,19 @@ __global__ void __launch_bounds__(NT) k_newton(PassArgs a, const BoxDev* bxs, in
   DevScalars* sc = a.sc;
   if (ld_flag(&sc->conv)) return;
   const double lam = sc->lam;
-  double v[3];
-  newton_block_sums<MIXED>(a, lam, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, blk, nblk, v);
+  constexpr int K = NSums<MIXED>::value;
+  double v[5];
+  newton_block_sums<MIXED>(a, lam, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, mixed_scal(sc, false), blk,
+                           nblk, v);
   if (threadIdx.x == 0) {
     double* p = a.part + (size_t)blk * kMaxSums;
-    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+    for (int j = 0; j < K; ++j) p[j] = v[j];
   }
   if (!last_block_done(&sc->counter, nblk)) return;
-  double S[3];
-  combine_partials<3, NT>(a.part, nblk, kMaxSums, S);
+  double S[5];
+  combine_partials_first<K, NT>(a.part, nblk, kMaxSums, S);
   if (threadIdx.x == 0) {
-    newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
+    lambda_update<MIXED>(sc, S);
     sc->counter = 0;
   }
 }
@@ -554,8 +633,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a, uint32_t
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TmaStage* stage = reinterpret_cast<TmaStage*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(TmaStage) * kTmaStages);
-  const double lam = sc->lam;
-  const double G = sc->omC * lam + sc->G0, tot = (double)sc->tally_total, S1s = sc->S1s;
+  const MixedScal ms = mixed_scal(sc, false);
   const int64_t n_tiles = a.n3 / kTmaTile;  // whole tiles, copied in bulk
   const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const float* delta = (const float*)a.delta;
@@ -576,18 +654,20 @@ __global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a, uint32_t
   };
   if (threadIdx.x == 0)
     for (int64_t it = 0; it < my_tiles && it < kTmaStages - 1; ++it) issue(it);
-  Kahan32 s0, s1, s2;
-  const CoefF32 f = coef_f32(a.k);
-  const float Gf = (float)G, lamf = (float)lam;
-  const float wscale = tot > 0.0 ? (float)(S1s / tot) : 0.0f;
+  Kahan32 acc[5];
+  const CoefF32& f = a.kf;
+  const float Gf = ms.Gf, lamf = ms.lamf, wscale = ms.wscale;
   auto cell = [&](float d, float2 xy, float T, uint32_t tal) {
     CellF32 c = cell_f32(f, a.k.mixing, d, xy, T, (a.k.mixing == REC_MIX_TALLY) ? tal : 0u, wscale);
-    float xr, yr, dxdG;
-    root_f32(c.A, c.s, Gf, c.xf, c.yf, &xr, &yr, &dxdG);
+    float xr, yr, dxdG, d2;
+    root_f32(c.A, c.s, Gf, c.xf, c.yf, &xr, &yr, &dxdG, &d2);
     float an2 = c.al * c.n * c.n;
-    s0.add(an2 * xr * xr);
-    s1.add(c.n * yr);
-    s2.add((2.0f * an2 * xr + lamf * c.n) * dxdG);
+    const float q = 2.0f * an2 * xr + lamf * c.n;
+    acc[0].add(an2 * xr * xr);
+    acc[1].add(c.n * yr);
+    acc[2].add(q * dxdG);
+    acc[3].add(2.0f * an2 * dxdG * dxdG + q * d2);
+    acc[4].add(c.n * dxdG);
   };
   bool timed_out = false;
   int64_t it = 0;
@@ -623,17 +703,17 @@ __global__ void __launch_bounds__(kTmaThreads) k_newton_tma(PassArgs a, uint32_t
   for (int64_t i = n_tiles * kTmaTile + (int64_t)blockIdx.x * kTmaThreads + threadIdx.x; i < a.n3;
        i += (int64_t)gridDim.x * kTmaThreads)
     cell(delta[i], a.xy[i], Tg[i], a.tally[i]);
-  double v[3] = {s0.value(), s1.value(), s2.value()};
-  block_sum<3, kTmaThreads>(v);
+  double v[5];
+  block_sum_kahan<5, kTmaThreads>(acc, v);
   if (threadIdx.x == 0) {
     double* p = a.part + (size_t)blockIdx.x * kMaxSums;
-    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+    for (int j = 0; j < 5; ++j) p[j] = v[j];
   }
   if (!last_block_done(&sc->counter)) return;
-  double S[3];
-  combine_partials<3, kTmaThreads>(a.part, gridDim.x, kMaxSums, S);
+  double S[5];
+  combine_partials<5, kTmaThreads>(a.part, gridDim.x, kMaxSums, S);
   if (threadIdx.x == 0) {
-    newton_update(sc, S[0], S[1], S[2], 1e-5);
+    halley_update(sc, S[0], S[1], S[2], S[3], S[4]);
     sc->counter = 0;
   }
 }
@@ -647,7 +727,7 @@ __global__ void __launch_bounds__(NT) k_final(PassArgs a, rec_stats* st, const B
   DevScalars* sc = a.sc;
   const double lam = sc->lam;
   double v[3];
-  final_block<MIXED>(a, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, blk, nblk, v);
+  final_block<MIXED>(a, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s, mixed_scal(sc, false), blk, nblk, v);
   if (threadIdx.x == 0) {
     double* p = a.part + (size_t)blk * kMaxSums;
     p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
@@ -680,18 +760,19 @@ __global__ void __launch_bounds__(NT) k_batch_substep(PassArgs a0, rec_stats* st
       DevScalars* sc = a.sc;
       if (__ldcg(&sc->conv)) continue;  // the same for the whole block
       const double lam = __ldcg(&sc->lam);
-      double v[3];
+      constexpr int K = NSums<MIXED>::value;
+      double v[5];
       newton_block_sums<MIXED>(a, lam, __ldcg(&sc->omC) * lam + __ldcg(&sc->G0), (double)__ldcg(&sc->tally_total),
-                               __ldcg(&sc->S1s), blk, nblk, v);
+                               __ldcg(&sc->S1s), mixed_scal(sc, true), blk, nblk, v);
       if (threadIdx.x == 0) {
         double* p = a.part + (size_t)blk * kMaxSums;
-        p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+        for (int j = 0; j < K; ++j) p[j] = v[j];
       }
       if (!last_block_done(&sc->counter, nblk)) continue;
-      double S[3];
-      combine_partials<3, NT>(a.part, nblk, kMaxSums, S);
+      double S[5];
+      combine_partials_first<K, NT>(a.part, nblk, kMaxSums, S);
       if (threadIdx.x == 0) {
-        newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
+        lambda_update<MIXED>(sc, S);
         sc->counter = 0;
       }
     }
@@ -708,7 +789,7 @@ __global__ void __launch_bounds__(NT) k_batch_substep(PassArgs a0, rec_stats* st
     const double lam = __ldcg(&sc->lam);
     double v[3];
     final_block<MIXED>(a, __ldcg(&sc->omC) * lam + __ldcg(&sc->G0), (double)__ldcg(&sc->tally_total), __ldcg(&sc->S1s),
-                       blk, nblk, v);
+                       mixed_scal(sc, true), blk, nblk, v);
     if (threadIdx.x == 0) {
       double* p = a.part + (size_t)blk * kMaxSums;
       p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
@@ -744,7 +825,7 @@ __global__ void __launch_bounds__(kTmaThreads, kFinCtasPerSm) k_final_tma(PassAr
   FinStage* stage = reinterpret_cast<FinStage*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(FinStage) * kFinStages);
   const double lam = sc->lam;
-  const FinalMixed fm = final_mixed_setup(a, sc->omC * lam + sc->G0, (double)sc->tally_total, sc->S1s);
+  const FinalMixed fm = final_mixed_setup(a, mixed_scal(sc, false));
   const bool zero_tally = a.k.last != 0;
   const bool tally_mode = a.k.mixing == REC_MIX_TALLY;
   const uint32_t stage_bytes = kTmaTile * (4 + 8 + 4 + 16) + (tally_mode ? kTmaTile * 4 : 0);
@@ -770,7 +851,7 @@ __global__ void __launch_bounds__(kTmaThreads, kFinCtasPerSm) k_final_tma(PassAr
   };
   if (threadIdx.x == 0)
     for (int64_t it = 0; it < my_tiles && it < kFinStages - 1; ++it) issue(it);
-  Kahan32 s0, s1, s2;
+  Kahan32 acc[3];
   bool timed_out = false;
   int64_t it = 0;
   for (; it < my_tiles; ++it) {
@@ -787,7 +868,7 @@ __global__ void __launch_bounds__(kTmaThreads, kFinCtasPerSm) k_final_tma(PassAr
       const int64_t c0 = ((int64_t)blockIdx.x + it * gridDim.x) * kTmaTile;
       for (int k = threadIdx.x; k < kTmaTile; k += kTmaThreads)
         final_cell_mixed<false>(a, fm, zero_tally, c0 + k, t.delta[k], t.x[k], t.T[k], tally_mode ? t.tally[k] : 0u,
-                                t.U[k], s0, s1, s2);
+                                t.U[k], acc);
     }
     if (__syncthreads_or(timed_out)) { timed_out = true; break; }
   }
@@ -807,10 +888,9 @@ __global__ void __launch_bounds__(kTmaThreads, kFinCtasPerSm) k_final_tma(PassAr
   // cells after the last whole tile
   for (int64_t i = n_tiles * kTmaTile + (int64_t)blockIdx.x * kTmaThreads + threadIdx.x; i < a.n3;
        i += (int64_t)gridDim.x * kTmaThreads)
-    final_cell_mixed<false>(a, fm, zero_tally, i, delta[i], a.x[i], Tg[i], tally_mode ? a.tally[i] : 0u, Ug[i], s0,
-                            s1, s2);
-  double v[3] = {s0.value(), s1.value(), s2.value()};
-  block_sum<3, kTmaThreads>(v);
+    final_cell_mixed<false>(a, fm, zero_tally, i, delta[i], a.x[i], Tg[i], tally_mode ? a.tally[i] : 0u, Ug[i], acc);
+  double v[3];
+  block_sum_kahan<3, kTmaThreads>(acc, v);
   if (threadIdx.x == 0) {
     double* p = a.part + (size_t)blockIdx.x * kMaxSums;
     p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
@@ -827,17 +907,19 @@ __global__ void __launch_bounds__(NT) k_newton_part(PassArgs a) {
   DevScalars* sc = a.sc;
   if (ld_flag(&sc->conv)) return;
   const double lam = sc->lam;
-  double v[3];
-  newton_block_sums<MIXED, true>(a, lam, sc->omC * lam + sc->G0, 0.0, sc->S1s, blockIdx.x, gridDim.x, v);
+  constexpr int K = NSums<MIXED>::value;
+  double v[5];
+  newton_block_sums<MIXED, true>(a, lam, sc->omC * lam + sc->G0, 0.0, sc->S1s, mixed_scal(sc, false), blockIdx.x,
+                                 gridDim.x, v);
   if (threadIdx.x == 0) {
     double* p = a.part + (size_t)blockIdx.x * kMaxSums;
-    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+    for (int j = 0; j < K; ++j) p[j] = v[j];
   }
   if (!last_block_done(&sc->counter)) return;
-  double S[3];
-  combine_partials<3, NT>(a.part, gridDim.x, kMaxSums, S);
+  double S[5];
+  combine_partials_first<K, NT>(a.part, gridDim.x, kMaxSums, S);
   if (threadIdx.x == 0) {
-    newton_update(sc, S[0], S[1], S[2], MIXED ? 1e-5 : 1e-8);
+    lambda_update<MIXED>(sc, S);
     sc->counter = 0;
   }
 }
@@ -847,7 +929,7 @@ __global__ void __launch_bounds__(NT) k_final_part(PassArgs a, rec_stats* st) {
   DevScalars* sc = a.sc;
   const double lam = sc->lam;
   double v[3];
-  final_block<MIXED, true>(a, sc->omC * lam + sc->G0, 0.0, sc->S1s, blockIdx.x, gridDim.x, v);
+  final_block<MIXED, true>(a, sc->omC * lam + sc->G0, 0.0, sc->S1s, mixed_scal(sc, false), blockIdx.x, gridDim.x, v);
   if (threadIdx.x == 0) {
     double* p = a.part + (size_t)blockIdx.x * kMaxSums;
     p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
@@ -1065,6 +1147,7 @@ PassArgs pass_args(rec_ctx* c, const StepCoef& k) {
   a.sc = c->sc;
   a.part = c->part;
   a.k = k;
+  a.kf = coef_f32(k);
   a.div = c->div;
   a.fmix = c->params.f_alpha;
   return a;
@@ -1187,6 +1270,7 @@ PassArgs batch_args(rec_ctx* c, const StepCoef& k) {
   std::memset(&a, 0, sizeof(a));
   a.part = c->part;
   a.k = k;
+  a.kf = coef_f32(k);
   return a;
 }
 }  // namespace

@@ -1303,9 +1303,11 @@ __device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const
     const EmitBox<R> e{d.P, d.first, (uint32_t)d.n3, d.n, (const V*)d.vel4, (const R*)d.T, d.tally,
                        (R)__ldcg(&bst[cur].kappa), (R)__ldcg(&bst[cur].cth),
                        Stream{a.strm.k0, a.strm.k1, (uint32_t)cur}, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0};
-    // one code path for all sides (the power-of-two specialisation would double
-    // the inlined body and spill registers)
-    emit_warp<R, false, FRESH>(a, e, (uint32_t)base, N, my_abs, my_cross);
+    // power-of-two sides take cell coordinates by shifts and the periodic wrap
+    // by masks; other sides by exact multiply-high divisions (the binary64 form
+    // keeps one path: both would not fit its register budget)
+    if (sizeof(R) == 4 && d.p2) emit_warp<R, true, FRESH>(a, e, (uint32_t)base, N, my_abs, my_cross);
+    else emit_warp<R, false, FRESH>(a, e, (uint32_t)base, N, my_abs, my_cross);
   }
   if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
   box_counters_flush(cnt, bxs, B);

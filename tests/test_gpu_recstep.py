@@ -155,3 +155,37 @@ def test_full_size_256_cubed_step(cosmo, precision):
     tally = rng.poisson(6.0 * d * d / (d * d).mean()).astype(np.uint32)
     _check_step(cosmo, box, x0, T0, tally, 1100.0, 1097.0)
     box.close()
+
+
+@pytest.mark.slow
+def test_mixed_form_error_per_output_over_200_steps(cosmo):
+    """The mixed form's error against the FP64 oracle, per output, over the
+    200 steps of the 128^3 configuration's schedule (z 1600 -> 700) on a 32^3
+    box with sigma_lnrho = 1 and 1 km/s flows, full mixing (no transport, so
+    both sides see the same inputs at every step): x_e, T_b, the drag-damped
+    velocity and the emission weight per cell, and X_e.  Starts from each
+    side's own Saha state.  The largest errors over all steps and cells are
+    printed and must stay inside the form's 1e-4 (3e-4 for the emission
+    weight, a product of four binary32 factors)."""
+    from paper_2312_11448_gb300.inputs import z_schedule
+    n, S = 32, 200
+    box = new_box(n, "mixed", "full", sigma=1.0, sigma_v=1.0)
+    zs = z_schedule(1600.0, 700.0, S)
+    d, U, _ = oracle_fields(box)
+    box.state_init(zs[0])
+    x = O.saha_xe(cosmo, zs[0], d)
+    T = np.full(n ** 3, O.background(cosmo, zs[0])["Tg"])
+    worst = dict(x_e=0.0, T=0.0, U=0.0, emis=0.0, X_e=0.0)
+    for s in range(S):
+        box.step(s, zs[s], zs[s + 1])
+        x, T, U, e, so = O.rec_step(cosmo, n, zs[s], zs[s + 1], d, x, T, U=U, mixing="full")
+        worst["x_e"] = max(worst["x_e"], np.max(np.abs(box.host("x") / x - 1)))
+        worst["T"] = max(worst["T"], np.max(np.abs(box.host("T").astype(np.float64) / T - 1)))
+        gU = box.host("vel4")[:, :3].astype(np.float64)
+        worst["U"] = max(worst["U"], np.max(np.abs(gU - U)) / np.max(np.abs(U)))
+        worst["emis"] = max(worst["emis"], np.max(np.abs(box.host("emis").astype(np.float64) / e - 1)))
+        worst["X_e"] = max(worst["X_e"], abs(box.stats()["X_e"] / so["Xe"] - 1))
+    print("mixed form, largest relative error over 200 steps:", worst)
+    assert worst["x_e"] < 1e-4 and worst["T"] < 1e-4 and worst["U"] < 1e-4 and worst["X_e"] < 1e-4
+    assert worst["emis"] < 3e-4
+    box.close()

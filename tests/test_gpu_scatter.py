@@ -134,13 +134,17 @@ def test_peebles_factor_on_gpu(cosmo):
     for zeta in (3e3, 1e4, 3e4):
         _, st = box.scatter_mc(z, 8192, records=False, zeta=zeta, lambda2g=0.0,
                                x_lost=50 * _x50(cosmo, z, zeta, n1s), max_steps=2_000_000)
-        # the lifetime tail: a few photons in 10^4 outlive the step cap
-        N = 8192 - st["count"][3]
-        assert st["count"][3] <= 8 and st["count"][1] == 0
+        # The lifetime tail: a few photons in 10^4 outlive the step cap.  They are
+        # kept in N and counted as not escaped; whatever their true fate, that
+        # moves C by at most p_alpha * capped / N, which widens the band.
+        N, capped = 8192, st["count"][3]
+        assert capped <= 8 and st["count"][1] == 0
         R = 8 * np.pi * zeta * bg["H"] / (LAMBDA_A ** 3 * n1s)
         C_th = R / (beta + R)
-        C_mc = 3 * A / (beta + 3 * A) * st["count"][0] / N
-        assert C_mc == pytest.approx(C_th, abs=4 * np.sqrt(C_th * (1 - C_th) / N)), zeta
+        p_alpha = 3 * A / (beta + 3 * A)
+        C_mc = p_alpha * st["count"][0] / N
+        band = 4 * np.sqrt(C_th * (1 - C_th) / N) + p_alpha * capped / N
+        assert C_mc == pytest.approx(C_th, abs=band), zeta
     box.close()
 
 

@@ -11,7 +11,7 @@ from gpu_helpers import new_box, oracle_fields, quantiles, set_state
 pytestmark = pytest.mark.gpu
 
 
-def _run_both(cosmo, box, emis, T, z, step, n_packets):
+def _run_both(cosmo, box, emis, T, z, step, n_packets, threads=0):
     n = box.n
     set_state(box, np.full(n ** 3, 0.5), T, tally=np.zeros(n ** 3, np.uint32), emis=emis)
     box.transport(step, z)
@@ -20,7 +20,7 @@ def _run_both(cosmo, box, emis, T, z, step, n_packets):
     _, _, v4 = oracle_fields(box)
     prec = "f32" if box.precision == "mixed" else "f64"
     tally, cnt, _ = O.transport(cosmo, n, z, 7, step, n_packets, box.host("emis"), v4, box.host("T"),
-                                quantiles(box), precision=prec)
+                                quantiles(box), precision=prec, threads=threads)
     return gpu, st, tally, cnt
 
 
@@ -102,6 +102,25 @@ def test_full_size_256_cubed_1e8_packets(cosmo):
     emis = d * d  # recombination weight of a uniformly ionised box: alpha n_e^2 ~ Delta^2
     T = np.full(n ** 3, 2.7255 * 1101.0) * (1.0 + 0.01 * np.sin(np.arange(n ** 3)))
     gpu, st, tally, cnt = _run_both(cosmo, box, emis, T, 1100.0, 17, Np)
+    assert st["emitted"] == cnt["emitted"] == Np and st["absorbed"] == Np
+    assert st["crossings"] == cnt["crossings"]
+    assert np.array_equal(gpu, tally)
+    box.close()
+
+
+@pytest.mark.slow
+def test_full_size_512_cubed_1e8_packets(cosmo):
+    """512^3 (the largest configuration's box, sigma_lnrho 1.2, sigma_v 2 km/s),
+    1e8 packets, binary32 transport: all 134M tallies bit-exact against the
+    oracle (its OpenMP build: the same integers in any order)."""
+    import os
+    from paper_2312_11448_gb300.inputs import density_field
+    n, Np = 512, 100_000_000
+    box = new_box(n, "mixed", n_packets=Np, sigma=1.2, sigma_v=2.0)
+    d = density_field(n, 1.2, 1).ravel()
+    emis = d * d
+    T = np.full(n ** 3, 2.7255 * 1101.0) * (1.0 + 0.01 * np.sin(np.arange(n ** 3)))
+    gpu, st, tally, cnt = _run_both(cosmo, box, emis, T, 1100.0, 23, Np, threads=os.cpu_count() or 1)
     assert st["emitted"] == cnt["emitted"] == Np and st["absorbed"] == Np
     assert st["crossings"] == cnt["crossings"]
     assert np.array_equal(gpu, tally)
