@@ -125,18 +125,32 @@ typedef struct {
   int32_t newton_passes; /* Newton evaluations of the last substep */
   int32_t flags;         /* bit 0: Newton did not converge; bit 1: packets hit the crossing cap;
                             bit 2: non-finite or negative emission weight; bit 3: a bounded
-                            device-side wait expired (copy pipeline of a Newton pass) */
+                            device-side wait expired (copy pipeline of a Newton pass); bit 4:
+                            region sweeps found their second queue full (the packets concerned
+                            marched on without a region limit: results unchanged, speed only) */
+  uint64_t requeued;     /* region sweeps (rec_tuning.march_halo > 0): packets queued again for a
+                            later sweep in the last lya_transport call; 0 otherwise */
 } rec_stats;
 
 /* Launch and scheduling parameters of the transport: a library setting with
  * no counterpart in the paper.  They change only the speed: tallies, counters
  * and every other result are identical for any valid setting. */
 typedef struct {
-  int32_t emit_blocks_per_sm;  /* emission grid, blocks of 256 threads per SM: 1..5 (FP64 form 1..3, batch 1..4) */
-  int32_t march_blocks_per_sm; /* march grid: 1..5 (FP64 form and batch 1..4) */
+  int32_t emit_blocks_per_sm;  /* emission grid, blocks of 256 threads per SM: 1..6 (FP64 form 1..4, batch 1..4) */
+  int32_t march_blocks_per_sm; /* march grid: 1..4 (FP64 form, batch and region sweeps 1..3) */
   int32_t march_refill;        /* idle lanes of a warp that trigger a refill from the queue: 1..32 */
   int32_t march_chunk;         /* queued packets per unit of march work handed to a warp: 8..4096 */
   int32_t tile;                /* side of the super-tiles that order the march queue: 8, 16, 32 or 64 */
+  int32_t march_halo;          /* region sweeps (single box, power-of-two side): 0 = off, every packet
+                                  marches to its end in one launch; h in 1..256 = a packet marches only
+                                  while it stays within h cells of the super-tile whose bucket it was
+                                  taken from, then is queued again in the bucket of the super-tile it
+                                  has reached, for the next of up to 8 sweeps (the last sweep has no
+                                  limit).  Each sweep then touches a region that the L2 cache holds,
+                                  which pays on boxes whose velocities are far larger than L2.  The
+                                  first rec_set_tuning with h > 0 allocates the second queue
+                                  (n_packets / 4 entries of 48 B, 96 B in the FP64 form); packets that
+                                  find it full march on without a limit. */
 } rec_tuning;
 
 /* Create a context for n_boxes independent boxes (1 <= n_boxes <= 128), each

@@ -35,9 +35,12 @@ class Trajectory:
         self.given = tallies
         self.run_transport = run_transport
         dev = box.x.device
-        self.tallies = torch.zeros(self.S, box.n3, dtype=torch.int32, device=dev)
+        # every buffer of the trajectory is made on the box's stream, where the
+        # library's kernels read and write it
+        with torch.cuda.stream(box.stream):
+            self.tallies = torch.zeros(self.S, box.n3, dtype=torch.int32, device=dev)
+            self._v4_0 = box.vel4.clone()  # velocity at the first node
         self.ckpt = {}
-        self._v4_0 = box.vel4.clone()  # velocity at the first node
         box.ensure_stats(self.S + 1)
 
     def _set_state(self, x, T, v4):
@@ -92,8 +95,8 @@ class Trajectory:
         w = np.asarray(dJ_dXe, dtype=np.float64)
         dev = b.x.device
         z = lambda: torch.zeros(b.n3, dtype=torch.float64, device=dev)
-        xbar, Tbar, g_delta, g_a = z(), z(), z(), z()
         with torch.cuda.stream(b.stream):
+            xbar, Tbar, g_delta, g_a = z(), z(), z(), z()
             for s0 in reversed(range(0, self.S, self.k)):
                 s1 = min(s0 + self.k, self.S)
                 states = [self.ckpt[s0]]

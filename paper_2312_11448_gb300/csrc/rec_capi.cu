@@ -76,6 +76,7 @@ rec_tuning default_tuning(bool mixed, bool batch) {
   t.march_refill = 8;
   t.march_chunk = 64;
   t.tile = 32;
+  t.march_halo = 0;
   return t;
 }
 
@@ -381,8 +382,36 @@ rec_status rec_set_tuning(rec_ctx* c, const rec_tuning* t) {
   if (t->march_chunk < 8 || t->march_chunk > 4096) return fail(c, REC_EINVAL, "march_chunk must be in [8, 4096]");
   if (t->tile != 8 && t->tile != 16 && t->tile != 32 && t->tile != 64)
     return fail(c, REC_EINVAL, "tile must be 8, 16, 32 or 64");
+  if (t->march_halo < 0 || t->march_halo > 256) return fail(c, REC_EINVAL, "march_halo must be in [0, 256]");
+  if (t->march_halo > 0) {
+    if (c->n_boxes > 1) return fail(c, REC_EINVAL, "march_halo needs a single-box context");
+    if ((c->box.n & (c->box.n - 1)) != 0) return fail(c, REC_EINVAL, "march_halo needs a power-of-two box side");
+    const int smax = rec::sweep_march_limit(c->params.precision == REC_PREC_MIXED);
+    if (t->march_blocks_per_sm > smax)
+      return fail(c, REC_EINVAL, "with march_halo > 0, march_blocks_per_sm must be in [1, " + std::to_string(smax) + "]");
+  }
   cudaError_t e = cudaStreamSynchronize(c->stream);  // no transport of this context in flight
   if (e != cudaSuccess) return cuda_fail(c, e, "rec_set_tuning");
+  if (t->march_halo > 0 && !c->rqueue) {
+    // the second queue of the region sweeps and its per-bucket counters
+    const size_t entry = c->params.precision == REC_PREC_MIXED ? 48 : 96;
+    const size_t cap = (std::max<uint64_t>(c->box.n_packets / 4, 1) + rec::kRqParts - 1) / rec::kRqParts * rec::kRqParts;
+    const size_t nt = (size_t)((c->box.n + rec::kMinTile - 1) / rec::kMinTile), nb = nt * nt * nt;
+    e = cudaMalloc(&c->rqueue, entry * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->rcount, sizeof(unsigned long long) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->scnt, sizeof(unsigned long long) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->rqn, sizeof(unsigned long long) * 2 * rec::kRqParts);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * nb, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      cudaFree(c->rqueue); cudaFree(c->rcount); cudaFree(c->scnt); cudaFree(c->rqn);
+      c->rqueue = nullptr; c->rcount = nullptr; c->scnt = nullptr; c->rqn = nullptr;
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? fail(c, REC_ENOMEM, "rec_set_tuning: second march queue")
+                                            : cuda_fail(c, e, "rec_set_tuning: second march queue");
+    }
+    c->rq_cap = cap;
+  }
   c->tune = *t;
   if (c->n_boxes > 1) {
     layout_buckets(c);
@@ -584,6 +613,10 @@ void rec_free(rec_ctx* c) {
   cudaFree(c->bcap);
   cudaFree(c->bfill);
   cudaFree(c->cpre);
+  cudaFree(c->rqueue);
+  cudaFree(c->rcount);
+  cudaFree(c->scnt);
+  cudaFree(c->rqn);
   cudaFree(c->div);
   cudaFree(c->mc_scratch);
   cudaFree(c->trb_scratch);

@@ -57,6 +57,7 @@ struct DevScalars {
   unsigned long long alloc_u;      // systematic-sampling offset in [0, sumQ)
   unsigned long long qtail;        // packets queued for the march
   unsigned long long march_next;   // next queue chunk handed to a march warp
+  unsigned long long requeued;     // region sweeps: packets queued again in this transport call
   uint32_t alloc_counter;
   int32_t emis_valid;
   GridBarrier bar;  // grid barrier of the persistent batched launches (batch-wide record)
@@ -158,6 +159,15 @@ struct rec_ctx {
   int batch_step_grid = 0;   // resident blocks of the persistent batched substep (0: not queried, -1: none)
   int batch_front_grid = 0;  // resident blocks of the persistent batched transport front (same)
   void* queue;               // queued packets of the march (2 x 16 B binary32, 3 x 32 B binary64) [n_packets]
+  // region sweeps (tuning.march_halo > 0): packets leaving their region are
+  // appended to rqueue (48 B binary32, 96 B binary64 entries), counted per
+  // bucket in rcount, and placed by bucket into queue for the next sweep (scnt:
+  // per-bucket fill of that placement)
+  void* rqueue = nullptr;
+  size_t rq_cap = 0;
+  unsigned long long* rcount = nullptr;
+  unsigned long long* scnt = nullptr;
+  unsigned long long* rqn = nullptr;  // [2 kRqParts]: entries appended per part; entries to place per part
   int sm_count;
   bool emis_ready;
   std::string err;
@@ -254,6 +264,12 @@ void enqueue_newton_passes(rec_ctx* c, DevScalars* sc, const StepCoef& k, const 
 cudaError_t launch_transport(rec_ctx* c, int step, double z, rec_stats* st);
 cudaError_t launch_transport_batch(rec_ctx* c, int step, double z, rec_stats* st);
 void transport_limits(bool mixed, bool batch, int* emit_max, int* march_max);
+// Largest march grid (blocks per SM) of the region-sweep march.
+int sweep_march_limit(bool mixed);
+constexpr int kMaxSweeps = 8;  // region sweeps per transport call (the last without a limit)
+// The second queue is split into parts, each with its own append counter, so
+// that the warps of the march do not all add to one address.
+constexpr int kRqParts = 256;
 
 // rec_step.cu, batched contexts
 cudaError_t launch_state_init_batch(rec_ctx* c, double z);

@@ -63,6 +63,36 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
   return U4{c0, c1, c2, c3};
 }
 
+// The keys of the ten rounds, (k0 + r W0, k1 + r W1), formed once on the host.
+// Kernels read them from their parameters, so every round takes its key as a
+// constant operand instead of adding the Weyl increments per packet.
+struct Keys {
+  uint32_t a[10], b[10];
+};
+inline Keys key_schedule(uint32_t k0, uint32_t k1) {
+  Keys K;
+  for (int r = 0; r < 10; ++r) {
+    K.a[r] = k0;
+    K.b[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return K;
+}
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const Keys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.a[r];
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.b[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
 // Streams: key (seed_lo, seed_hi ^ step), counter (cell, packet-in-cell, block, box).
 struct Stream {
   uint32_t k0, k1, box;
@@ -70,10 +100,23 @@ struct Stream {
 __device__ __forceinline__ U4 draw(const Stream& s, uint32_t cell, uint32_t j, uint32_t block) {
   return philox4x32_10(cell, j, block, s.box, s.k0, s.k1);
 }
+// The same draw with the keys from a schedule (emission).
+struct KStream {
+  const Keys& K;
+  uint32_t box;
+};
+__device__ __forceinline__ U4 draw(const KStream& s, uint32_t cell, uint32_t j, uint32_t block) {
+  return philox4x32_10(cell, j, block, s.box, s.K);
+}
 constexpr uint32_t kAllocBlock = 0x000A110Cu;  // counter block of the allocation offset
 
 // Uniform deviates strictly inside (0,1), exactly representable.
-__device__ __forceinline__ float u01f(uint32_t r) { return __uint2float_rn((r >> 8) | 1u) * 0x1p-24f; }
+// Binary32: the float 1 + m 2^-23 with m the top 23 bits of r, minus 1 - 2^-24,
+// is exactly (2m + 1) 2^-24 (Sterbenz: the operands are within a factor of
+// two), with no integer-to-float conversion.
+__device__ __forceinline__ float u01f(uint32_t r) {
+  return __fsub_rn(__uint_as_float(0x3f800000u | (r >> 9)), 0x1.fffffep-1f);
+}
 __device__ __forceinline__ double u01d(uint32_t lo, uint32_t hi) {
   uint64_t w = ((uint64_t)hi << 32) | lo;
   return __ull2double_rn((w >> 11) | 1ull) * 0x1p-53;
@@ -112,13 +155,15 @@ template <> struct Draws<float> {
   // block 0: three cell offsets and the frequency quantile; blocks 1..16: two
   // direction pairs each
   static constexpr int kPairs = 2;
-  static __device__ __forceinline__ void position(const Stream& s, uint32_t c, uint32_t j, float f[3], float* uq) {
+  template <class S>
+  static __device__ __forceinline__ void position(const S& s, uint32_t c, uint32_t j, float f[3], float* uq) {
     U4 r = draw(s, c, j, 0u);
     f[0] = u01f(r.a); f[1] = u01f(r.b); f[2] = u01f(r.c); *uq = u01f(r.d);
   }
   using Block = U4;
   static __device__ __forceinline__ bool first_of_block(int t) { return (t & 1) == 0; }
-  static __device__ __forceinline__ U4 block(const Stream& s, uint32_t c, uint32_t j, int t) {
+  template <class S>
+  static __device__ __forceinline__ U4 block(const S& s, uint32_t c, uint32_t j, int t) {
     return draw(s, c, j, 1u + (uint32_t)(t >> 1));
   }
   static __device__ __forceinline__ void pair_from(const U4& r, int t, float* a, float* b) {
@@ -130,13 +175,15 @@ template <> struct Draws<double> {
   // blocks 0, 1: three cell offsets and the quantile (two words per deviate);
   // blocks 2..33: one direction pair each
   static constexpr int kPairs = 1;
-  static __device__ __forceinline__ void position(const Stream& s, uint32_t c, uint32_t j, double f[3], double* uq) {
+  template <class S>
+  static __device__ __forceinline__ void position(const S& s, uint32_t c, uint32_t j, double f[3], double* uq) {
     U4 r = draw(s, c, j, 0u), q = draw(s, c, j, 1u);
     f[0] = u01d(r.a, r.b); f[1] = u01d(r.c, r.d); f[2] = u01d(q.a, q.b); *uq = u01d(q.c, q.d);
   }
   using Block = U4;
   static __device__ __forceinline__ bool first_of_block(int) { return true; }
-  static __device__ __forceinline__ U4 block(const Stream& s, uint32_t c, uint32_t j, int t) {
+  template <class S>
+  static __device__ __forceinline__ U4 block(const S& s, uint32_t c, uint32_t j, int t) {
     return draw(s, c, j, 2u + (uint32_t)t);
   }
   static __device__ __forceinline__ void pair_from(const U4& r, int, double* a, double* b) {
@@ -481,6 +528,7 @@ __device__ __forceinline__ void bucket_scan_block(const unsigned long long* bfil
     cpre[nb] = run;
     sc->qtail = qt;
     sc->march_next = 0;
+    sc->requeued = 0;
   }
   __syncthreads();
   unsigned long long run = part[threadIdx.x];
@@ -516,6 +564,7 @@ struct TransportArgs {
   int M;
   R kappa, cth;
   Stream strm;
+  Keys ks;  // round keys of strm (emission)
   uint32_t* tally;
   DevScalars* sc;
   typename Vec4<R>::T* queue;  // 3 entries per queued packet
@@ -526,6 +575,13 @@ struct TransportArgs {
   const unsigned long long* cpre;  // first march chunk of each bucket [nb + 1]
   uint32_t chunk;                  // queued packets per march chunk
   int refill;                      // idle lanes of a warp that trigger a refill
+  // region sweeps (single box, power-of-two side)
+  typename Vec4<R>::T* rq;         // second queue: full traversal states, 3 vectors per entry
+  unsigned long long* rcount;      // entries per bucket appended to the second queue
+  unsigned long long* rqn;         // entries appended per part of the second queue [kRqParts]
+  uint64_t rq_part;                // entries one part holds
+  uint32_t halo;                   // region of a bucket: its super-tile and halo cells around it; 0: no limit
+  int resumed;                     // the queue holds full states of an earlier sweep (3 vectors per entry)
 };
 
 // Loads of the packet prefix and coarse index: the read-only path, or through
@@ -552,6 +608,26 @@ template <> __device__ __forceinline__ double bits_to<double>(uint32_t v) { retu
 template <class R> __device__ __forceinline__ uint32_t to_bits(R v);
 template <> __device__ __forceinline__ uint32_t to_bits<float>(float v) { return __float_as_uint(v); }
 template <> __device__ __forceinline__ uint32_t to_bits<double>(double v) { return (uint32_t)__double_as_longlong(v); }
+
+// Lower table node of the frequency quantile: k = min(trunc(tq), M - 2) (0 <= tq
+// < M - 1) and k as a value of R.  Binary32: adding 2^23 rounded toward zero
+// leaves 2^23 + trunc(tq) exactly, whose bits give k without a conversion.
+template <class R>
+__device__ __forceinline__ R quant_node(R tq, int M, int* k) {
+  int kk = Ar<R>::trunc(tq);
+  if (kk > M - 2) kk = M - 2;
+  *k = kk;
+  return (R)kk;
+}
+template <>
+__device__ __forceinline__ float quant_node<float>(float tq, int M, int* k) {
+  const float t = __fadd_rz(tq, 0x1p23f);
+  int kk = __float_as_int(t) - 0x4b000000;
+  float kf = __fsub_rn(t, 0x1p23f);
+  if (kk > M - 2) { kk = M - 2; kf = (float)(M - 2); }
+  *k = kk;
+  return kf;
+}
 
 // Traversal state of one packet.
 template <class R>
@@ -706,7 +782,7 @@ struct EmitBox {
   const R* T;
   uint32_t* tally;
   R kappa, cth;
-  Stream strm;
+  uint32_t box;  // fourth Philox counter word
   Tiles tl;
   uint32_t bk0;
 };
@@ -753,13 +829,14 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
     const uint32_t j = p - Pc;
     // (1) injection point uniform in the cell, frequency quantile
     R f[3], uq;
-    Draws<R>::position(e.strm, cell, j, f, &uq);
+    const KStream ks{a.ks, e.box};
+    Draws<R>::position(ks, cell, j, f, &uq);
     // isotropic direction (Marsaglia 1972): the first accepted of the candidate
     // pairs t = 0, 1, ... (each Philox block is computed once for the pairs it
     // holds).  The pairs of the first block are tested side by side; the loop
     // over later blocks runs for the few packets that reject all of them.
     {
-      typename Draws<R>::Block blk = Draws<R>::block(e.strm, cell, j, 0);
+      typename Draws<R>::Block blk = Draws<R>::block(ks, cell, j, 0);
       R ua, ub;
       Draws<R>::pair_from(blk, 0, &ua, &ub);
       R v1 = A::sub(A::mul(two, ua), one), v2 = A::sub(A::mul(two, ub), one);
@@ -774,7 +851,7 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
         t = 2;
       }
       for (; !ok && t < 32; ++t) {
-        if (Draws<R>::first_of_block(t)) blk = Draws<R>::block(e.strm, cell, j, t);
+        if (Draws<R>::first_of_block(t)) blk = Draws<R>::block(ks, cell, j, t);
         Draws<R>::pair_from(blk, t, &ua, &ub);
         v1 = A::sub(A::mul(two, ua), one);
         v2 = A::sub(A::mul(two, ub), one);
@@ -788,9 +865,8 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
     }
     // emission frequency from the tabulated inverse CDF
     R tq = A::mul(uq, (R)(a.M - 1));
-    int k = A::trunc(tq);
-    if (k > a.M - 2) k = a.M - 2;
-    R fr = A::sub(tq, (R)k);
+    int k;
+    const R fr = A::sub(tq, quant_node<R>(tq, a.M, &k));
     R q0 = __ldg(a.quant + k), q1 = __ldg(a.quant + k + 1);
     R xi = A::add(q0, A::mul(fr, A::sub(q1, q0)));
     R vt = A::sqr(A::mul(__ldg(e.T + cell), e.cth));
@@ -849,11 +925,11 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
 }
 
 // Resident blocks per SM of the emission (register budget per thread).
-template <class R> constexpr int emit_occupancy() { return sizeof(R) == 4 ? 5 : 3; }
+template <class R> constexpr int emit_occupancy() { return sizeof(R) == 4 ? 6 : 4; }
 
 template <class R, bool P2>
 __global__ void __launch_bounds__(TT, emit_occupancy<R>()) k_emit(TransportArgs<R> a) {
-  const EmitBox<R> e{a.P, a.first, (uint32_t)a.n3, (uint32_t)a.n, a.vel, a.T, a.tally, a.kappa, a.cth, a.strm, a.tl, 0u};
+  const EmitBox<R> e{a.P, a.first, (uint32_t)a.n3, (uint32_t)a.n, a.vel, a.T, a.tally, a.kappa, a.cth, 0u, a.tl, 0u};
   const uint32_t N = __ldg(a.P + a.n3);  // packets actually allocated
   uint64_t my_abs = 0, my_cross = 0;
   const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
@@ -881,8 +957,9 @@ template <class R> struct MarchAhead { static constexpr int value = sizeof(R) ==
 
 // Resident blocks per SM of the march (register budget per thread; a batch
 // keeps the box of each lane's packet in registers).
-template <class R, bool MB> constexpr int march_occupancy() {
-  return MB ? 3 : (sizeof(R) == 4 ? (MarchAhead<R>::value > 4 ? 3 : MarchAhead<R>::value > 2 ? 4 : 5) : 3);
+template <class R, bool MB, bool RS = false> constexpr int march_occupancy() {
+  return RS ? (sizeof(R) == 4 ? 3 : 2)
+            : (MB ? 3 : (sizeof(R) == 4 ? (MarchAhead<R>::value > 4 ? 3 : MarchAhead<R>::value > 2 ? 4 : 5) : 3));
 }
 
 __device__ __forceinline__ void transport_end_batch(const BoxDev* bxs, int B, const unsigned long long* bfill,
@@ -890,13 +967,19 @@ __device__ __forceinline__ void transport_end_batch(const BoxDev* bxs, int B, co
 
 // P2: the box side is a power of two (cell index by shifts and masks).
 // MB: batched context; the lanes of a warp may hold packets of different boxes.
-template <class R, bool P2, bool MB>
-__global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(TransportArgs<R> a, const BoxDev* bxs, int B,
-                                                                        const BoxStep* bst, rec_stats* st) {
+template <class R, bool P2, bool MB, bool RS = false>
+__global__ void __launch_bounds__(TT, (march_occupancy<R, MB, RS>())) k_march(TransportArgs<R> a, const BoxDev* bxs,
+                                                                              int B, const BoxStep* bst,
+                                                                              rec_stats* st) {
+  static_assert(!RS || (P2 && !MB), "region sweeps: single box of power-of-two side");
   using V = typename Vec4<R>::T;
   const int lane = threadIdx.x & 31;
   const uint32_t n = (uint32_t)a.n;
   const uint32_t lg = P2 ? (uint32_t)(__ffs((int)n) - 1) : 0u;
+  // region sweeps: bucket of the open chunk and of the lane's packet (its
+  // super-tile), 0xffffffff for a packet that marches without a limit
+  uint32_t cbk = 0, lbk = 0;
+  bool rqp = false;  // the lane's packet leaves its region: queue it again
   __shared__ BoxCounters cnt;
   if (MB) box_counters_clear(cnt, B);
   // box of the lane's packet (batch) and of the open chunk
@@ -943,6 +1026,7 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
           pos = a.boff[lo] + k0;
           end = pos + min((uint64_t)a.chunk, (uint64_t)(a.bfill[lo] - k0));
           have = true;
+          if (RS) cbk = lo;
           if (MB) {  // box of this bucket: last b with bk0 <= lo
             cbox = last_le(B, lo, [&](int i) { return bxs[i].bk0; });
             cvel = (const V*)bxs[cbox].vel4;
@@ -956,6 +1040,22 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
         if (((idle >> lane) & 1u) && rank < take) {
           const uint64_t slot = pos + rank;
           constexpr int QV = QueueVecs<R>::value;
+          if (RS) lbk = cbk;
+          if (RS && a.resumed) {
+            // a full state queued again by an earlier sweep
+            const V q0v = a.queue[3 * slot], q1v = a.queue[3 * slot + 1], q2v = a.queue[3 * slot + 2];
+            cell = to_bits<R>(q0v.x);
+            r.ix = cell & (n - 1u); r.iy = (cell >> lg) & (n - 1u); r.iz = cell >> (2u * lg);
+            r.tMx = q0v.y; r.tMy = q0v.z; r.tMz = q0v.w;
+            r.sx = q1v.x < (R)0 ? -1 : 1; r.tDx = fabs(q1v.x);
+            r.sy = q1v.y < (R)0 ? -1 : 1; r.tDy = fabs(q1v.y);
+            r.sz = q1v.z < (R)0 ? -1 : 1; r.tDz = fabs(q1v.z);
+            r.u0 = q1v.w;
+            r.knx = q2v.x; r.kny = q2v.y; r.knz = q2v.z;
+            r.kc = to_bits<R>(q2v.w);
+            Uc = lvel[cell];
+            active = true;
+          } else {
           const V q0v = a.queue[QV * slot], q1v = a.queue[QV * slot + 1];
           if (MB) {
             if (lbox != cbox) {  // counters of the previous box to shared memory
@@ -993,6 +1093,7 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
           r.kc = 1;  // the step out of the home cell
           Uc = lvel[cell];
           active = true;
+          }
         }
         // lanes taken this round leave the idle set (the lowest `take` idle lanes)
         unsigned taken = 0, m = idle;
@@ -1034,11 +1135,61 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
       if (res == 0) {
         cell = cl[kA];
         Uc = Un[kA - 1];
+        if (RS && a.halo && lbk != 0xffffffffu) {
+          // still inside the super-tile of its bucket widened by the halo?
+          // (periodic: offsets from the region's low corner modulo n)
+          const uint32_t tlg = a.tl.tlg, ntl = lg - tlg, ntm = (1u << ntl) - 1u, m = n - 1u;
+          const uint32_t span = (1u << tlg) + 2u * a.halo;
+          const uint32_t ox = (((lbk & ntm) << tlg) - a.halo) & m;
+          const uint32_t oy = ((((lbk >> ntl) & ntm) << tlg) - a.halo) & m;
+          const uint32_t oz = (((lbk >> (2u * ntl)) << tlg) - a.halo) & m;
+          if (((r.ix - ox) & m) >= span || ((r.iy - oy) & m) >= span || ((r.iz - oz) & m) >= span) {
+            rqp = true;
+            active = false;
+          }
+        }
       } else {
         active = false;
         my_cross += kc0 + kend - 1;  // crossings up to the last cell; the first was counted at emission
         if (res == 1) { atomicAdd(ltally + cend, 1u); ++my_abs; }
         else ++my_cap;
+      }
+    }
+    if (RS) {
+      // packets that left their region: appended to the second queue as full
+      // states (the current cell is the next to test), counted in the bucket
+      // of the super-tile they have reached
+      const unsigned rm = __ballot_sync(0xffffffffu, rqp);
+      if (rm) {
+        // the warp's part of the second queue
+        const uint32_t part = (blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) & (uint32_t)(kRqParts - 1);
+        unsigned long long qb = 0;
+        const int leader = __ffs(rm) - 1;
+        if (lane == leader) qb = atomicAdd(&a.rqn[part], (unsigned long long)__popc(rm));
+        qb = __shfl_sync(0xffffffffu, qb, leader);
+        const uint64_t k = qb + __popc(rm & ((1u << lane) - 1u));
+        const bool stored = rqp && k < a.rq_part;
+        const uint64_t slot = (uint64_t)part * a.rq_part + k;
+        if (stored) {
+          V q0v, q1v, q2v;
+          q0v.x = bits_to<R>(cell); q0v.y = r.tMx; q0v.z = r.tMy; q0v.w = r.tMz;
+          q1v.x = r.sx < 0 ? -r.tDx : r.tDx; q1v.y = r.sy < 0 ? -r.tDy : r.tDy; q1v.z = r.sz < 0 ? -r.tDz : r.tDz;
+          q1v.w = r.u0;
+          q2v.x = r.knx; q2v.y = r.kny; q2v.z = r.knz; q2v.w = bits_to<R>(r.kc);
+          a.rq[3 * slot] = q0v;
+          a.rq[3 * slot + 1] = q1v;
+          a.rq[3 * slot + 2] = q2v;
+        }
+        const unsigned sm = __ballot_sync(0xffffffffu, stored);
+        const uint32_t bk = stored ? a.tl.template at<true>(cell) : 0xffffffffu;
+        const unsigned gm = __match_any_sync(0xffffffffu, bk) & sm;
+        if (stored && lane == __ffs(gm) - 1) atomicAdd(&a.rcount[bk], (unsigned long long)__popc(gm));
+        if (rqp && !stored) {  // the second queue is full: this packet marches on without a limit
+          active = true;
+          lbk = 0xffffffffu;
+        }
+        if (__any_sync(0xffffffffu, rqp && !stored) && lane == 0) atomicOr(&a.sc->flags, 16);
+        rqp = false;
       }
     }
   }
@@ -1055,6 +1206,96 @@ __global__ void __launch_bounds__(TT, march_occupancy<R, MB>()) k_march(Transpor
   }
 }
 
+// Region sweeps, between two march launches (one block): the entries each
+// bucket received in the second queue become the march queue of the next
+// sweep: bucket offsets (exclusive prefix of the counts), fills, march-chunk
+// prefix; the counts and the placement fills are reset.
+__global__ void __launch_bounds__(1024) k_requeue_scan(unsigned long long* rcount, unsigned long long* boff,
+                                                       unsigned long long* bfill, unsigned long long* cpre,
+                                                       unsigned long long* scnt, unsigned long long* rqn, int nb,
+                                                       DevScalars* sc, uint32_t chunk, uint64_t part_cap) {
+  constexpr int NTH = 1024;
+  static_assert(kRqParts <= NTH, "one thread per part");
+  __shared__ unsigned long long pe[NTH], pc[NTH];
+  __shared__ unsigned long long stored;
+  if (threadIdx.x == 0) stored = 0;
+  __syncthreads();
+  if (threadIdx.x < kRqParts) {  // entries each part holds for the placement; append counters reset
+    const unsigned long long m = rqn[threadIdx.x], c = m < part_cap ? m : part_cap;
+    rqn[kRqParts + threadIdx.x] = c;
+    rqn[threadIdx.x] = 0;
+    atomicAdd(&stored, c);
+  }
+  const int per = (nb + NTH - 1) / NTH;
+  const int b0 = threadIdx.x * per, b1 = min(nb, (int)(threadIdx.x + 1) * per);
+  unsigned long long se = 0, sc_ = 0;
+  for (int b = b0; b < b1; ++b) {
+    const unsigned long long f = __ldcg(&rcount[b]);
+    se += f;
+    sc_ += (f + chunk - 1) / chunk;
+  }
+  pe[threadIdx.x] = se;
+  pc[threadIdx.x] = sc_;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long re = 0, rc = 0;
+    for (int t = 0; t < NTH; ++t) {
+      const unsigned long long ve = pe[t], vc = pc[t];
+      pe[t] = re; pc[t] = rc;
+      re += ve; rc += vc;
+    }
+    cpre[nb] = rc;
+    sc->requeued += stored;
+    sc->march_next = 0;
+  }
+  __syncthreads();
+  unsigned long long re = pe[threadIdx.x], rc = pc[threadIdx.x];
+  for (int b = b0; b < b1; ++b) {
+    const unsigned long long f = __ldcg(&rcount[b]);
+    boff[b] = re;
+    bfill[b] = f;
+    cpre[b] = rc;
+    re += f;
+    rc += (f + chunk - 1) / chunk;
+    rcount[b] = 0;
+    scnt[b] = 0;
+  }
+}
+
+// Region sweeps: every entry of the second queue to its bucket's range of the
+// march queue (order within a bucket is free: the march of a packet does not
+// depend on the others).
+template <class R>
+__global__ void __launch_bounds__(TT) k_requeue_place(TransportArgs<R> a, unsigned long long* scnt) {
+  using V = typename Vec4<R>::T;
+  const int lane = threadIdx.x & 31;
+  for (int part = blockIdx.x; part < kRqParts; part += gridDim.x) {
+  const uint64_t m = a.rqn[kRqParts + part], off = (uint64_t)part * a.rq_part;
+  for (uint64_t base = (uint64_t)(threadIdx.x >> 5) * 32; base < m; base += TT) {
+    const uint64_t i = base + lane;
+    const bool act = i < m;
+    V q0v, q1v, q2v;
+    uint32_t bk = 0xffffffffu;
+    if (act) {
+      q0v = a.rq[3 * (off + i)]; q1v = a.rq[3 * (off + i) + 1]; q2v = a.rq[3 * (off + i) + 2];
+      bk = a.tl.template at<true>(to_bits<R>(q0v.x));
+    }
+    const unsigned am = __ballot_sync(0xffffffffu, act);
+    const unsigned gm = __match_any_sync(0xffffffffu, bk) & am;
+    const int leader = __ffs(gm) - 1;
+    unsigned long long qb = 0;
+    if (act && lane == leader) qb = atomicAdd(&scnt[bk], (unsigned long long)__popc(gm));
+    qb = __shfl_sync(0xffffffffu, qb, leader < 0 ? 0 : leader);
+    if (act) {
+      const uint64_t slot = a.boff[bk] + qb + __popc(gm & ((1u << lane) - 1u));
+      a.queue[3 * slot] = q0v;
+      a.queue[3 * slot + 1] = q1v;
+      a.queue[3 * slot + 2] = q2v;
+    }
+  }
+  }
+}
+
 __global__ void k_transport_end(DevScalars* sc, rec_stats* st) {
   if (threadIdx.x != 0) return;
   sc->tally_total += sc->absorbed;
@@ -1065,6 +1306,7 @@ __global__ void k_transport_end(DevScalars* sc, rec_stats* st) {
     st->capped = sc->capped;
     st->crossings = sc->crossings;
     st->queued = sc->qtail;
+    st->requeued = sc->requeued;
     st->flags = sc->flags;
   }
 }
@@ -1101,6 +1343,7 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.kappa = (R)kappa;
   a.cth = (R)cth;
   a.strm = s;
+  a.ks = key_schedule(s.k0, s.k1);
   a.tally = b.tally;
   a.sc = c->sc;
   a.queue = (typename Vec4<R>::T*)c->queue;
@@ -1111,6 +1354,12 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
   a.cpre = c->cpre;
   a.chunk = (uint32_t)tu.march_chunk;
   a.refill = tu.march_refill;
+  a.rq = nullptr;
+  a.rcount = nullptr;
+  a.rqn = nullptr;
+  a.rq_part = 0;
+  a.halo = 0;
+  a.resumed = 0;
   {
     GroupTimer t(c, kTEmit, 2);
     const int eb = c->sm_count * tu.emit_blocks_per_sm;
@@ -1118,11 +1367,35 @@ cudaError_t run_transport(rec_ctx* c, int step, double z, rec_stats* st) {
     else k_emit<R, false><<<eb, TT, 0, c->stream>>>(a);
     k_bucket_scan<<<1, 1024, 0, c->stream>>>(c->bfill, c->cpre, nb, c->sc, a.chunk);
   }
-  {
+  const uint32_t halo = (uint32_t)tu.march_halo;
+  const bool sweeps = p2 && halo > 0 && c->rqueue && ((uint32_t)tu.tile + 2u * halo) < (uint32_t)b.n;
+  if (!sweeps) {
     GroupTimer t(c, kTMarch, 1);
     const int mb = c->sm_count * tu.march_blocks_per_sm;
     if (p2) k_march<R, true, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1, nullptr, nullptr);
     else k_march<R, false, false><<<mb, TT, 0, c->stream>>>(a, nullptr, 1, nullptr, nullptr);
+  } else {
+    // region sweeps: each march leaves the packets that stray beyond the halo of
+    // their bucket's super-tile in the second queue; those are placed by the
+    // super-tile they reached and marched by the next sweep; the last sweep has
+    // no limit, so every packet ends
+    GroupTimer t(c, kTMarch, 3 * kMaxSweeps - 2);
+    const int mb = c->sm_count * tu.march_blocks_per_sm;
+    a.rq = (typename Vec4<R>::T*)c->rqueue;
+    a.rcount = c->rcount;
+    a.rqn = c->rqn;
+    a.rq_part = c->rq_cap / kRqParts;
+    cudaMemsetAsync(c->rqn, 0, sizeof(unsigned long long) * kRqParts, c->stream);
+    for (int k = 0; k < kMaxSweeps; ++k) {
+      if (k > 0) {
+        k_requeue_scan<<<1, 1024, 0, c->stream>>>(c->rcount, c->bcap, c->bfill, c->cpre, c->scnt, c->rqn, nb, c->sc,
+                                                  a.chunk, a.rq_part);
+        k_requeue_place<R><<<kRqParts, TT, 0, c->stream>>>(a, c->scnt);
+      }
+      a.resumed = k > 0;
+      a.halo = (k + 1 < kMaxSweeps) ? halo : 0u;
+      k_march<R, true, false, true><<<mb, TT, 0, c->stream>>>(a, nullptr, 1, nullptr, nullptr);
+    }
   }
   {
     GroupTimer t(c, kTEnd, 1);
@@ -1302,7 +1575,7 @@ __device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const
     const BoxDev& d = bxs[cur];
     const EmitBox<R> e{d.P, d.first, (uint32_t)d.n3, d.n, (const V*)d.vel4, (const R*)d.T, d.tally,
                        (R)__ldcg(&bst[cur].kappa), (R)__ldcg(&bst[cur].cth),
-                       Stream{a.strm.k0, a.strm.k1, (uint32_t)cur}, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0};
+                       (uint32_t)cur, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0};
     // power-of-two sides take cell coordinates by shifts and the periodic wrap
     // by masks; other sides by exact multiply-high divisions (the binary64 form
     // keeps one path: both would not fit its register budget)
@@ -1344,6 +1617,7 @@ __device__ __forceinline__ void transport_end_batch(const BoxDev* bxs, int B, co
       st[b].capped = capped;
       st[b].crossings = __ldcg(&sc->crossings);
       st[b].queued = q;
+      st[b].requeued = 0;
       st[b].flags = __ldcg(&sc->flags);
     }
   }
@@ -1394,6 +1668,7 @@ cudaError_t run_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
   a.quant = (const R*)c->quant;
   a.M = c->params.n_quantiles;
   a.strm = Stream{k0, k1, 0u};
+  a.ks = key_schedule(k0, k1);
   a.sc = c->gsc;
   a.queue = (typename Vec4<R>::T*)c->queue;
   a.nb = nb;
@@ -1456,6 +1731,10 @@ cudaError_t run_transport_batch(rec_ctx* c, int step, double z, rec_stats* st) {
 
 // Largest resident blocks per SM of the emission and the march (their
 // launch bounds), for the checks of rec_set_tuning.
+int sweep_march_limit(bool mixed) {
+  return mixed ? march_occupancy<float, false, true>() : march_occupancy<double, false, true>();
+}
+
 void transport_limits(bool mixed, bool batch, int* emit_max, int* march_max) {
   *emit_max = batch ? 4 : (mixed ? emit_occupancy<float>() : emit_occupancy<double>());
   *march_max = batch ? march_occupancy<float, true>()

@@ -42,13 +42,13 @@ class BoxDesc(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("emitted", C.c_uint64), ("absorbed", C.c_uint64), ("capped", C.c_uint64),
                 ("crossings", C.c_uint64), ("queued", C.c_uint64), ("X_e", C.c_double), ("lambda_", C.c_double), ("C_mix", C.c_double),
-                ("S1s", C.c_double), ("newton_passes", C.c_int32), ("flags", C.c_int32)]
+                ("S1s", C.c_double), ("newton_passes", C.c_int32), ("flags", C.c_int32), ("requeued", C.c_uint64)]
 
 
 class Tuning(C.Structure):
     """rec_tuning: transport launch and scheduling parameters (speed only)."""
     _fields_ = [("emit_blocks_per_sm", C.c_int32), ("march_blocks_per_sm", C.c_int32), ("march_refill", C.c_int32),
-                ("march_chunk", C.c_int32), ("tile", C.c_int32)]
+                ("march_chunk", C.c_int32), ("tile", C.c_int32), ("march_halo", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -356,7 +356,8 @@ def _set_tuning(obj, **kw):
 
 def _stats_dict(s) -> dict:
     return dict(emitted=s.emitted, absorbed=s.absorbed, capped=s.capped, crossings=s.crossings, queued=s.queued,
-                X_e=s.X_e, lam=s.lambda_, C=s.C_mix, S1s=s.S1s, newton_passes=s.newton_passes, flags=s.flags)
+                X_e=s.X_e, lam=s.lambda_, C=s.C_mix, S1s=s.S1s, newton_passes=s.newton_passes, flags=s.flags,
+                requeued=s.requeued)
 
 
 class Box:

@@ -15,15 +15,18 @@ apply with `apply_table`.
   python -m paper_2312_11448_gb300.tune --batch 64 --out table.json
 """
 import json
+
+import numpy as np
 import os
 
-FIELDS = ("emit_blocks_per_sm", "march_blocks_per_sm", "march_refill", "march_chunk", "tile")
+FIELDS = ("emit_blocks_per_sm", "march_blocks_per_sm", "march_refill", "march_chunk", "tile", "march_halo")
 CANDIDATES = {
-    "emit_blocks_per_sm": (2, 3, 4, 5),
+    "emit_blocks_per_sm": (2, 3, 4, 5, 6),
     "march_blocks_per_sm": (2, 3, 4, 5),
     "march_refill": (2, 4, 8, 12, 16, 24),
     "march_chunk": (16, 32, 64, 128, 256),
     "tile": (8, 16, 32, 64),
+    "march_halo": (0, 8, 16, 32, 64),
 }
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
@@ -114,7 +117,10 @@ def autotune(obj, step, z, reps=3, rounds=2, candidates=None):
     obj.set_tuning(**start)
 
     def cost(s):
-        obj.set_tuning(**s)
+        try:
+            obj.set_tuning(**s)
+        except RecError:  # a combination the kernels do not accept (e.g. a grid above a variant's limit)
+            return float("inf")
         return time_transport(obj, step, z, reps)
 
     best, ms, log = coordinate_descent(start, cost, candidates, rounds, allowed)
@@ -137,7 +143,8 @@ def apply_table(obj, key, path=TABLE):
     # a stored grid above the kernels' current residency limit (the defaults
     # after rec_init are those limits) is clamped to it
     cur = obj.tuning()
-    setting = {f: entry["setting"][f] for f in FIELDS}
+    # fields the entry predates keep their current value
+    setting = {f: entry["setting"].get(f, cur[f]) for f in FIELDS}
     for f in ("emit_blocks_per_sm", "march_blocks_per_sm"):
         setting[f] = min(setting[f], cur[f])
     obj.set_tuning(**setting)
@@ -158,6 +165,12 @@ def main():
     ap.add_argument("--out", default=None, help="JSON table to update (default: print only)")
     ap.add_argument("--batch", type=int, default=0,
                     help="tune the batched workload of this many boxes instead (z schedule 1600->700, 200)")
+    ap.add_argument("--config", default=None,
+                    help="a named single-box workload of inputs.CONFIGS (its fields, packets and z schedule) "
+                         "instead of --n/--packets")
+    ap.add_argument("--start-z", type=float, default=None,
+                    help="start from the Saha state at the schedule node nearest this redshift, then --prep steps")
+    ap.add_argument("--rounds", type=int, default=2, help="coordinate-descent rounds")
     a = ap.parse_args()
     if a.batch:
         from .inputs import batched_configs
@@ -170,19 +183,27 @@ def main():
         prep = min(a.prep, 60)
         key = batch_key(a.batch, a.precision)
     else:
-        cfg = BoxConfig("tune", a.n, 0.8, 1.0, a.packets, 400, 1800.0, 600.0, None, a.precision)
-        zs = z_schedule(1800.0, 600.0, 400)
+        if a.config:
+            from .inputs import CONFIGS
+            cfg = CONFIGS[a.config]
+            zs = z_schedule(cfg.z_start, cfg.z_end, cfg.n_steps)
+        else:
+            cfg = BoxConfig("tune", a.n, 0.8, 1.0, a.packets, 400, 1800.0, 600.0, None, a.precision)
+            zs = z_schedule(1800.0, 600.0, 400)
         d, U = make_box(cfg, seed=1)
-        box = Box(a.n, d, U, a.packets, precision=a.precision, mixing="tally", seed=1, stream=torch.cuda.Stream())
+        box = Box(cfg.n, d, U, cfg.n_packets, precision=a.precision, mixing="tally", seed=1,
+                  stream=torch.cuda.Stream())
         prep = a.prep
-        key = workload_key(a.n, a.packets, a.precision)
-    box.state_init(zs[0])
-    for s in range(prep):
+        key = workload_key(cfg.n, cfg.n_packets, a.precision)
+    s0 = 0 if a.start_z is None else int(np.argmin(np.abs(zs - a.start_z)))
+    box.state_init(zs[s0])
+    for s in range(s0, s0 + prep):
         box.transport(s, zs[s])
         box.step(s, zs[s], zs[s + 1])
+    prep += s0
     default = box.tuning()
     ms_default = time_transport(box, prep, zs[prep], a.reps)
-    best, ms, log = autotune(box, prep, zs[prep], reps=a.reps)
+    best, ms, log = autotune(box, prep, zs[prep], reps=a.reps, rounds=a.rounds)
     entry = {"setting": best, "ms_per_transport": ms, "default": default, "ms_default": ms_default,
              "trials": len(log), "device": torch.cuda.get_device_name(), "step": prep}
     print(json.dumps({key: entry}))

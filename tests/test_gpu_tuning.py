@@ -35,7 +35,7 @@ def test_single_box_tallies_do_not_depend_on_tuning(precision):
     ref = None
     for s in _settings(t0):
         box.set_tuning(**s)
-        assert box.tuning() == s
+        assert all(box.tuning()[k] == v for k, v in s.items())
         _zero_tallies(box, [box.tally])
         box.transport(3, 1390.0)
         got = (box.tally_np().copy(), {k: box.stats()[k] for k in ("emitted", "absorbed", "crossings", "queued")})
@@ -73,9 +73,85 @@ def test_invalid_tuning_rejected():
     from paper_2312_11448_gb300 import rec
     box = new_box(8, "fp64", n_packets=100)
     t0 = box.tuning()
-    for bad in (dict(emit_blocks_per_sm=0), dict(emit_blocks_per_sm=4), dict(march_blocks_per_sm=5),
+    # the defaults are the kernels' residency limits: one block more is rejected
+    for bad in (dict(emit_blocks_per_sm=0), dict(emit_blocks_per_sm=t0["emit_blocks_per_sm"] + 1),
+                dict(march_blocks_per_sm=t0["march_blocks_per_sm"] + 1),
                 dict(march_refill=33), dict(march_chunk=4), dict(tile=12)):
         with pytest.raises(rec.RecError):
             box.set_tuning(**bad)
         assert box.tuning() == t0
+    box.close()
+
+
+def _sweep_case(cosmo, n, Np, precision, settings):
+    """Tallies and counters of lya_transport under each (halo, tile) setting
+    against the oracle's; returns the statistics records."""
+    import oracle as O
+    from gpu_helpers import oracle_fields, quantiles, set_state
+    box = new_box(n, precision, n_packets=Np, sigma_v=2.0)
+    rng = np.random.default_rng(5)
+    emis = rng.lognormal(0.0, 1.0, n ** 3)
+    T = rng.uniform(2800.0, 3200.0, n ** 3)
+    set_state(box, np.full(n ** 3, 0.5), T, tally=np.zeros(n ** 3, np.uint32), emis=emis)
+    _, _, v4 = oracle_fields(box)
+    prec = "f32" if precision == "mixed" else "f64"
+    ref, cnt, _ = O.transport(cosmo, n, 1100.0, 7, 4, Np, box.host("emis"), v4, box.host("T"), quantiles(box),
+                              precision=prec)
+    limit = box.tuning()["march_blocks_per_sm"]
+    out = []
+    for halo, tile in settings:
+        box.set_tuning(march_halo=halo, tile=tile, march_blocks_per_sm=min(limit, 2))
+        _zero_tallies(box, [box.tally])
+        box.timing(True)
+        box.transport(4, 1100.0)
+        kt = box.kernel_times()
+        box.timing(False)
+        st = box.stats()
+        assert np.array_equal(box.tally_np(), ref), (halo, tile)
+        assert st["absorbed"] == cnt["absorbed"] == Np and st["crossings"] == cnt["crossings"], (halo, tile)
+        if halo:
+            assert kt["march"][1] == 22 and st["requeued"] > 0, (halo, tile, kt["march"], st["requeued"])
+        else:
+            assert kt["march"][1] == 1 and st["requeued"] == 0
+        out.append(st)
+    box.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_region_sweeps_match_the_oracle(cosmo, precision):
+    """march_halo > 0 (region sweeps) on a 64^3 box: tallies and counters
+    bit-identical to the oracle for several halos and super-tile sides; the
+    march group runs its eight sweeps and packets are queued again."""
+    _sweep_case(cosmo, 64, 400_000, precision, ((4, 8), (8, 16), (0, 32)))
+
+
+def test_region_sweeps_with_a_full_second_queue(cosmo):
+    """A one-cell halo around 8-cell super-tiles on a 256^3 box: about 29 % of
+    the packets end outside their first region (oracle per-packet dump), more
+    than the second queue holds (n_packets / 4), so packets find it full and
+    march on without a limit (flags bit 4); the result is still exact."""
+    st = _sweep_case(cosmo, 256, 1_000_000, "mixed", ((1, 8),))
+    assert st[0]["flags"] & 16
+
+
+def test_region_sweep_settings_rejected():
+    from paper_2312_11448_gb300 import rec
+    box = new_box(12, "mixed", n_packets=100)  # not a power of two
+    with pytest.raises(rec.RecError, match="power-of-two"):
+        box.set_tuning(march_halo=4)
+    box.close()
+    box = new_box(16, "mixed", n_packets=100)
+    for bad in (dict(march_halo=-1), dict(march_halo=257)):
+        with pytest.raises(rec.RecError):
+            box.set_tuning(**bad)
+    box.set_tuning(march_halo=4, march_blocks_per_sm=3)
+    assert box.tuning()["march_halo"] == 4
+    box.close()
+    # the FP64 form's sweep march has a lower residency limit (2) than its plain march (3)
+    box = new_box(16, "fp64", n_packets=100)
+    assert box.tuning()["march_blocks_per_sm"] == 3
+    with pytest.raises(rec.RecError, match="march_halo"):
+        box.set_tuning(march_halo=4)
+    box.set_tuning(march_halo=4, march_blocks_per_sm=2)
     box.close()

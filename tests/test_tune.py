@@ -6,11 +6,13 @@ from paper_2312_11448_gb300 import tune
 
 
 def _start():
-    return {"emit_blocks_per_sm": 5, "march_blocks_per_sm": 5, "march_refill": 8, "march_chunk": 64, "tile": 32}
+    return {"emit_blocks_per_sm": 5, "march_blocks_per_sm": 5, "march_refill": 8, "march_chunk": 64, "tile": 32,
+            "march_halo": 0}
 
 
 def test_coordinate_descent_finds_separable_minimum():
-    target = {"emit_blocks_per_sm": 3, "march_blocks_per_sm": 4, "march_refill": 16, "march_chunk": 128, "tile": 16}
+    target = {"emit_blocks_per_sm": 3, "march_blocks_per_sm": 4, "march_refill": 16, "march_chunk": 128, "tile": 16,
+              "march_halo": 16}
 
     def cost(s):
         return sum((s[f] - target[f]) ** 2 / (1 + target[f]) for f in tune.FIELDS) + 1.0
@@ -42,6 +44,9 @@ def test_workload_keys_and_table(tmp_path):
     assert tune.workload_key(8, 0, "fp64") == "n8-ppc1-fp64-single"
     p = tmp_path / "t.json"
     p.write_text(json.dumps({"k": {"setting": _start()}}))
+    old = {f: v for f, v in _start().items() if f != "march_halo"}  # an entry that predates a field
+    p_old = tmp_path / "old.json"
+    p_old.write_text(json.dumps({"k": {"setting": old}}))
     assert tune.load_table(str(p))["k"]["setting"]["tile"] == 32
     assert tune.load_table(str(tmp_path / "missing.json")) == {}
 
@@ -62,3 +67,6 @@ def test_workload_keys_and_table(tmp_path):
     f = Fake(limit=4)
     assert tune.apply_table(f, "k", str(p)) == dict(_start(), emit_blocks_per_sm=4, march_blocks_per_sm=4)
     assert tune.apply_table(f, "absent", str(p)) is None
+    # the missing field keeps the context's current value
+    f = Fake()
+    assert tune.apply_table(f, "k", str(p_old)) == _start()
