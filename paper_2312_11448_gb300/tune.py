@@ -45,8 +45,15 @@ def batch_key(n_boxes, precision):
     return f"batch{n_boxes}-{precision}"
 
 
-def coordinate_descent(start, cost, candidates=None, rounds=2, allowed=None):
-    """Minimise cost(setting) over the candidate grid, one field at a time.
+# Fields searched together: the region sweeps change which march grid is best
+# (a smaller working set per sweep admits more resident blocks), so one field
+# at a time would not leave the grid the plain march prefers.
+JOINT = (("march_blocks_per_sm", "march_halo"),)
+
+
+def coordinate_descent(start, cost, candidates=None, rounds=2, allowed=None, joint=JOINT):
+    """Minimise cost(setting) over the candidate grid, one field (or one joint
+    pair of fields, every combination) at a time.
     start: dict of FIELDS; allowed(field, value) -> bool filters candidates.
     Returns (best setting, best cost, list of (setting, cost) tried)."""
     cand = dict(CANDIDATES if candidates is None else candidates)
@@ -59,12 +66,29 @@ def coordinate_descent(start, cost, candidates=None, rounds=2, allowed=None):
             seen[key] = cost(dict(s))
         return seen[key]
 
+    def ok(f, v):
+        return allowed is None or allowed(f, v)
+
+    paired = {f for pair in joint for f in pair}
     best_cost = evaluate(best)
     for _ in range(rounds):
         improved = False
+        # the joint pairs first: they decide which march variant runs, and the
+        # other fields are then tuned for it
+        for f1, f2 in joint:
+            for v1 in cand.get(f1, (best[f1],)):
+                for v2 in cand.get(f2, (best[f2],)):
+                    if (v1, v2) == (best[f1], best[f2]) or not ok(f1, v1) or not ok(f2, v2):
+                        continue
+                    trial = dict(best, **{f1: v1, f2: v2})
+                    c = evaluate(trial)
+                    if c < best_cost:
+                        best, best_cost, improved = trial, c, True
         for f in FIELDS:
+            if f in paired:
+                continue
             for v in cand.get(f, (best[f],)):
-                if v == best[f] or (allowed is not None and not allowed(f, v)):
+                if v == best[f] or not ok(f, v):
                     continue
                 trial = dict(best, **{f: v})
                 c = evaluate(trial)

@@ -70,3 +70,19 @@ def test_workload_keys_and_table(tmp_path):
     # the missing field keeps the context's current value
     f = Fake()
     assert tune.apply_table(f, "k", str(p_old)) == _start()
+
+
+def test_joint_search_of_march_grid_and_halo():
+    """The sweep march admits a grid the plain march does not want: the best
+    (grid, halo) pair is reachable only by changing both at once."""
+    table = {(4, 0): 6.0, (2, 0): 5.0, (3, 0): 7.0, (3, 32): 1.0, (2, 32): 5.5}
+
+    def cost(s):
+        return table.get((s["march_blocks_per_sm"], s["march_halo"]), float("inf"))
+
+    start = dict(_start(), march_blocks_per_sm=4)
+    best, c, _ = tune.coordinate_descent(start, cost)
+    assert (best["march_blocks_per_sm"], best["march_halo"]) == (3, 32) and c == 1.0
+    # one field at a time stops at the plain march's best grid
+    best1, c1, _ = tune.coordinate_descent(start, cost, joint=())
+    assert (best1["march_blocks_per_sm"], best1["march_halo"]) == (2, 0) and c1 == 5.0
