@@ -103,6 +103,7 @@ typedef struct {
   int32_t n;          /* cube side, 1 <= n <= 1024 */
   void* delta;        /* overdensity rho_b/<rho_b> [n^3]: float (MIXED) | double (FP64); read-only */
   void* vel4;         /* peculiar velocity {Ux,Uy,Uz,unused} km/s [n^3]: float4 | double4;
+                         32-byte aligned (cudaMalloc's alignment; REC_EINVAL otherwise);
                          updated by rec_step (Compton drag) */
   double* x_e;        /* ionisation fraction n_e/n_H [n^3]; updated by rec_step */
   void* T;            /* baryon temperature K [n^3]: float | double; updated by rec_step */

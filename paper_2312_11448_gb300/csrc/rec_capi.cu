@@ -65,6 +65,8 @@ rec_status check_box(const rec_box& b, std::string* why) {
   if (b.n < 1 || b.n > 1024) { *why = "box side n must be in [1, 1024]"; return REC_EINVAL; }
   if (!b.delta || !b.vel4 || !b.x_e || !b.T || !b.tally || !b.emis) { *why = "a field buffer is NULL"; return REC_EINVAL; }
   if (b.n_packets >= (1ull << 32)) { *why = "n_packets must be below 2^32"; return REC_EINVAL; }
+  // the FP64 form reads each velocity as one 32-byte vector; one rule for both forms
+  if (reinterpret_cast<uintptr_t>(b.vel4) % 32 != 0) { *why = "vel4 must be 32-byte aligned"; return REC_EINVAL; }
   return REC_OK;
 }
 
@@ -242,10 +244,7 @@ rec_status rec_init(const rec_params* params, const rec_box* boxes, int32_t n_bo
   if (!boxes || n_boxes < 1) return fail(nullptr, REC_EINVAL, "need at least one box");
   if (n_boxes > 1) return init_batch(params, boxes, n_boxes, cuda_stream, out);
   const rec_box& b = boxes[0];
-  if (b.n < 1 || b.n > 1024) return fail(nullptr, REC_EINVAL, "box side n must be in [1, 1024]");
-  if (!b.delta || !b.vel4 || !b.x_e || !b.T || !b.tally || !b.emis)
-    return fail(nullptr, REC_EINVAL, "a field buffer is NULL");
-  if (b.n_packets >= (1ull << 32)) return fail(nullptr, REC_EINVAL, "n_packets must be below 2^32");
+  if (check_box(b, &why) != REC_OK) return fail(nullptr, REC_EINVAL, why);
 
   rec_ctx* c = new (std::nothrow) rec_ctx();
   if (!c) return fail(nullptr, REC_ENOMEM, "host allocation failed");
@@ -479,6 +478,7 @@ rec_status rec_step_noalloc(const rec_params* params, const rec_box* box, double
   if (box->n < 1 || box->n > 1024) return fail(nullptr, REC_EINVAL, "box side n must be in [1, 1024]");
   if (!box->delta || !box->vel4 || !box->x_e || !box->T || !box->tally || !box->emis)
     return fail(nullptr, REC_EINVAL, "a field buffer is NULL");
+  if (reinterpret_cast<uintptr_t>(box->vel4) % 32 != 0) return fail(nullptr, REC_EINVAL, "vel4 must be 32-byte aligned");
   if (!(z_from > z_to) || !(z_to > 0) || !is_finite(z_from)) return fail(nullptr, REC_EINVAL, "need z_from > z_to > 0");
   s = rec::launch_rec_step_noalloc(*params, *box, z_from, z_to, (cudaStream_t)cuda_stream, dev_stats, &why);
   if (s != REC_OK) return fail(nullptr, s, "rec_step_noalloc: " + why);

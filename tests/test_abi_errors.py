@@ -15,12 +15,14 @@ def _init(params, box, n_boxes=1):
     return rc, rec.lib().rec_last_error(None).decode(), ctx
 
 
-def _box(n=8, n_packets=100, null=None):
+def _box(n=8, n_packets=100, null=None, vel4=None):
     from paper_2312_11448_gb300 import rec
     fake = C.c_void_p(0x1000)  # never dereferenced: validation fails first
     f = {k: fake for k in ("delta", "vel4", "x_e", "T", "tally", "emis")}
     if null:
         f[null] = None
+    if vel4 is not None:
+        f["vel4"] = C.c_void_p(vel4)
     return rec.BoxDesc(n, f["delta"], f["vel4"], f["x_e"], f["T"], f["tally"], f["emis"], n_packets)
 
 
@@ -40,7 +42,8 @@ def test_rec_init_rejects_bad_params(bad, match):
 
 
 @pytest.mark.parametrize("box_kw,match", [(dict(n=0), "box side"), (dict(n=1025), "box side"),
-                                          (dict(null="tally"), "NULL"), (dict(n_packets=2 ** 32), "2^32")])
+                                          (dict(null="tally"), "NULL"), (dict(n_packets=2 ** 32), "2^32"),
+                                          (dict(vel4=0x1010), "32-byte aligned")])
 def test_rec_init_rejects_bad_boxes(box_kw, match):
     from paper_2312_11448_gb300 import rec
     p, q = rec.make_params()

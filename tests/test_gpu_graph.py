@@ -16,20 +16,27 @@ def _zs(n_steps=6):
     return z_schedule(1500.0, 1400.0, n_steps)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_graph_steps_equal_direct_calls(precision):
+@pytest.mark.parametrize("precision,n,halo", [("mixed", 24, 0), ("fp64", 24, 0), ("mixed", 64, 8)])
+def test_graph_steps_equal_direct_calls(precision, n, halo):
+    """halo > 0: the region-sweep march (a memset and 22 kernel nodes) in the graph;
+    the graph step after a change of halo re-instantiates the executable graph."""
     import torch
     from paper_2312_11448_gb300 import rec
-    d, U = make_fields(24, 0.8, 1.0, seed=3)
+    d, U = make_fields(n, 0.8, 2.0, seed=3)
     zs = _zs()
     boxes = []
     for _ in range(2):
         s = torch.cuda.Stream()
-        b = rec.Box(24, d, U, 150_000, precision=precision, mixing="tally", seed=5, stream=s, n_stats=1)
+        b = rec.Box(n, d, U, 150_000, precision=precision, mixing="tally", seed=5, stream=s, n_stats=1)
+        if halo:
+            b.set_tuning(march_halo=halo, tile=16, march_blocks_per_sm=2)
         b.state_init(zs[0])
         boxes.append(b)
     direct, graph = boxes
     for k in range(len(zs) - 1):
+        if halo and k == 3:  # sweeps off, then the graph changes its topology
+            for b in boxes:
+                b.set_tuning(march_halo=0)
         direct.transport(k, zs[k])
         direct.step(k, zs[k], zs[k + 1])
         graph.graph_step(k, zs[k], zs[k + 1])
