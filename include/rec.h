@@ -138,7 +138,8 @@ typedef struct {
  * and every other result are identical for any valid setting. */
 typedef struct {
   int32_t emit_blocks_per_sm;  /* emission grid, blocks of 256 threads per SM: 1..6 (FP64 form 1..4, batch 1..4) */
-  int32_t march_blocks_per_sm; /* march grid: 1..4 (FP64 form, batch and region sweeps 1..3) */
+  int32_t march_blocks_per_sm; /* march grid: 1..4 (FP64 form and batch 1..3); with march_halo > 0
+                                  1..3 (FP64 form 1..2) */
   int32_t march_refill;        /* idle lanes of a warp that trigger a refill from the queue: 1..32 */
   int32_t march_chunk;         /* queued packets per unit of march work handed to a warp: 8..4096 */
   int32_t tile;                /* side of the super-tiles that order the march queue: 8, 16, 32 or 64 */
@@ -244,7 +245,9 @@ rec_status rec_get_tuning(const rec_ctx* ctx, rec_tuning* out);
 
 /* Set the transport tuning; takes effect from the next lya_transport.
  * Synchronises the context stream (a set-up call, not for inside a step).
- * Errors: REC_EINVAL (a field out of range; nothing changed), REC_ECUDA. */
+ * Errors: REC_EINVAL (a field out of range, march_halo > 0 on a batched context
+ * or a box side that is not a power of two; nothing changed), REC_ENOMEM (the
+ * second march queue of the region sweeps), REC_ECUDA. */
 rec_status rec_set_tuning(rec_ctx* ctx, const rec_tuning* tuning);
 
 /* Allocation-free step.  The paper has no counterpart: this is a library entry

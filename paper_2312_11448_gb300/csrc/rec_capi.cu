@@ -143,7 +143,7 @@ rec_status init_batch(const rec_params* params, const rec_box* boxes, int32_t n_
     d.mn2 = b.n >= 2 ? UINT64_MAX / ((uint64_t)b.n * b.n) + 1 : 0;
     d.npk = b.n_packets;
     d.pk0 = c->tot_pk;
-    c->tot_pk += round_up(b.n_packets, 32);
+    c->tot_pk += round_up(b.n_packets, 64);  // a 64-packet emission window never spans two boxes
     d.ablk0 = (uint32_t)c->tot_ablk;
     c->tot_ablk += (int)((d.n3 + rec::kAllocChunk - 1) / rec::kAllocChunk);
     d.pblk = (uint32_t)std::max<int64_t>(1, (d.n3 + rec::kPassThreads * rec::kPassCellsPerThread - 1) /

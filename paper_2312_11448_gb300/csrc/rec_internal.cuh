@@ -94,7 +94,7 @@ struct BoxDev {
   uint64_t mn, mn2;        // multipliers ceil(2^64/n), ceil(2^64/n^2) of the exact divisions (n >= 2)
   uint32_t tlg;            // log2 of the super-tile side in use
   uint64_t npk;        // packets requested per transport
-  uint64_t pk0;        // first packet of the box in the batch packet space (multiple of 32)
+  uint64_t pk0;        // first packet of the box in the batch packet space (multiple of 64)
   uint32_t ablk0;      // first allocation block
   uint32_t bk0;        // first march-queue bucket
   uint32_t pblk0;      // first block of the streaming passes
@@ -190,7 +190,7 @@ struct rec_ctx {
   int tot_ablk = 0;              // allocation blocks of all boxes
   int tot_pblk = 0;              // streaming-pass blocks of all boxes
   int tot_buckets = 0;           // march-queue buckets of all boxes
-  uint64_t tot_pk = 0;           // batch packet space (each box padded to 32)
+  uint64_t tot_pk = 0;           // batch packet space (each box padded to 64)
   // resonant-scattering Monte Carlo (lya_scatter_mc): Voigt nodes and counters
   void* mc_scratch = nullptr;
   size_t mc_bytes = 0;

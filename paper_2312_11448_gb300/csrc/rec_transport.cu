@@ -222,8 +222,10 @@ __global__ void __launch_bounds__(kPassThreads) k_alloc_max(const R* emis, int64
 
 template <class R>
 __device__ __forceinline__ uint64_t quantised(R r, R rmax) {
-  // Q = floor(2^31 r / r_max), the ratio rounded once in the working precision
-  return (uint64_t)Ar<R>::mul(Ar<R>::div(r, rmax), (R)2147483648.0);
+  // Q = floor(2^31 r / r_max), the ratio rounded once in the working precision.
+  // Q <= 2^31 fits 32 bits: the 32-bit truncation gives the same integer as a
+  // 64-bit one without the 64-bit conversion (a binary64-pipe instruction).
+  return (uint64_t)(uint32_t)Ar<R>::mul(Ar<R>::div(r, rmax), (R)2147483648.0);
 }
 
 // Inclusive block scan of 64-bit counts (thread order); returns the block total.
@@ -787,21 +789,21 @@ struct EmitBox {
   uint32_t bk0;
 };
 
-// Emission: one packet per thread.  Packets resonant in their home cell are
-// tallied here; the others take their first step and are queued.  One warp
-// emits the packets base .. base + 31 of one box (N packets).
-template <class R, bool P2, bool FRESH = false>
-__device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitBox<R>& e, uint32_t base, uint32_t N,
-                                          uint64_t& my_abs, uint64_t& my_cross) {
-  using A = Ar<R>;
-  using V = typename Vec4<R>::T;
+// Emission of one packet, in three parts: the cell of each of a warp's 32
+// packets (warp-collective), the packet's first Philox block, frequency and
+// thermal speed (per lane), and the rest (warp-collective): direction, the
+// resonance test in the home cell, the home tally or the queue entry.
+
+// Cell and index within the cell of packet base + lane (< N): the coarse index
+// gives the cell of the warp's first packet, then a 32-cell window of the
+// packet prefix resolves the rest with shuffles.
+template <class R, bool FRESH>
+__device__ __forceinline__ bool emit_locate(const EmitBox<R>& e, uint32_t base, uint32_t N, uint32_t* cell_out,
+                                            uint32_t* j_out) {
   const int lane = threadIdx.x & 31;
-  const uint32_t n = e.n, n3 = e.n3;
-  const R one = (R)1, two = (R)2, zero = (R)0;
-  const uint32_t p = (uint32_t)base + lane;
+  const uint32_t n3 = e.n3;
+  const uint32_t p = base + lane;
   const bool act = p < N;
-  // ---- cell of each packet: the coarse index gives the cell of the warp's
-  // first packet, then a 32-cell window of P resolves the rest with ballots
   const uint32_t c0 = ld_index<FRESH>(e.first + (base >> 5));
   const uint32_t Pc0 = ld_index<FRESH>(e.P + c0);
   const uint32_t widx = c0 + 1u + lane;
@@ -822,15 +824,47 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
     cell = upper_bound<FRESH>(e.P, c0 + 32u, n3, p) - 1u;
     Pc = ld_index<FRESH>(e.P + cell);
   }
+  *cell_out = cell;
+  *j_out = p - Pc;
+  return act;
+}
+
+// (1) injection point uniform in the cell (Philox block 0, which also holds the
+// frequency quantile), the emission frequency from the tabulated inverse CDF
+// and the thermal speed in cells.
+template <class R>
+__device__ __forceinline__ void emit_draw0(const TransportArgs<R>& a, const EmitBox<R>& e, uint32_t cell, uint32_t j,
+                                           R f[3], R* xi, R* vt) {
+  using A = Ar<R>;
+  R uq;
+  Draws<R>::position(KStream{a.ks, e.box}, cell, j, f, &uq);
+  R tq = A::mul(uq, (R)(a.M - 1));
+  int k;
+  const R fr = A::sub(tq, quant_node<R>(tq, a.M, &k));
+  R q0 = __ldg(a.quant + k), q1 = __ldg(a.quant + k + 1);
+  *xi = A::add(q0, A::mul(fr, A::sub(q1, q0)));
+  *vt = A::sqr(A::mul(__ldg(e.T + cell), e.cth));
+}
+
+// The rest of a packet's emission (all lanes of the warp call it; lanes with
+// act false take no part): isotropic direction (Philox blocks 1, 2, ...),
+// u0, the Amanatides-Woo set-up and the resonance test in the home cell;
+// packets resonant at home are tallied (warp-aggregated), the others take
+// their first step and are queued in their home super-tile's bucket.
+template <class R, bool P2>
+__device__ __forceinline__ void emit_rest(const TransportArgs<R>& a, const EmitBox<R>& e, bool act, uint32_t cell,
+                                          uint32_t j, const R f[3], R xi, R vt, uint64_t& my_abs,
+                                          uint64_t& my_cross) {
+  using A = Ar<R>;
+  using V = typename Vec4<R>::T;
+  const int lane = threadIdx.x & 31;
+  const uint32_t n = e.n;
+  const R one = (R)1, two = (R)2, zero = (R)0;
   bool home = false, queued = false;
   Ray<R> r;
   R nx = zero, ny = zero, nz = one;
   if (act) {
-    const uint32_t j = p - Pc;
-    // (1) injection point uniform in the cell, frequency quantile
-    R f[3], uq;
     const KStream ks{a.ks, e.box};
-    Draws<R>::position(ks, cell, j, f, &uq);
     // isotropic direction (Marsaglia 1972): the first accepted of the candidate
     // pairs t = 0, 1, ... (each Philox block is computed once for the pairs it
     // holds).  The pairs of the first block are tested side by side; the loop
@@ -863,13 +897,6 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
         nx = A::mul(v1, fac); ny = A::mul(v2, fac); nz = A::sub(one, A::mul(two, s));
       }
     }
-    // emission frequency from the tabulated inverse CDF
-    R tq = A::mul(uq, (R)(a.M - 1));
-    int k;
-    const R fr = A::sub(tq, quant_node<R>(tq, a.M, &k));
-    R q0 = __ldg(a.quant + k), q1 = __ldg(a.quant + k + 1);
-    R xi = A::add(q0, A::mul(fr, A::sub(q1, q0)));
-    R vt = A::sqr(A::mul(__ldg(e.T + cell), e.cth));
     r.knx = A::mul(e.kappa, nx); r.kny = A::mul(e.kappa, ny); r.knz = A::mul(e.kappa, nz);
     V Uh = e.vel[cell];
     R dh = A::add(A::add(A::mul(r.knx, Uh.x), A::mul(r.kny, Uh.y)), A::mul(r.knz, Uh.z));
@@ -924,6 +951,89 @@ __device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitB
   }
 }
 
+// One warp emits the packets base .. base + 31 of one box (N packets).
+template <class R, bool P2, bool FRESH = false>
+__device__ __forceinline__ void emit_warp(const TransportArgs<R>& a, const EmitBox<R>& e, uint32_t base, uint32_t N,
+                                          uint64_t& my_abs, uint64_t& my_cross) {
+  uint32_t cell, j;
+  const bool act = emit_locate<R, FRESH>(e, base, N, &cell, &j);
+  R f[3] = {(R)0, (R)0, (R)0}, xi = (R)0, vt = (R)0;
+  if (act) emit_draw0<R>(a, e, cell, j, f, &xi, &vt);
+  emit_rest<R, P2>(a, e, act, cell, j, f, xi, vt, my_abs, my_cross);
+}
+
+// A packet emitted at or below the line centre (xi <= 0) is resonant in its
+// home cell whatever its direction: u0 - kappa n.U_home = (xi v_t + d) - d
+// with d = kappa n.U_home is <= 0 by the monotonicity of rounding, and the
+// exit distance is >= 0.  This holds exactly when xi v_t is not NaN (v_t
+// finite) and d is finite (|U| components <= 1e30 keep kappa n.U far from
+// overflow); such packets need no direction and are tallied at once.
+template <class R>
+__device__ __forceinline__ bool home_without_direction(R xi, R vt, const typename Vec4<R>::T& U) {
+  const R big = (R)1e30, vmax = sizeof(R) == 4 ? (R)3.4028234e38f : (R)1.7976931348623157e308;
+  return xi <= (R)0 && vt <= vmax && fabs(U.x) <= big && fabs(U.y) <= big && fabs(U.z) <= big;
+}
+
+// Single-box emission, 64 packets per warp-iteration.  The first Philox block
+// of every packet gives its frequency; the packets with xi <= 0 (about half)
+// are absorbed at home without a direction.  The others are compacted into
+// the warp's lanes through shared memory and finished 32 at a time, so the
+// warp's lanes stay busy in the costly part (direction, ray set-up, home test).
+template <class R>
+struct EmitStash {
+  uint32_t cell[64], j[64];
+  R f0[64], f1[64], f2[64], xi[64], vt[64];
+};
+template <class R, bool P2, bool FRESH = false>
+__device__ __forceinline__ void emit_window64(const TransportArgs<R>& a, const EmitBox<R>& e, EmitStash<R>& st,
+                                              uint32_t base, uint32_t N, uint64_t& my_abs, uint64_t& my_cross) {
+  using V = typename Vec4<R>::T;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t npend = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t cell, j;
+    const bool act = emit_locate<R, FRESH>(e, base + 32u * h, N, &cell, &j);
+    R f[3] = {(R)0, (R)0, (R)0}, xi = (R)0, vt = (R)0;
+    bool early = false;
+    if (act) {
+      emit_draw0<R>(a, e, cell, j, f, &xi, &vt);
+      const V Uh = e.vel[cell];
+      early = home_without_direction<R>(xi, vt, Uh);
+    }
+    // home tally of the early packets (warp-aggregated)
+    const uint32_t key = early ? cell : 0xffffffffu;
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    if (early && lane == __ffs(m) - 1) atomicAdd(e.tally + cell, (uint32_t)__popc(m));
+    if (early) ++my_abs;
+    // the others to the stash, in lane order after the pending ones
+    const bool pend = act && !early;
+    const unsigned pm = __ballot_sync(0xffffffffu, pend);
+    if (pend) {
+      const uint32_t k = npend + __popc(pm & lt);
+      st.cell[k] = cell; st.j[k] = j;
+      st.f0[k] = f[0]; st.f1[k] = f[1]; st.f2[k] = f[2];
+      st.xi[k] = xi; st.vt[k] = vt;
+    }
+    npend += __popc(pm);
+  }
+  __syncwarp();
+  for (uint32_t r0 = 0; r0 < npend; r0 += 32) {
+    const uint32_t k = r0 + lane;
+    const bool act = k < npend;
+    uint32_t cell = 0, j = 0;
+    R f[3] = {(R)0, (R)0, (R)0}, xi = (R)0, vt = (R)0;
+    if (act) {
+      cell = st.cell[k]; j = st.j[k];
+      f[0] = st.f0[k]; f[1] = st.f1[k]; f[2] = st.f2[k];
+      xi = st.xi[k]; vt = st.vt[k];
+    }
+    emit_rest<R, P2>(a, e, act, cell, j, f, xi, vt, my_abs, my_cross);
+  }
+  __syncwarp();  // the stash is reused by the next window
+}
+
 // Resident blocks per SM of the emission (register budget per thread).
 template <class R> constexpr int emit_occupancy() { return sizeof(R) == 4 ? 6 : 4; }
 
@@ -931,11 +1041,13 @@ template <class R, bool P2>
 __global__ void __launch_bounds__(TT, emit_occupancy<R>()) k_emit(TransportArgs<R> a) {
   const EmitBox<R> e{a.P, a.first, (uint32_t)a.n3, (uint32_t)a.n, a.vel, a.T, a.tally, a.kappa, a.cth, 0u, a.tl, 0u};
   const uint32_t N = __ldg(a.P + a.n3);  // packets actually allocated
+  __shared__ EmitStash<R> stash[TT / 32];
+  EmitStash<R>& st = stash[threadIdx.x >> 5];
   uint64_t my_abs = 0, my_cross = 0;
   const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
-  for (uint64_t base = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 32; base < N;
-       base += warps_total * 32)
-    emit_warp<R, P2>(a, e, (uint32_t)base, N, my_abs, my_cross);
+  for (uint64_t base = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 64; base < N;
+       base += warps_total * 64)
+    emit_window64<R, P2>(a, e, st, (uint32_t)base, N, my_abs, my_cross);
   add_counters(a.sc, my_abs, 0, my_cross);
 }
 
@@ -1545,22 +1657,25 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix_batch(const BoxDev* bxs, in
   alloc_prefix_batch<R>(bxs, B, partQ, bcap, blockIdx.x);
 }
 
-// Emission over the batch packet space (each box padded to a multiple of 32,
-// so a warp's 32 packets belong to one box).  FRESH: the packet prefixes and
+// Emission over the batch packet space (each box padded to a multiple of 64,
+// so a warp's 64-packet window belongs to one box).  FRESH: the packet prefixes and
 // box scalars were written earlier in the same launch (read through L2).
 template <class R, bool FRESH>
 __device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const BoxDev* bxs, const BoxStep* bst, int B,
                                                 uint64_t tot_pk) {
   using V = typename Vec4<R>::T;
   __shared__ BoxCounters cnt;
+  __shared__ EmitStash<R> stash[TT / 32];
+  EmitStash<R>& st = stash[threadIdx.x >> 5];
   box_counters_clear(cnt, B);
   uint64_t my_abs = 0, my_cross = 0;
   int cur = -1;
   uint64_t lo_pk = 1, hi_pk = 0;  // packet range of box cur (empty before the first lookup)
   uint32_t N = 0;
   const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
-  for (uint64_t gbase = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 32; gbase < tot_pk;
-       gbase += warps_total * 32) {
+  // 64-packet windows: every box's packet space is padded to a multiple of 64
+  for (uint64_t gbase = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 64; gbase < tot_pk;
+       gbase += warps_total * 64) {
     if (gbase < lo_pk || gbase >= hi_pk) {  // next box (uniform over the warp)
       const int b = last_le(B, gbase, [&](int i) { return bxs[i].pk0; });
       if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
@@ -1579,8 +1694,8 @@ __device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const
     // power-of-two sides take cell coordinates by shifts and the periodic wrap
     // by masks; other sides by exact multiply-high divisions (the binary64 form
     // keeps one path: both would not fit its register budget)
-    if (sizeof(R) == 4 && d.p2) emit_warp<R, true, FRESH>(a, e, (uint32_t)base, N, my_abs, my_cross);
-    else emit_warp<R, false, FRESH>(a, e, (uint32_t)base, N, my_abs, my_cross);
+    if (sizeof(R) == 4 && d.p2) emit_window64<R, true, FRESH>(a, e, st, (uint32_t)base, N, my_abs, my_cross);
+    else emit_window64<R, false, FRESH>(a, e, st, (uint32_t)base, N, my_abs, my_cross);
   }
   if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
   box_counters_flush(cnt, bxs, B);
