@@ -137,7 +137,7 @@ typedef struct {
  * no counterpart in the paper.  They change only the speed: tallies, counters
  * and every other result are identical for any valid setting. */
 typedef struct {
-  int32_t emit_blocks_per_sm;  /* emission grid, blocks of 256 threads per SM: 1..6 (FP64 form 1..4, batch 1..4) */
+  int32_t emit_blocks_per_sm;  /* emission grid, blocks of 256 threads per SM: 1..5 (FP64 form and batch 1..4) */
   int32_t march_blocks_per_sm; /* march grid: 1..4 (FP64 form and batch 1..3); with march_halo > 0
                                   1..3 (FP64 form 1..2) */
   int32_t march_refill;        /* idle lanes of a warp that trigger a refill from the queue: 1..32 */
