@@ -357,3 +357,22 @@ def test_two_slab_flow_closed_form(cosmo, precision, eps):
     s_wrong, _ = _slab_walk(pk, n, s0 - shift, shift, sig)
     c_wrong, _ = _closed_form_cell(pk, n, np.maximum(np.nan_to_num(s_wrong), 0.0), eps)
     assert (c_wrong[ok] != pk["absorb"][ok]).mean() > 0.2
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_packets_at_or_below_line_centre_end_at_home(cosmo, precision):
+    """Emitted at or below the line centre (xi <= 0), a packet is resonant in its
+    home cell whatever its direction and the flow: in the gas frame its
+    frequency is already at or below resonance (u0 - kappa n.U_home = xi v_th
+    <= 0 up to rounding, which cannot make it positive).  The oracle's packets
+    with xi <= 0, in strong random flows of 20 km/s, all end in their home cell
+    without crossing a face, while most of those above the line centre leave."""
+    n, z, Np = 16, 1100.0, 40000
+    emis, _, T, q = _inputs(n, 0.0, seed=9, precision=precision)
+    rng = np.random.default_rng(13)
+    vel4 = pack_vel4(rng.normal(0.0, 20.0, (n ** 3, 3)), emis.dtype)
+    _, cnt, pk = O.transport(cosmo, n, z, 31, 2, Np, emis, vel4, T, q, precision=precision, dump=Np)
+    low = pk["xi"] <= 0.0
+    assert 0.4 < low.mean() < 0.6
+    assert np.array_equal(pk["absorb"][low], pk["home"][low]) and not pk["crossings"][low].any()
+    assert (pk["crossings"][~low] > 0).mean() > 0.75
