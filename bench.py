@@ -683,20 +683,45 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# Source text a kernel's counters depend on: the whole file, or for the march the
+# traversal helpers and the march kernel itself (the emission, which shares the
+# file, can change without changing a byte of the march).
+PROFILED_SOURCE = {
+    "march": ("k_march_256.md", "rec_transport.cu",
+              (("// Traversal state of one packet.", "__device__ __forceinline__ void add_counters("),
+               ("// March of the queued packets.", "__global__ void k_transport_end("))),
+    "emit": ("k_emit_256.md", "rec_transport.cu", None),
+    "rec_step": ("rec_step_passes_256.md", "rec_step.cu", None),
+}
+
+
+def source_hash(src_text, regions):
+    """sha256 (16 hex digits) of the file, or of the concatenated marked regions."""
+    import hashlib
+    if regions is None:
+        return hashlib.sha256(src_text.encode()).hexdigest()[:16]
+    parts = []
+    for a, b in regions:
+        i = src_text.index(a)
+        parts.append(src_text[i:src_text.index(b, i)])
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+
+
 def profiled_traffic(group):
     """dram bytes per launch of a kernel from its committed ncu summary
-    (profiles/<kernel>_256.md), valid only while the kernel source is unchanged
-    (its hash is recorded beside the figure)."""
-    import hashlib
-    files = {"march": ("k_march_256.md", "rec_transport.cu"), "emit": ("k_emit_256.md", "rec_transport.cu"),
-             "rec_step": ("rec_step_passes_256.md", "rec_step.cu")}
-    if group not in files:
+    (profiles/<kernel>_256.md), valid only while the source it depends on is
+    unchanged (its hash is recorded beside the figure)."""
+    if group not in PROFILED_SOURCE:
         return None
-    f = os.path.join(ROOT, "profiles", files[group][0])
-    src = os.path.join(ROOT, "paper_2312_11448_gb300", "csrc", files[group][1])
+    md, src, regions = PROFILED_SOURCE[group]
+    f = os.path.join(ROOT, "profiles", md)
+    srcp = os.path.join(ROOT, "paper_2312_11448_gb300", "csrc", src)
     if not os.path.exists(f):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    try:
+        h = source_hash(open(srcp).read(), regions)
+    except ValueError:  # a marker is gone: the source was reorganised
+        return None
     vals = {}
     for line in open(f):
         if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256_16")):

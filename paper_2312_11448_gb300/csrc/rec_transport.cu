@@ -1739,7 +1739,7 @@ __global__ void __launch_bounds__(AT) k_alloc_prefix_batch(const BoxDev* bxs, in
 // so a warp's 64-packet window belongs to one box).  FRESH: the packet prefixes and
 // box scalars were written earlier in the same launch (read through L2).
 template <class R, bool FRESH>
-__device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const BoxDev* bxs, const BoxStep* bst, int B,
+__device__ __forceinline__ void emit_batch_body_drain(const TransportArgs<R>& a, const BoxDev* bxs, const BoxStep* bst, int B,
                                                 uint64_t tot_pk) {
   using V = typename Vec4<R>::T;
   __shared__ BoxCounters cnt;
@@ -1778,6 +1778,57 @@ __device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const
   if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
   box_counters_flush(cnt, bxs, B);
 }
+// Binary32 batches: the ring carried over between windows (as the single-box
+// emission), flushed at each change of box; one cell-coordinate path (exact
+// multiply-high divisions) for every side keeps the kernel within its registers.
+template <class R, bool FRESH>
+__device__ __forceinline__ void emit_batch_body_ring(const TransportArgs<R>& a, const BoxDev* bxs, const BoxStep* bst,
+                                                     int B, uint64_t tot_pk) {
+  using V = typename Vec4<R>::T;
+  __shared__ BoxCounters cnt;
+  __shared__ EmitStash<R> stash[TT / 32];
+  EmitStash<R>& st = stash[threadIdx.x >> 5];
+  box_counters_clear(cnt, B);
+  uint64_t my_abs = 0, my_cross = 0;
+  int cur = -1;
+  uint64_t lo_pk = 1, hi_pk = 0;  // packet range of box cur (empty before the first lookup)
+  uint32_t N = 0;
+  uint32_t head = 0, count = 0;   // the warp's ring of packets waiting for their direction
+  auto box_of = [&](int b) {
+    const BoxDev& d = bxs[b];
+    return EmitBox<R>{d.P, d.first, (uint32_t)d.n3, d.n, (const V*)d.vel4, (const R*)d.T, d.tally,
+                      (R)__ldcg(&bst[b].kappa), (R)__ldcg(&bst[b].cth),
+                      (uint32_t)b, Tiles{d.n, d.nt, d.lg, d.mn, d.mn2, d.tlg}, d.bk0};
+  };
+  const uint64_t warps_total = (uint64_t)gridDim.x * (TT / 32);
+  for (uint64_t gbase = ((uint64_t)blockIdx.x * (TT / 32) + (threadIdx.x >> 5)) * 64; gbase < tot_pk;
+       gbase += warps_total * 64) {
+    if (gbase < lo_pk || gbase >= hi_pk) {  // next box (uniform over the warp)
+      if (count) emit_flush<R, false>(a, box_of(cur), st, head, count, my_abs, my_cross);
+      const int b = last_le(B, gbase, [&](int i) { return bxs[i].pk0; });
+      if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
+      my_abs = my_cross = 0;
+      cur = b;
+      lo_pk = bxs[b].pk0;
+      hi_pk = (b + 1 < B) ? bxs[b + 1].pk0 : tot_pk;
+      N = ld_index<FRESH>(bxs[b].P + bxs[b].n3);  // packets actually allocated to this box
+    }
+    const uint64_t base = gbase - lo_pk;
+    if (base >= N) continue;  // padding of the packet space
+    emit_window64<R, false, FRESH>(a, box_of(cur), st, (uint32_t)base, N, head, count, my_abs, my_cross);
+  }
+  if (count) emit_flush<R, false>(a, box_of(cur), st, head, count, my_abs, my_cross);
+  if (cur >= 0) box_counters_add(cnt, cur, my_abs, 0, my_cross);
+  box_counters_flush(cnt, bxs, B);
+}
+
+template <class R, bool FRESH>
+__device__ __forceinline__ void emit_batch_body(const TransportArgs<R>& a, const BoxDev* bxs, const BoxStep* bst, int B,
+                                                uint64_t tot_pk) {
+  if (sizeof(R) == 4) emit_batch_body_ring<R, FRESH>(a, bxs, bst, B, tot_pk);
+  else emit_batch_body_drain<R, FRESH>(a, bxs, bst, B, tot_pk);
+}
+
 template <class R>
 __global__ void __launch_bounds__(TT, 4) k_emit_batch(TransportArgs<R> a, const BoxDev* bxs, const BoxStep* bst,
                                                       int B, uint64_t tot_pk) {
