@@ -186,7 +186,7 @@ rec_status rec_refresh(rec_ctx* ctx, double z);
 /* Ly-alpha packet transport at redshift z for step index `step` (keys the
  * random streams): Sec. III.B (packets in proportion to alpha_e n_e^2),
  * Appendix A steps (1) and (4) and omega_r = omega (1 - U_par).  Emits
- * n_packets packets (allocation proportional to emis; x_e, T and vel4 are read,
+ * n_packets packets (allocation proportional to emis; emis, T and vel4 are read,
  * not written), marches each to its resonance cell and adds it to tally
  * (uint32, caller-owned; rec_step zeroes it).  The result does not depend on
  * rec_tuning.  Counters go to dev_stats (device pointer, may be NULL).
