@@ -30,7 +30,8 @@ def test_march_traffic_is_keyed_to_the_march_source_only():
         assert src.count(a) == 1 and src.count(b) == 1 and src.index(a) < src.index(b)
     h = bench.source_hash(src, regions)
     # a change outside the march regions (the emission) keeps the hash ...
-    i = src.index("__device__ __forceinline__ void add_counters(") + 10
+    end1 = "__device__ __forceinline__ void add_counters("
+    i = src.index(end1) + len(end1)
     assert bench.source_hash(src[:i] + "// x\n" + src[i:], regions) == h
     # ... one inside them does not
     j = src.index("// March of the queued packets.") + 40
