@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kPassThreads) k_alloc_max(const R* emis, int64
   double anybad = combine_max<kPassThreads>(part, gridDim.x, kMaxSums, 1);
   if (threadIdx.x == 0) {
     sc->rmax = anybad > 0.0 ? 0.0 : mx;  // invalid weights: emit nothing
-    sc->flags &= ~(2 | 4);               // transport flags describe this call only
+    sc->flags &= ~(2 | 4 | 16);          // transport flags describe this call only
     if (anybad > 0.0) sc->flags |= 4;
     sc->counter = 0;
   }
@@ -1646,7 +1646,7 @@ __device__ __forceinline__ void alloc_max_batch(const BoxDev* bxs, int B, DevSca
     if (lane == 0) {
       DevScalars* sc = bxs[i].sc;
       sc->rmax = anybad > 0.0 ? 0.0 : mx;
-      sc->flags &= ~(2 | 4);
+      sc->flags &= ~(2 | 4 | 16);
       if (anybad > 0.0) sc->flags |= 4;
     }
   }

@@ -131,8 +131,9 @@ def test_region_sweeps_with_a_full_second_queue(cosmo):
     the packets end outside their first region (oracle per-packet dump), more
     than the second queue holds (n_packets / 4), so packets find it full and
     march on without a limit (flags bit 4); the result is still exact."""
-    st = _sweep_case(cosmo, 256, 1_000_000, "mixed", ((1, 8),))
+    st = _sweep_case(cosmo, 256, 1_000_000, "mixed", ((1, 8), (0, 32)))
     assert st[0]["flags"] & 16
+    assert not st[1]["flags"] & 16  # the flag describes one transport call
 
 
 def test_region_sweep_settings_rejected():
