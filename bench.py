@@ -637,31 +637,46 @@ def oracle_sample(cfg, zs, sample_packets, threads=0):
     return t_tr, t_st
 
 
+def oracle_step_estimate(cfg, zs, sample_packets, threads=0):
+    """Seconds of one whole oracle step on this workload, from the transport of
+    `sample_packets` and of half as many (the time is affine in the packet
+    count: a fixed part for the allocation over every cell, then a cost per
+    packet) plus one rec_step over every cell.  Returns (step s, transport s of
+    the sample, rec_step s, fixed transport s, transport s per packet)."""
+    sample_packets = min(sample_packets, cfg.n_packets)
+    half = max(1, sample_packets // 2)
+    t_tr, t_st = oracle_sample(cfg, zs, sample_packets, threads)
+    t_half, _ = oracle_sample(cfg, zs, half, threads)
+    per = max(t_tr - t_half, 0.0) / max(sample_packets - half, 1)
+    fixed = max(t_tr - per * sample_packets, 0.0)
+    return fixed + per * cfg.n_packets + t_st, t_tr, t_st, fixed, per
+
+
 def cpu_baseline_all_cores(cfg, zs, sample_packets=20_000_000):
     """The OpenMP build of the oracle's transport on every host core (the
     rec_step single-threaded), same workload and sample scaling."""
     cores = os.cpu_count() or 1
     sample_packets = min(sample_packets, cfg.n_packets)
-    t_tr, t_st = oracle_sample(cfg, zs, sample_packets, threads=cores)
-    t_step = t_st + t_tr * (cfg.n_packets / sample_packets)
+    t_step, t_tr, t_st, fixed, per = oracle_step_estimate(cfg, zs, sample_packets, threads=cores)
     return {"value": cfg.n ** 3 / t_step, "unit": "cell-steps/s", "cores": cores, "kind": "oracle (OpenMP build)",
-            "packets_per_s": sample_packets / t_tr,
-            "sample": (f"OpenMP build of the oracle source: transport of {sample_packets:.0e} of the "
-                       f"{cfg.n_packets:.0e} packets over {cores} threads ({t_tr:.2f} s, scaled linearly) + the "
+            "packets_per_s": 1.0 / per if per > 0 else None,
+            "sample": (f"OpenMP build of the oracle source: transport of {sample_packets:.0e} and of half as many "
+                       f"of the {cfg.n_packets:.0e} packets over {cores} threads ({t_tr:.2f} s for the sample; "
+                       f"extrapolated affinely: {fixed:.2f} s fixed + {per * 1e6:.3f} s per 1e6 packets) + the "
                        f"single-threaded oracle rec_step over all {cfg.n}^3 cells ({t_st:.2f} s); "
                        f"{platform_name()}")}
 
 
 def cpu_baseline(cfg, zs, sample_packets=4_000_000):
     sample_packets = min(sample_packets, cfg.n_packets)
-    t_tr, t_st = oracle_sample(cfg, zs, sample_packets)
-    t_step = t_st + t_tr * (cfg.n_packets / sample_packets)
+    t_step, t_tr, t_st, fixed, per = oracle_step_estimate(cfg, zs, sample_packets)
     return {"value": cfg.n ** 3 / t_step, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "packets_per_s": sample_packets / t_tr,
+            "packets_per_s": 1.0 / per if per > 0 else None,
             "sample": (f"one oracle rec_step over all {cfg.n}^3 cells ({t_st:.2f} s) + oracle transport of "
-                       f"{sample_packets:.0e} of the {cfg.n_packets:.0e} packets ({t_tr:.2f} s), transport time "
-                       f"scaled linearly to the full packet count; single-threaded, {os.cpu_count()} host cores "
-                       f"present ({platform_name()})")}
+                       f"{sample_packets:.0e} and of half as many of the {cfg.n_packets:.0e} packets ({t_tr:.2f} s "
+                       f"for the sample), extrapolated affinely to the full packet count ({fixed:.2f} s fixed + "
+                       f"{per * 1e6:.3f} s per 1e6 packets); single-threaded, {os.cpu_count()} host cores present "
+                       f"({platform_name()})")}
 
 
 def platform_name():
@@ -952,20 +967,35 @@ def run_reference(args):
         oracle_sample(cfg, zs, sample)
     tot = 0.0
     for _ in range(K):
-        t_tr, t_st = oracle_sample(cfg, zs, sample)
-        tot += t_st + t_tr * (cfg.n_packets / sample)
+        tot += oracle_step_estimate(cfg, zs, sample)[0]
     ms = tot / K * 1e3
     value = cfg.n ** 3 / (ms * 1e-3)
+    # an unsampled anchor: one whole oracle step (every packet) on a 64^3 box at
+    # the same packets per cell, against the rate the sampled step assumes
+    n_a = 64
+    cfg_a, zs_a = workload(n_a, max(1, int(round(cfg.n_packets * (n_a / cfg.n) ** 3))))
+    t_tr_a, t_st_a = oracle_sample(cfg_a, zs_a, cfg_a.n_packets)
+    est_a = oracle_step_estimate(cfg_a, zs_a, cfg_a.n_packets // 16)[0]
+    anchor = {"workload": describe(cfg_a, "oracle") + ", every packet transported",
+              "ms_per_step": (t_tr_a + t_st_a) * 1e3, "cell_steps_per_s": n_a ** 3 / (t_tr_a + t_st_a),
+              "packets_per_s": cfg_a.n_packets / t_tr_a,
+              "estimate_from_a_1_16_sample_ms": est_a * 1e3,
+              "note": "a whole oracle step at 64^3 (same packets per cell), and the same step estimated the "
+                      "way the 256^3 line is (affine in the packets, from a sample and half of it)"}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": 0, "steps": K,
            "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64 (oracle; binary32 transport arithmetic; transport sampled and scaled)", "data": "synthetic",
+           "dtype": "f64 (oracle; binary32 transport arithmetic; transport sampled and extrapolated)", "data": "synthetic",
            "config": {"workload": describe(cfg, "oracle"), "n": cfg.n, "packets_per_step": cfg.n_packets,
-                      "sampled": f"each timed step transports {sample:.0e} of the {cfg.n_packets:.0e} packets and "
-                                 f"scales that time linearly; ms_per_step is the scaled step, not wall time"},
+                      "sampled": f"each timed step transports {sample:.0e} and {sample // 2:.0e} of the "
+                                 f"{cfg.n_packets:.0e} packets and extrapolates the transport time affinely "
+                                 f"(fixed allocation + cost per packet); ms_per_step is that estimate, not wall "
+                                 f"time"},
            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                            "sample": f"per step: oracle rec_step over all cells + transport of {sample:.0e} packets "
-                                      f"scaled to {cfg.n_packets:.0e}; {platform_name()}"},
-           "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                            "sample": f"per step: oracle rec_step over all cells + transport of {sample:.0e} and "
+                                      f"{sample // 2:.0e} packets extrapolated to {cfg.n_packets:.0e}; "
+                                      f"{platform_name()}"},
+           "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "unsampled_anchor": anchor}
     print(json.dumps(out), flush=True)
 
 
